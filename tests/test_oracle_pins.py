@@ -1,0 +1,424 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: brute force
+in numpy, finite differences, scipy/numpy library routines, closed forms and
+invariants.  The cited passages are those of the Open3D paper (arXiv 1801.09847).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+from scipy.spatial.transform import Rotation
+
+from paper_1801_09847_gb300 import synth
+from tests import _independent as ind
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+# ------------------------------------------------------------ a3: transform
+
+
+def test_transform_identity_is_exact(ora):
+    g = synth.rng(10)
+    s = g.uniform(-3, 3, (500, 3)).astype(np.float32)
+    assert np.array_equal(ora.transform(s, np.eye(4)), s)
+
+
+def test_transform_within_fp32_rounding_of_fp64(ora):
+    """p = R s + t evaluated in FP32 stays within a few ulps of the exact FP64 value."""
+    g = synth.rng(11)
+    s = g.uniform(-3, 3, (2000, 3)).astype(np.float32)
+    T = synth.perturbation(g, 40.0, 0.7)
+    p = ora.transform(s, T).astype(np.float64)
+    exact = synth.apply_T(T, s.astype(np.float64))
+    scale = np.abs(s.astype(np.float64)) @ np.abs(T[:3, :3]).T + np.abs(T[:3, 3])
+    assert np.all(np.abs(p - exact) <= 8 * 2.0**-24 * scale)
+
+
+# ------------------------------------------------------------------ a4: NN
+
+
+def test_nn_golden_tiny(ora):
+    gd = _golden("nn_tiny.json")
+    corr, d2 = ora.nn(np.array(gd["queries"], np.float32), np.array(gd["targets"], np.float32), gd["r_max"])
+    assert corr.tolist() == gd["corr"]
+    assert np.array_equal(d2, np.array(gd["d2"], np.float32))
+
+
+@pytest.mark.parametrize("ns,nt,r", [(1, 1, 0.3), (257, 1000, 0.2), (1500, 700, 0.5), (64, 2000, 0.05)])
+def test_nn_matches_numpy_bruteforce_bitexact(ora, ns, nt, r):
+    g = synth.rng(100 + ns)
+    tgt = g.uniform(-1, 1, (nt, 3)).astype(np.float32)
+    # include duplicates of targets (exact ties) and points far away
+    p = g.uniform(-1.2, 1.2, (ns, 3)).astype(np.float32)
+    p[: ns // 4] = tgt[g.integers(0, nt, ns // 4)]
+    dup = tgt.copy()
+    tgt2 = np.vstack([tgt, dup[: nt // 3]])  # later duplicates must lose ties
+    c1, d1 = ora.nn(p, tgt2, r, threads=3)
+    c2, d2 = ind.nn_bruteforce_f32(p, tgt2, r)
+    assert np.array_equal(c1, c2)
+    assert np.array_equal(d1, d2)
+    assert np.all(c1[: ns // 4] < nt)  # duplicates never win over the lower index
+
+
+def test_nn_agrees_with_kdtree_where_unambiguous(ora):
+    """scipy's kd-tree (FP64 distances) gives the same neighbour wherever the FP64 gap is not tiny."""
+    g = synth.rng(12)
+    tgt = g.uniform(-1, 1, (3000, 3)).astype(np.float32)
+    p = g.uniform(-1, 1, (3000, 3)).astype(np.float32)
+    r = 0.15
+    corr, d2 = ora.nn(p, tgt, r)
+    tree = cKDTree(tgt.astype(np.float64))
+    dist, idx = tree.query(p.astype(np.float64), k=2)
+    within = dist[:, 0] <= r * (1 - 1e-5)
+    clear = (dist[:, 1] - dist[:, 0] > 1e-5) & within
+    assert np.array_equal(corr[clear], idx[clear, 0])
+    outside = dist[:, 0] > r * (1 + 1e-5)
+    assert np.all(corr[outside] == -1)
+    assert np.allclose(np.sqrt(d2[clear]), dist[clear, 0], rtol=1e-6, atol=1e-7)
+
+
+def test_nn_radius_boundary_inclusive(ora):
+    r = np.float32(0.05)
+    tgt = np.array([[r, 0, 0], [0, np.nextafter(r, np.float32(1)), 0]], np.float32)
+    p = np.zeros((1, 3), np.float32)
+    corr, d2 = ora.nn(p, tgt, float(r))
+    assert corr[0] == 0 and d2[0] == r * r
+    corr, _ = ora.nn(p, tgt[1:], float(r))
+    d_out = np.float32(tgt[1, 1]) * np.float32(tgt[1, 1])
+    assert (corr[0] == -1) == (d_out > r * r)
+
+
+def test_nn_empty_target(ora):
+    p = np.zeros((5, 3), np.float32)
+    corr, _ = ora.nn(p, np.zeros((0, 3), np.float32), 1.0)
+    assert np.all(corr == -1)
+
+
+# --------------------------------------------------- a5: residual, Jacobian
+
+
+def test_jacobian_matches_finite_differences(ora):
+    """J = [p x n ; n] is the derivative of r(xi) = (exp(xi) p - q) . n at xi = 0 (Eq. 2's J_r)."""
+    g = synth.rng(13)
+    for _ in range(20):
+        p = g.uniform(-2, 2, 3).astype(np.float32)
+        q = (p + g.normal(0, 0.05, 3)).astype(np.float32)
+        n = synth.random_unit(g).astype(np.float32)
+        J, r = ora.residual_jacobian(p, q, n)
+        Jfd = ind.fd_jacobian(p[None], q[None], n[None])[0]
+        assert np.allclose(J, Jfd, rtol=1e-6, atol=1e-8)
+        assert r == pytest.approx(float(np.dot(p.astype(np.float64) - q, n.astype(np.float64))), abs=1e-15)
+
+
+def _random_corr_problem(g, n=400):
+    tgt = g.uniform(-1, 1, (n, 3)).astype(np.float32)
+    nrm = np.array([synth.random_unit(g) for _ in range(n)], np.float32)
+    p = (tgt + g.normal(0, 0.02, tgt.shape)).astype(np.float32)
+    corr = np.arange(n, dtype=np.int32)
+    corr[::7] = -1
+    d2 = np.sum((p - tgt) ** 2, axis=1).astype(np.float32)
+    return p, tgt, nrm, corr, d2
+
+
+def test_normal_equations_equal_gauss_newton_of_fd_jacobian(ora):
+    """A = J^T J and b = J^T r with J from finite differences of the residuals (Eq. 1-2)."""
+    g = synth.rng(14)
+    p, tgt, nrm, corr, d2 = _random_corr_problem(g)
+    A, b, sr2, sd2, cnt = ora.normal_equations(p, tgt, nrm, corr, d2)
+    m = corr >= 0
+    Jfd = ind.fd_jacobian(p[m], tgt[corr[m]], nrm[corr[m]])
+    r = ind.residuals(np.zeros(6), p[m], tgt[corr[m]], nrm[corr[m]])
+    assert cnt == m.sum()
+    assert np.allclose(A, Jfd.T @ Jfd, rtol=1e-6, atol=1e-9)
+    assert np.allclose(b, Jfd.T @ r, rtol=1e-6, atol=1e-10)
+    assert sr2 == pytest.approx(float(r @ r), rel=1e-12)
+    assert sd2 == pytest.approx(float(np.sum(d2[m].astype(np.float64))), rel=1e-12)
+
+
+def test_normal_equations_symmetric_psd_and_sign_invariant(ora):
+    g = synth.rng(15)
+    p, tgt, nrm, corr, d2 = _random_corr_problem(g)
+    A, b, *_ = ora.normal_equations(p, tgt, nrm, corr, d2)
+    assert np.array_equal(A, A.T)
+    ev = np.linalg.eigvalsh(A)
+    assert ev.min() >= -1e-12 * ev.max()
+    flip = nrm.copy()
+    flip[::3] *= -1
+    A2, b2, *_ = ora.normal_equations(p, tgt, flip, corr, d2)
+    assert np.array_equal(A, A2) and np.array_equal(b, b2)
+
+
+def test_normal_equations_identity_gives_zero_gradient(ora):
+    g = synth.rng(16)
+    s = g.uniform(-1, 1, (300, 3)).astype(np.float32)
+    nrm = np.array([synth.random_unit(g) for _ in range(300)], np.float32)
+    p = ora.transform(s, np.eye(4))
+    corr, d2 = ora.nn(p, s, 0.01)
+    assert np.array_equal(corr, np.arange(300))
+    A, b, sr2, sd2, cnt = ora.normal_equations(p, s, nrm, corr, d2)
+    assert np.all(b == 0.0) and sr2 == 0.0 and sd2 == 0.0 and cnt == 300
+
+
+def test_plane_gives_rank_three(ora):
+    g = synth.rng(17)
+    tgt = np.column_stack([g.uniform(-1, 1, 500), g.uniform(-1, 1, 500), np.zeros(500)]).astype(np.float32)
+    nrm = np.tile(np.array([0, 0, 1], np.float32), (500, 1))
+    p = (tgt + np.array([0, 0, 0.01], np.float32)).astype(np.float32)
+    corr = np.arange(500, dtype=np.int32)
+    A, b, *_ = ora.normal_equations(p, tgt, nrm, corr, np.zeros(500, np.float32))
+    for k in (2, 3, 4):  # gamma, t_x, t_y
+        assert np.all(A[k] == 0) and np.all(A[:, k] == 0) and b[k] == 0
+    assert np.linalg.matrix_rank(A) == 3
+
+
+# -------------------------------------------------------------- a6: solve
+
+
+def test_ldlt_matches_numpy_solve_on_spd(ora):
+    g = synth.rng(18)
+    for _ in range(50):
+        M = g.standard_normal((6, 6))
+        A = M @ M.T + 0.1 * np.eye(6)
+        b = g.standard_normal(6)
+        xi, nf = ora.ldlt_solve(A, b)
+        assert nf == 0
+        ref = np.linalg.solve(A, -b)
+        assert np.linalg.norm(xi - ref) <= 1e-12 * np.linalg.cond(A) * np.linalg.norm(ref)
+
+
+def test_ldlt_frozen_pivot_solves_reduced_system(ora):
+    g = synth.rng(19)
+    M = g.standard_normal((6, 6))
+    A = M @ M.T + np.eye(6)
+    A[[1, 4], :] = 0
+    A[:, [1, 4]] = 0
+    b = g.standard_normal(6)
+    b[[1, 4]] = 0
+    xi, nf = ora.ldlt_solve(A, b)
+    assert nf == 2 and xi[1] == 0 and xi[4] == 0
+    keep = [0, 2, 3, 5]
+    ref = np.linalg.solve(A[np.ix_(keep, keep)], -b[keep])
+    assert np.allclose(xi[keep], ref, rtol=1e-12, atol=1e-14)
+
+
+def test_ldlt_all_zero_freezes_everything(ora):
+    xi, nf = ora.ldlt_solve(np.zeros((6, 6)), np.ones(6))
+    assert nf == 6 and np.all(xi == 0)
+
+
+def test_delta_T_is_intrinsic_zyx_euler(ora):
+    """dR = Rz(gamma) Ry(beta) Rx(alpha): scipy's intrinsic 'ZYX' with angles (gamma, beta, alpha)."""
+    g = synth.rng(20)
+    for _ in range(20):
+        xi = g.uniform(-0.5, 0.5, 6)
+        dT = ora.delta_T(xi)
+        R = Rotation.from_euler("ZYX", [xi[2], xi[1], xi[0]]).as_matrix()
+        assert np.allclose(dT[:3, :3], R, atol=1e-15)
+        assert np.array_equal(dT[:3, 3], xi[3:]) and np.array_equal(dT[3], [0, 0, 0, 1])
+
+
+def test_one_gauss_newton_step_matches_lstsq(ora):
+    """The step of Eq. 2 is the least-squares solution of J xi = -r with J from finite differences."""
+    g = synth.rng(21)
+    p, tgt, nrm, corr, d2 = _random_corr_problem(g, 300)
+    A, b, *_ = ora.normal_equations(p, tgt, nrm, corr, d2)
+    xi, nf = ora.ldlt_solve(A, b)
+    m = corr >= 0
+    Jfd = ind.fd_jacobian(p[m], tgt[corr[m]], nrm[corr[m]])
+    r = ind.residuals(np.zeros(6), p[m], tgt[corr[m]], nrm[corr[m]])
+    ref = np.linalg.lstsq(Jfd, -r, rcond=None)[0]
+    assert nf == 0
+    assert np.allclose(xi, ref, rtol=1e-5, atol=1e-9)
+
+
+def test_planar_closed_form_golden(ora):
+    """Golden closed-form step on a planar scene (Eq. 2); derivation in tests/golden/planar_step.json."""
+    gd = _golden("planar_step.json")
+    xs, ys = np.meshgrid(np.linspace(-1, 1, 21), np.linspace(-1, 1, 21))
+    tgt = np.column_stack([xs.ravel(), ys.ravel(), np.zeros(xs.size)]).astype(np.float32)
+    nrm = np.tile(np.array([0, 0, 1], np.float32), (len(tgt), 1))
+    for case in gd["cases"]:
+        a, b_, c = case["a"], case["b"], case["c"]
+        src = np.column_stack([xs.ravel(), ys.ravel(), a * xs.ravel() + b_ * ys.ravel() + c]).astype(np.float32)
+        p = ora.transform(src, np.eye(4))
+        corr = np.arange(len(tgt), dtype=np.int32)  # the vertical neighbour is the correspondence
+        d2 = np.sum((p - tgt) ** 2, axis=1).astype(np.float32)
+        A, b, *_ = ora.normal_equations(p, tgt, nrm, corr, d2)
+        xi, nf = ora.ldlt_solve(A, b)
+        assert nf == 3
+        assert np.allclose(xi, case["xi"], atol=2e-7), (xi, case["xi"])
+
+
+# --------------------------------------------------------- whole ICP loop
+
+
+def _corner_scene(g, spacing=0.02):
+    """Three orthogonal 1 x 1 planes (a room corner) plus a sphere: all six DOF observable; analytic normals."""
+    u = np.arange(0.0, 1.0, spacing)
+    a, b = np.meshgrid(u, u)
+    a, b = a.ravel(), b.ravel()
+    z0 = np.zeros_like(a)
+    P = [np.column_stack([a, b, z0]), np.column_stack([a, z0, b]), np.column_stack([z0, a, b])]
+    N = [np.tile([0, 0, 1.0], (len(a), 1)), np.tile([0, 1.0, 0], (len(a), 1)), np.tile([1.0, 0, 0], (len(a), 1))]
+    v = g.standard_normal((1500, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    P.append(0.2 * v + np.array([0.5, 0.5, 0.5]))
+    N.append(v)
+    return np.vstack(P), np.vstack(N)
+
+
+def test_icp_recovers_known_transform_noise_free(ora):
+    """Noise-free source = T_gt^-1 target: ICP returns T_gt (limited by FP32 input rounding), fitness 1."""
+    g = synth.rng(22)
+    tgt, nrm = _corner_scene(g)
+    T_gt = synth.perturbation(g, 2.0, 0.02)
+    src = synth.apply_T(synth.inv_T(T_gt), tgt).astype(np.float32)
+    res = ora.icp_point_to_plane(src, tgt.astype(np.float32), nrm.astype(np.float32), np.eye(4), 0.05, 30)
+    ang, dt = synth.pose_error(res["T"], T_gt)
+    assert ang < 1e-6 and dt < 1e-6, (ang, dt)
+    assert res["fitness"] == 1.0 and res["rmse"] < 1e-6 and res["status"] == 0
+
+
+def test_icp_equivariance(ora):
+    """Moving both clouds by G turns the result T into G T G^-1."""
+    g = synth.rng(23)
+    tgt, nrm = _corner_scene(g, spacing=0.03)
+    T_gt = synth.perturbation(g, 2.0, 0.02)
+    src = synth.apply_T(synth.inv_T(T_gt), tgt) + g.normal(0, 0.001, tgt.shape)
+    G = synth.perturbation(g, 30.0, 0.5)
+    r1 = ora.icp_point_to_plane(src.astype(np.float32), tgt.astype(np.float32), nrm.astype(np.float32),
+                                np.eye(4), 0.05, 20)
+    tgt_g = synth.apply_T(G, tgt)
+    nrm_g = nrm @ G[:3, :3].T
+    r2 = ora.icp_point_to_plane(synth.apply_T(G, src).astype(np.float32), tgt_g.astype(np.float32),
+                                nrm_g.astype(np.float32), np.eye(4), 0.05, 20)
+    ang, dt = synth.pose_error(r2["T"], G @ r1["T"] @ synth.inv_T(G))
+    assert ang < 1e-5 and dt < 1e-5, (ang, dt)
+
+
+def test_icp_few_correspondences_status(ora):
+    g = synth.rng(24)
+    tgt = g.uniform(-1, 1, (100, 3)).astype(np.float32)
+    src = (tgt + 10.0).astype(np.float32)
+    nrm = np.tile(np.array([0, 0, 1], np.float32), (100, 1))
+    T0 = np.eye(4)
+    res = ora.icp_point_to_plane(src, tgt, nrm, T0, 0.1, 10)
+    assert res["status"] == ora.WARN_FEW_CORR and res["iters"] == 0
+    assert np.array_equal(res["T"], T0) and res["fitness"] == 0.0 and res["rmse"] == 0.0
+
+
+def test_icp_planar_scene_is_degenerate(ora):
+    g = synth.rng(25)
+    tgt = np.column_stack([g.uniform(-1, 1, 800), g.uniform(-1, 1, 800), np.zeros(800)]).astype(np.float32)
+    nrm = np.tile(np.array([0, 0, 1], np.float32), (800, 1))
+    src = (tgt + np.array([0, 0, 0.01], np.float32)).astype(np.float32)
+    res = ora.icp_point_to_plane(src, tgt, nrm, np.eye(4), 0.1, 5)
+    assert res["status"] == ora.WARN_DEGENERATE
+    assert abs(res["T"][2, 3] + 0.01) < 1e-6  # t_z recovered; the in-plane DOF stay frozen
+
+
+def test_icp_sphere_plane_config_runs(ora):
+    """The 4,096-point sphere-plus-plane pair: all source points find partners and the rmse is near the noise."""
+    pr = synth.sphere_plane_pair()
+    res = ora.icp_point_to_plane(pr.src, pr.tgt, pr.tgt_nrm, np.eye(4), pr.max_corr_dist, pr.max_iter)
+    assert res["iters"] == 30 and res["fitness"] > 0.99
+    ang, dt = synth.pose_error(res["T"], pr.T_gt)
+    assert dt < 2e-3  # rotation about z is unobservable for this scene (see the scene notes)
+
+
+def test_max_iter_zero_is_evaluation_only(ora):
+    pr = synth.sphere_plane_pair(n=500)
+    res = ora.icp_point_to_plane(pr.src, pr.tgt, pr.tgt_nrm, np.eye(4), 0.05, 0)
+    assert res["iters"] == 0 and np.array_equal(res["T"], np.eye(4))
+    p = ora.transform(pr.src, np.eye(4))
+    corr, d2 = ind.nn_bruteforce_f32(p, pr.tgt, 0.05)
+    m = corr >= 0
+    assert res["fitness"] == m.sum() / len(p)
+    assert res["rmse"] == pytest.approx(math.sqrt(np.sum(d2[m].astype(np.float64)) / m.sum()), rel=1e-12)
+
+
+# ------------------------------------------------------------- a2: normals
+
+
+def test_knn_matches_numpy_bruteforce(ora):
+    g = synth.rng(26)
+    pts = g.uniform(-0.3, 0.3, (1200, 3)).astype(np.float32)
+    pts[100:120] = pts[0]  # exact ties
+    q = pts[::5]
+    for radius, k in [(0.1, 30), (0.05, 7), (0.5, 64)]:
+        idx, dd, cnt = ora.knn_hybrid(pts, q, radius, k)
+        for i in range(len(q)):
+            ri, rd = ind.knn_bruteforce_f32(pts, q[i], radius, k)
+            assert cnt[i] == len(ri)
+            assert np.array_equal(idx[i, : cnt[i]], ri) and np.array_equal(dd[i, : cnt[i]], rd)
+            assert np.all(idx[i, cnt[i]:] == -1)
+
+
+def test_jacobi_matches_numpy_eigh(ora):
+    g = synth.rng(27)
+    for _ in range(200):
+        M = g.standard_normal((3, 3))
+        C = M @ M.T * g.uniform(1e-6, 1.0)
+        ev, V = ora.jacobi_eig3(C)
+        ref = np.linalg.eigvalsh(C)
+        assert np.allclose(np.sort(ev), ref, rtol=1e-12, atol=1e-14 * ref.max())
+        assert np.allclose(C @ V, V * ev[None, :], atol=1e-12 * ref.max())
+        assert np.allclose(V.T @ V, np.eye(3), atol=1e-13)
+
+
+def test_normals_on_plane_are_exact(ora):
+    g = synth.rng(28)
+    pts = np.column_stack([g.uniform(-1, 1, 2000), g.uniform(-1, 1, 2000), np.full(2000, 0.25)]).astype(np.float32)
+    nrm = ora.estimate_normals(pts, 0.1, 30, viewpoint=(0.0, 0.0, 5.0))
+    assert np.array_equal(nrm, np.tile(np.array([0, 0, 1], np.float32), (2000, 1)))
+    nrm = ora.estimate_normals(pts, 0.1, 30, viewpoint=(0.0, 0.0, -5.0))
+    assert np.array_equal(nrm, np.tile(np.array([0, 0, -1], np.float32), (2000, 1)))
+
+
+def test_normals_on_sphere_are_radial_and_oriented(ora):
+    g = synth.rng(29)
+    v = g.standard_normal((20000, 3))  # ~50 points within 0.1, so the 30 nearest span a small cap
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    pts = v.astype(np.float32)
+    nrm = ora.estimate_normals(pts, 0.1, 30, viewpoint=(0.0, 0.0, 0.0))
+    cosang = np.abs(np.sum(nrm.astype(np.float64) * v, axis=1))
+    ang = np.arccos(np.clip(cosang, -1, 1))
+    # a plane fitted to a cap of angular radius 0.1 tilts by at most about half of it when the
+    # neighbours are lopsided; a wrong eigenvector would be off by ~90 degrees
+    assert np.all(ang < 0.05) and np.median(ang) < 1e-2
+    assert np.all(np.sum(nrm * (0 - pts), axis=1) >= 0)  # facing the centre viewpoint
+
+
+def test_normals_few_neighbours_default(ora):
+    pts = np.array([[0, 0, 0], [0.01, 0, 0], [5, 5, 5]], np.float32)
+    nrm = ora.estimate_normals(pts, 0.05, 30)
+    assert np.array_equal(nrm, np.tile(np.array([0, 0, 1], np.float32), (3, 1)))
+
+
+def test_normals_match_eigh_of_neighbour_covariance(ora):
+    """The normal is numpy.linalg.eigh's smallest eigenvector of the neighbourhood covariance."""
+    g = synth.rng(30)
+    pts = (g.uniform(-0.2, 0.2, (800, 3)) * np.array([1, 1, 0.2])).astype(np.float32)
+    radius, k = 0.1, 30
+    nrm, ev = ora.estimate_normals(pts, radius, k, viewpoint=(0.0, 0.0, 1.0), return_evals=True)
+    for i in range(0, 800, 13):
+        idx, _ = ind.knn_bruteforce_f32(pts, pts[i], radius, k)
+        X = pts[idx].astype(np.float64)
+        C = np.cov(X.T, bias=True)
+        w, V = np.linalg.eigh(C)
+        assert np.allclose(ev[i], w, rtol=1e-9, atol=1e-15)
+        if w[1] - w[0] > 1e-3 * w[2]:
+            cosang = abs(float(np.dot(nrm[i].astype(np.float64), V[:, 0])))
+            assert cosang > 1 - 2e-7  # FP32 storage of a unit vector
