@@ -1,0 +1,339 @@
+"""Benchmark: point-to-plane ICP on an RGB-D-frame-scale pair (one GB300 per rank).
+
+One step = the whole registration path on one pair of seeded synthetic clouds
+already resident in HBM: build the target grid, estimate target normals on the
+GPU (hybrid radius 0.05 m, 30 neighbours), 30 point-to-plane ICP iterations
+(max_correspondence_distance 0.05 m) and the final fitness / rmse evaluation.
+Metric: ICP point-pairs per second per iteration = N_source x iterations / step
+time.  L2 is flushed (a 512 MiB write) before every step, outside the timed
+events.  `e2e` repeats the measurement through the host-buffer entry point
+(o3g_register_point_to_plane_host) with page-locked inputs, so the host-to-device
+copies and the result read-back are inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (plain C, brute force, FP64 sums) on the
+host cores, on a bounded sample of the same workload.  Under torchrun every
+rank registers its own pair (independent problems, weak scaling, no data-path
+collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ICP point-pairs/s per iteration"
+UNIT = "point-pairs/s"
+NORMAL_RADIUS, NORMAL_MAX_NN = 0.05, 30
+WORKLOAD = ("RGB-D frame pair: seeded room (20 boxes, 10 spheres, 4 m), 640x480 PrimeSense ray-cast depth, "
+            "noise 0.001 z^2, 0.01 m voxel thinning; second frame moved 3 deg / 0.05 m; GPU normals "
+            "(radius 0.05, 30 NN); point-to-plane ICP max_corr_dist 0.05, 30 iterations")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = None
+        if shutil.which("nvidia-smi"):
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix="o3g_clocks_", suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_pair(rank: int):
+    from paper_1801_09847_gb300 import synth
+    return synth.room_frame_pair(seed=2 + rank)
+
+
+# ------------------------------------------------------------- our arm
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    from paper_1801_09847_gb300 import build, o3g
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pr = make_pair(rank)
+    ns, nt = len(pr.src), len(pr.tgt)
+    src = torch.from_numpy(pr.src).to(dev)
+    tgt = torch.from_numpy(pr.tgt).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    init = np.eye(4)
+
+    def step():
+        g = o3g.build_grid(tgt, pr.max_corr_dist)
+        g.estimate_normals(NORMAL_RADIUS, NORMAL_MAX_NN, out=False)
+        res = o3g.icp_point_to_plane_grid(g, src, init, pr.max_corr_dist, pr.max_iter)
+        g.free()
+        return res
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize()
+
+    def timed(fn, reads_kernels: bool):
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        total = 0.0
+        if reads_kernels:
+            o3g.timing_enable(True)
+            for k in (o3g.KERNEL_ICP_CORR, o3g.KERNEL_ICP_SOLVE, o3g.KERNEL_NORMALS, o3g.KERNEL_GRID):
+                o3g.timing_read(k, reset=True)
+        l0 = o3g.launch_count()
+        out = None
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        torch.cuda.synchronize()
+        launches = o3g.launch_count() - l0
+        kern = {}
+        if reads_kernels:
+            o3g.timing_enable(False)
+            for name, k in (("icp_corr", o3g.KERNEL_ICP_CORR), ("icp_solve", o3g.KERNEL_ICP_SOLVE),
+                            ("normals", o3g.KERNEL_NORMALS), ("grid", o3g.KERNEL_GRID)):
+                kern[name] = o3g.timing_read(k, reset=True)
+        if dist:
+            t = torch.tensor([total], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        return total, launches, kern, out
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    total_ms, launches, kern, res = timed(step, True)
+    clocks = sampler.stop() if sampler else None
+
+    # e2e: host buffers in page-locked memory, copies inside the timed region
+    src_h = torch.from_numpy(pr.src).pin_memory()
+    tgt_h = torch.from_numpy(pr.tgt).pin_memory()
+
+    def step_host():
+        return o3g.register_point_to_plane_host(src_h, tgt_h, None, init, pr.max_corr_dist, pr.max_iter,
+                                                normal_radius=NORMAL_RADIUS, normal_max_nn=NORMAL_MAX_NN)
+
+    for _ in range(max(1, args.warmup // 2)):
+        step_host()
+    e2e_ms, _, _, res_h = timed(step_host, False)
+
+    iters = res["iters"]
+    units_rank = ns * iters
+    ms_step = total_ms / args.steps
+    # weak scaling: every rank registers its own pair of the same size class
+    if dist:
+        u = torch.tensor([float(units_rank)], device=dev, dtype=torch.float64)
+        dist.all_reduce(u)
+        units = float(u.item())
+    else:
+        units = float(units_rank)
+    value = units / (ms_step / 1e3)
+    e2e_value = units / (e2e_ms / args.steps / 1e3)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(pr, budget_s=args.cpu_budget)
+
+    if rank == 0:
+        peak, which = peaks()
+        corr_ms, corr_n = kern["icp_corr"]
+        fitness = res["fitness"]
+        # algorithmic bytes of one correspondence + reduction launch: source xyz (12 B) for every
+        # point and matched target xyz + normal (24 B) per correspondence
+        alg_bytes = ns * (12.0 + 24.0 * fitness)
+        avg_s = corr_ms / max(corr_n, 1) / 1e3
+        achieved = alg_bytes / avg_s / 1e9 if avg_s > 0 else 0.0
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_source": ns, "n_target": nt, "iterations": iters,
+                       "max_corr_dist": pr.max_corr_dist, "normal_radius": NORMAL_RADIUS,
+                       "normal_max_nn": NORMAL_MAX_NN, "l2": "flushed (512 MiB write) before every step",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (ns + nt) * 12,
+                    "d2h_bytes_per_step": 16 * 8 + 8 + 8 + 4, "ms_per_step": e2e_ms / args.steps},
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_icp_corr",
+                         "peak_source": which, "launches_timed": corr_n,
+                         "avg_launch_us": avg_s * 1e6, "algorithmic_bytes_per_launch": alg_bytes},
+            "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
+            "result": {"fitness": fitness, "rmse": res["rmse"], "status": res["status"]},
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ CPU oracle
+
+
+def cpu_sample_run(pr, n_sample: int, threads: int):
+    """The oracle on a seeded source sample: normals on the full target, then ICP; returns (seconds, pairs)."""
+    import oracle
+    from paper_1801_09847_gb300 import synth
+    oracle.build()
+    g = synth.rng(99)
+    idx = np.sort(g.choice(len(pr.src), min(n_sample, len(pr.src)), replace=False))
+    src = np.ascontiguousarray(pr.src[idx])
+    t0 = time.perf_counter()
+    nrm = oracle.estimate_normals(pr.tgt, NORMAL_RADIUS, NORMAL_MAX_NN, threads=threads)
+    t1 = time.perf_counter()
+    res = oracle.icp_point_to_plane(src, pr.tgt, nrm, np.eye(4), pr.max_corr_dist, pr.max_iter, threads=threads)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1, len(src) * res["iters"]
+
+
+def cpu_baseline(pr, budget_s: float = 20.0):
+    import oracle
+    threads = oracle.default_threads()
+    n_sample = 4096
+    t_nrm, t_icp, pairs = cpu_sample_run(pr, n_sample, threads)
+    # the ICP part scales with the sample; the target normals are paid once per pair
+    per_pair_s = t_nrm + t_icp * len(pr.src) / n_sample
+    value = len(pr.src) * pr.max_iter / per_pair_s
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": (f"oracle normals on the full {len(pr.tgt)}-point target ({t_nrm:.2f} s) + oracle ICP on a "
+                       f"seeded {n_sample}-point source sample ({t_icp:.2f} s, {pr.max_iter} iterations), ICP time "
+                       f"scaled to the full {len(pr.src)}-point source")}
+
+
+def run_reference(args, ws, rank, local):
+    if rank != 0:
+        return
+    import oracle
+    threads = oracle.default_threads()
+    pr = make_pair(0)
+    n_sample = args.ref_sample
+    for _ in range(args.warmup):
+        cpu_sample_run(pr, min(n_sample, 256), threads)
+    times = []
+    pairs = 0
+    for _ in range(args.steps):
+        t_nrm, t_icp, p = cpu_sample_run(pr, n_sample, threads)
+        times.append(t_nrm + t_icp)
+        pairs += p
+    total = sum(times)
+    value = pairs / total
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "n_source": len(pr.src), "n_target": len(pr.tgt),
+                   "iterations": pr.max_iter, "parallelism": "CPU threads"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": (f"each step: oracle normals on the full {len(pr.tgt)}-point target + oracle ICP "
+                                    f"on a seeded {n_sample}-point source sample, {pr.max_iter} iterations")},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--ref-sample", type=int, default=2048)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank, local)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

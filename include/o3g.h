@@ -1,0 +1,213 @@
+/*
+ * o3g.h - C ABI of the GB300-native point-to-plane ICP library (libo3g.so).
+ *
+ * The library implements the local-refinement step of Open3D's pairwise
+ * registration workflow (arXiv 1801.09847, Sec. 3.3, registration_icp with
+ * TransformationEstimationPointToPlane) and the normal estimation that feeds it
+ * (Fig. 1 and Sec. 3.3, estimate_normals with KDTreeSearchParamHybrid), on one
+ * CUDA GPU.  The iteration is the Gauss-Newton step of Sec. 4, Eq. (1)-(2).
+ *
+ * Conventions shared by every entry point
+ *  - Return value: an o3g_status code.  Negative = error: outputs are left
+ *    untouched and o3g_last_error() describes the failure.  Positive = warning:
+ *    outputs are valid.  No C++ exception and no abort crosses this boundary.
+ *  - Point clouds are float32.  Point i of a cloud is (xyz[i*stride],
+ *    xyz[i*stride+1], xyz[i*stride+2]); stride >= 3 floats.  Device pointers
+ *    (prefix d_) are caller-owned, read-only unless documented as outputs, and
+ *    never freed by the library.  They must stay valid until the call returns
+ *    or, for asynchronous calls, until the stream has passed the work.
+ *  - Poses are 4x4 row-major float64 matrices in HOST memory that map source
+ *    coordinates into the target frame: q = T[0:3,0:3] p + T[0:3,3].
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls that return host-side results synchronise that stream
+ *    before returning; the others only enqueue work.
+ *  - The library allocates device memory from a private stream-ordered pool.
+ *    Handles (o3g_grid) are library-owned and released with o3g_free_grid.
+ *  - Non-finite input coordinates are rejected with O3G_ERR_NONFINITE.
+ *  - Thread safety: calls on different handles may run concurrently from
+ *    different host threads; a handle must not be used by two calls at once.
+ */
+#ifndef O3G_H
+#define O3G_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define O3G_API __attribute__((visibility("default")))
+#else
+#define O3G_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  O3G_OK = 0,
+  O3G_WARN_DEGENERATE = 1, /* some 6x6 pivot was frozen (unobservable DOF); pose still valid */
+  O3G_WARN_FEW_CORR = 2,   /* ICP stopped early: fewer than 6 correspondences */
+  O3G_ERR_ARG = -1,        /* invalid argument (null pointer, negative size, bad stride, ...) */
+  O3G_ERR_OOM = -2,        /* device allocation failed */
+  O3G_ERR_CUDA = -3,       /* a CUDA runtime call failed; see o3g_last_error() */
+  O3G_ERR_NONFINITE = -4,  /* a point coordinate or the pose is NaN or infinite */
+  O3G_ERR_TIMEOUT = -5     /* a bounded device-side wait gave up */
+} o3g_status;
+
+/* Largest max_nn accepted by the hybrid search and normal estimation. */
+#define O3G_MAX_NN 64
+
+/* Opaque uniform grid over one point cloud, resident in device memory. */
+typedef struct o3g_grid o3g_grid;
+
+/* Human-readable description of the last error on the calling host thread. */
+O3G_API const char* o3g_last_error(void);
+
+/* ABI version of this header (bumped on any signature change). */
+O3G_API int32_t o3g_abi_version(void);
+
+/*
+ * Builds the device uniform grid that replaces Open3D's kd-tree (Sec. 2: FLANN
+ * for nearest-neighbour search) for fixed-radius and hybrid queries.
+ *   d_xyz, n, stride : the cloud (device); n may be 0.
+ *   cell_size        : edge of a grid cell (> 0).  Any query radius works with
+ *                      any cell size; a cell near the typical query radius is
+ *                      fastest.  If the cloud's bounding box would need more
+ *                      than 32*n + 2^20 cells the library enlarges the cell.
+ *   out              : receives the handle.
+ * The grid copies the points (sorted by cell) and does not keep d_xyz.
+ * Synchronises `stream` once (to size the grid from the bounding box).
+ */
+O3G_API int32_t o3g_build_grid(const float* d_xyz, int64_t n, int32_t stride, float cell_size, void* stream,
+                       o3g_grid** out);
+
+/* Releases a grid (NULL is accepted).  Enqueued on the stream given at build. */
+O3G_API int32_t o3g_free_grid(o3g_grid* grid);
+
+/* Number of points and the cell size actually used. */
+O3G_API int32_t o3g_grid_info(const o3g_grid* grid, int64_t* n, float* cell_size);
+
+/*
+ * Attaches normals to a grid's points (Sec. 3.1: normals are valid only when
+ * they have as many records as the points -> n != grid's n gives O3G_ERR_ARG).
+ * d_nrm is read in the caller's point order and copied into the grid.
+ */
+O3G_API int32_t o3g_grid_set_normals(o3g_grid* grid, const float* d_nrm, int64_t n, int32_t stride, void* stream);
+
+/*
+ * Hybrid radius/kNN search (KDTreeSearchParamHybrid(radius, max_nn), Fig. 1):
+ * for each query, the at most max_nn grid points with
+ *   d2 = (dx*dx + dy*dy) + dz*dz <= fl(radius)*fl(radius)   (float32, each op rounded),
+ * ordered by (d2, point index); indices are the grid cloud's original indices.
+ *   d_idx [nq*max_nn] int32, -1 padded;  d_d2 [nq*max_nn] float32, 0 padded;
+ *   d_cnt [nq] int32.  1 <= max_nn <= O3G_MAX_NN.  Asynchronous.
+ */
+O3G_API int32_t o3g_knn_hybrid(const o3g_grid* grid, const float* d_qry, int64_t nq, int32_t stride, float radius,
+                       int32_t max_nn, int32_t* d_idx, float* d_d2, int32_t* d_cnt, void* stream);
+
+/*
+ * estimate_normals(pc, KDTreeSearchParamHybrid(radius, max_nn)) (Fig. 1,
+ * Sec. 3.3) for the grid's own points: the hybrid neighbourhood of each point
+ * (itself included), covariance of the neighbourhood about its mean divided by
+ * m, unit eigenvector of the smallest eigenvalue, turned so that
+ * n . (viewpoint - q) >= 0.  Fewer than 3 neighbours give (0, 0, 1).
+ *   viewpoint  : 3 floats in host memory (NULL = origin).
+ *   d_nrm_out  : n x nrm_stride floats (device) in the caller's point order, or
+ *                NULL to only keep them in the grid.
+ * The normals are also attached to the grid (as o3g_grid_set_normals would).
+ * Asynchronous.
+ */
+O3G_API int32_t o3g_estimate_normals(o3g_grid* grid, float radius, int32_t max_nn, const float* viewpoint,
+                             float* d_nrm_out, int32_t nrm_stride, void* stream);
+
+/*
+ * Correspondence step of registration_icp at a given pose (Sec. 3.3):
+ * p_i = R s_i + t in float32 with R, t rounded to nearest from T and each row
+ * evaluated as ((R0 sx + R1 sy) + R2 sz) + t, no fused multiply-add; then the
+ * target j minimising (d2(p_i, q_j), j) with d2 <= fl(max_corr_dist)^2.
+ *   d_corr [ns] int32 : original target index, or -1.   d_d2 [ns] float32 (0 if none).
+ * Asynchronous.
+ */
+O3G_API int32_t o3g_correspondences(const o3g_grid* tgt, const float* d_src, int64_t ns, int32_t stride,
+                            const double* T, float max_corr_dist, int32_t* d_corr, float* d_d2, void* stream);
+
+/*
+ * Gauss-Newton normal equations at a given pose (Sec. 4, Eq. 1-2):
+ * over the correspondences of o3g_correspondences, r_i = (p_i - q_i) . n_i,
+ * J_i = [p_i x n_i ; n_i] (target normals), and
+ *   out_A [36] = sum J J^T (row-major, symmetric),  out_b [6] = sum J r,
+ *   out_stats [3] = (sum r^2, sum d2, |C|).
+ * Per-correspondence arithmetic is float32 with compensated block sums; the
+ * cross-block sum is float64.  Requires normals on the target grid.  Synchronous.
+ */
+O3G_API int32_t o3g_normal_equations(const o3g_grid* tgt, const float* d_src, int64_t ns, int32_t stride, const double* T,
+                             float max_corr_dist, double* out_A, double* out_b, double* out_stats, void* stream);
+
+/*
+ * Point-to-plane ICP against a resident target grid that carries normals
+ * (registration_icp(source, target, max_correspondence_distance, init,
+ * TransformationEstimationPointToPlane()), Sec. 3.3).  Each iteration: the
+ * correspondence step, the normal equations, the LDL^T solve of
+ * (J^T J) xi = -J^T r (Eq. 2) with xi = (alpha, beta, gamma, tx, ty, tz), and
+ * T <- [Rz(gamma) Ry(beta) Rx(alpha), t; 0 1] T.  A pivot D_kk <= 1e-12 max_j A_jj
+ * freezes its unknown (status O3G_WARN_DEGENERATE).  Iteration stops after
+ * max_iter updates, when fewer than 6 correspondences remain
+ * (O3G_WARN_FEW_CORR, pose of the last update kept), or when
+ * max(|(alpha,beta,gamma)|, |t|) < eps after an update (eps <= 0: never).
+ * Results at the final pose: fitness = |C| / ns, rmse = sqrt(sum d2 / |C|)
+ * (0 when C is empty).  out_iters may be NULL.  All iteration state stays on
+ * the device; synchronous.
+ */
+O3G_API int32_t o3g_icp_point_to_plane_grid(const o3g_grid* tgt, const float* d_src, int64_t ns, int32_t stride,
+                                    const double* init_T, double max_corr_dist, int32_t max_iter, double eps,
+                                    double* out_T, double* out_fitness, double* out_rmse, int32_t* out_iters,
+                                    void* stream);
+
+/*
+ * One-shot form of the above on raw device clouds: builds a grid over the
+ * target (cell = max_corr_dist), attaches d_tgt_nrm (n_nrm must equal nt,
+ * Sec. 3.1), runs ICP with eps = 0 on the legacy default stream and frees the
+ * grid.
+ */
+O3G_API int32_t o3g_icp_point_to_plane(const float* d_src, int64_t ns, int32_t src_stride, const float* d_tgt, int64_t nt,
+                               int32_t tgt_stride, const float* d_tgt_nrm, int64_t n_nrm, int32_t nrm_stride,
+                               const double* init_T, double max_corr_dist, int32_t max_iter, double* out_T,
+                               double* out_fitness, double* out_rmse);
+
+/*
+ * The whole pairwise refinement from HOST buffers (the call a user with data in
+ * host memory makes): copies source and target to the device, builds the
+ * target grid (cell = max_corr_dist), attaches h_tgt_nrm or, if it is NULL,
+ * estimates target normals (normal_radius, normal_max_nn, viewpoint = origin),
+ * runs ICP and returns the results in host memory.  h_src, h_tgt and h_tgt_nrm
+ * are packed xyz (stride 3); page-locked buffers make the copies asynchronous.
+ */
+O3G_API int32_t o3g_register_point_to_plane_host(const float* h_src, int64_t ns, const float* h_tgt, int64_t nt,
+                                         const float* h_tgt_nrm, float normal_radius, int32_t normal_max_nn,
+                                         const double* init_T, double max_corr_dist, int32_t max_iter, double eps,
+                                         double* out_T, double* out_fitness, double* out_rmse, int32_t* out_iters,
+                                         void* stream);
+
+/*
+ * Instrumentation (no counterpart in the paper; used by benchmarks and tests).
+ * o3g_launch_count: kernels this library has launched since it was loaded.
+ * o3g_timing_enable(1): from then on, each launch of the kernels listed below
+ * is bracketed by CUDA events recorded on its launching stream.
+ * o3g_timing_read(kind, ...): waits for the recorded events, returns the summed
+ * device time in milliseconds and the number of launches timed, and (reset != 0)
+ * forgets them.  kind: O3G_KERNEL_ICP_CORR (per-iteration correspondence +
+ * reduction), O3G_KERNEL_ICP_SOLVE (per-iteration reduce + solve + update),
+ * O3G_KERNEL_NORMALS (normal estimation), O3G_KERNEL_GRID (one whole grid build).
+ */
+#define O3G_KERNEL_ICP_CORR 0
+#define O3G_KERNEL_ICP_SOLVE 1
+#define O3G_KERNEL_NORMALS 2
+#define O3G_KERNEL_GRID 3
+O3G_API int64_t o3g_launch_count(void);
+O3G_API int32_t o3g_timing_enable(int32_t on);
+O3G_API int32_t o3g_timing_read(int32_t kind, double* total_ms, int64_t* launches, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* O3G_H */

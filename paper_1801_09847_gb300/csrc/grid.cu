@@ -1,0 +1,616 @@
+// Uniform grid over a point cloud, built by a stable sort on the linear cell
+// index.  Replaces the kd-tree that Open3D uses for nearest-neighbour search
+// (Sec. 2: FLANN) with a layout suited to fixed-radius queries on the GPU:
+//   1. bounding box of the cell coordinates (one host round-trip, to size it);
+//   2. key = linear cell index over that box (z fastest), value = point index;
+//   3. stable LSD radix sort of (key, value), 8-bit digits;
+//   4. cell_start[c] = number of points with key < c (dense, cells + 1 entries);
+//   5. gather the points into sorted order as float4 (x, y, z, original index).
+// A query box then reads each (x, y) column of cells as ONE contiguous run of
+// the sorted points: [cell_start[col + z_lo], cell_start[col + z_hi + 1]).
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <new>
+
+#include "o3g_internal.cuh"
+
+namespace o3g {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// --------------------------------------------------------------- bbox
+
+__global__ void k_bbox_init(int* bb) {
+  if (threadIdx.x < 3) bb[threadIdx.x] = INT_MAX;
+  else if (threadIdx.x < 6) bb[threadIdx.x] = INT_MIN;
+  else if (threadIdx.x == 6) bb[6] = 0;
+}
+
+__global__ void __launch_bounds__(kThreads) k_bbox(const float* __restrict__ xyz, int n, int stride, float inv,
+                                                   int* __restrict__ bb) {
+  int mn0 = INT_MAX, mn1 = INT_MAX, mn2 = INT_MAX;
+  int mx0 = INT_MIN, mx1 = INT_MIN, mx2 = INT_MIN;
+  int bad = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float* p = xyz + static_cast<int64_t>(i) * stride;
+    float x = p[0], y = p[1], z = p[2];
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) {
+      bad = 1;
+      continue;
+    }
+    int cx = cell_coord(x, inv), cy = cell_coord(y, inv), cz = cell_coord(z, inv);
+    mn0 = min(mn0, cx);
+    mn1 = min(mn1, cy);
+    mn2 = min(mn2, cz);
+    mx0 = max(mx0, cx);
+    mx1 = max(mx1, cy);
+    mx2 = max(mx2, cz);
+  }
+  const unsigned full = 0xffffffffu;
+  mn0 = __reduce_min_sync(full, mn0);
+  mn1 = __reduce_min_sync(full, mn1);
+  mn2 = __reduce_min_sync(full, mn2);
+  mx0 = __reduce_max_sync(full, mx0);
+  mx1 = __reduce_max_sync(full, mx1);
+  mx2 = __reduce_max_sync(full, mx2);
+  bad = __reduce_or_sync(full, bad);
+  if ((threadIdx.x & 31) == 0) {
+    if (mn0 != INT_MAX) {
+      atomicMin(bb + 0, mn0);
+      atomicMin(bb + 1, mn1);
+      atomicMin(bb + 2, mn2);
+      atomicMax(bb + 3, mx0);
+      atomicMax(bb + 4, mx1);
+      atomicMax(bb + 5, mx2);
+    }
+    if (bad) atomicOr(bb + 6, 1);
+  }
+}
+
+// ---------------------------------------------------------------- keys
+
+__global__ void __launch_bounds__(kThreads) k_keys(const float* __restrict__ xyz, int n, int stride, float inv, int lx,
+                                                   int ly, int lz, uint32_t sy, uint32_t sz, uint32_t* __restrict__ keys,
+                                                   uint32_t* __restrict__ vals) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* p = xyz + static_cast<int64_t>(i) * stride;
+  uint32_t cx = static_cast<uint32_t>(cell_coord(p[0], inv) - lx);
+  uint32_t cy = static_cast<uint32_t>(cell_coord(p[1], inv) - ly);
+  uint32_t cz = static_cast<uint32_t>(cell_coord(p[2], inv) - lz);
+  keys[i] = (cx * sy + cy) * sz + cz;
+  vals[i] = static_cast<uint32_t>(i);
+}
+
+// -------------------------------------------------------- exclusive scan
+
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kThreads * kScanItems;
+
+// Exclusive scan of one value per thread across the block; *total = block sum.
+__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t warp_sums[kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) warp_sums[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < kThreads / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kThreads / 32) warp_sums[lane] = w;  // inclusive
+  }
+  __syncthreads();
+  uint32_t warp_off = warp == 0 ? 0 : warp_sums[warp - 1];
+  *total = warp_sums[kThreads / 32 - 1];
+  __syncthreads();
+  return warp_off + inc - v;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_reduce(const uint32_t* __restrict__ in, int64_t m,
+                                                          uint32_t* __restrict__ bsum) {
+  int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < m) s += in[base + k];
+  uint32_t total;
+  block_exclusive_scan(s, &total);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// Single block: in-place exclusive scan of nb block sums.
+__global__ void __launch_bounds__(kThreads) k_scan_top(uint32_t* __restrict__ bsum, int nb) {
+  uint32_t carry = 0;
+  for (int c0 = 0; c0 < nb; c0 += kScanTile) {
+    int base = c0 + threadIdx.x * kScanItems;
+    uint32_t v[kScanItems], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      v[k] = base + k < nb ? bsum[base + k] : 0;
+      s += v[k];
+    }
+    uint32_t total;
+    uint32_t off = block_exclusive_scan(s, &total) + carry;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (base + k < nb) bsum[base + k] = off;
+      off += v[k];
+    }
+    carry += total;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_down(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                        int64_t m, const uint32_t* __restrict__ bsum) {
+  int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
+  uint32_t v[kScanItems], s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = base + k < m ? in[base + k] : 0;
+    s += v[k];
+  }
+  uint32_t total;
+  uint32_t off = block_exclusive_scan(s, &total) + bsum[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < m) out[base + k] = off;
+    off += v[k];
+  }
+}
+
+// ---------------------------------------------------------- radix sort
+
+constexpr int kRsRounds = 8;
+constexpr int kRsTile = kThreads * kRsRounds;
+constexpr int kWarps = kThreads / 32;
+
+__global__ void __launch_bounds__(kThreads) k_rs_hist(const uint32_t* __restrict__ keys, int n, int shift,
+                                                      uint32_t* __restrict__ hist, int nblk) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  int base = blockIdx.x * kRsTile;
+#pragma unroll
+  for (int r = 0; r < kRsRounds; ++r) {
+    int i = base + r * kThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[static_cast<size_t>(threadIdx.x) * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter of one tile: elements keep their input order within a digit.
+// Rounds walk the tile in order; inside a round, warps in order; inside a warp,
+// lanes in order (rank among equal digits via __match_any_sync).
+__global__ void __launch_bounds__(kThreads) k_rs_scatter(const uint32_t* __restrict__ kin,
+                                                         const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+                                                         uint32_t* __restrict__ vout, int n, int shift,
+                                                         const uint32_t* __restrict__ offs, int nblk) {
+  __shared__ uint32_t base[256];
+  __shared__ uint32_t wcnt[kWarps][256];
+  __shared__ uint32_t total[256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  base[tid] = offs[static_cast<size_t>(tid) * nblk + blockIdx.x];
+  const int tile0 = blockIdx.x * kRsTile;
+  for (int r = 0; r < kRsRounds; ++r) {
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
+    __syncthreads();
+    int i = tile0 + r * kThreads + tid;
+    bool valid = i < n;
+    uint32_t k = valid ? kin[i] : 0u, v = valid ? vin[i] : 0u;
+    uint32_t d = (k >> shift) & 255u;
+    uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 256u);
+    uint32_t rank = __popc(peers & lt);
+    if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+    __syncthreads();
+    {
+      uint32_t run = 0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) {
+        uint32_t c = wcnt[w][tid];
+        wcnt[w][tid] = run;
+        run += c;
+      }
+      total[tid] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      uint32_t pos = base[d] + wcnt[warp][d] + rank;
+      kout[pos] = k;
+      vout[pos] = v;
+    }
+    __syncthreads();
+    base[tid] += total[tid];
+  }
+}
+
+// ------------------------------------------------------ cell table, gather
+
+__global__ void __launch_bounds__(kThreads) k_cell_start(const uint32_t* __restrict__ skeys, int n,
+                                                         uint32_t* __restrict__ cell_start, int64_t cells) {
+  for (int64_t c = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; c <= cells;
+       c += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int lo = 0, hi = n;  // first position with key >= c
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (static_cast<int64_t>(skeys[mid]) < c) lo = mid + 1;
+      else hi = mid;
+    }
+    cell_start[c] = static_cast<uint32_t>(lo);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_gather(const float* __restrict__ xyz, int n, int stride,
+                                                     const uint32_t* __restrict__ perm, float4* __restrict__ pts,
+                                                     int32_t* __restrict__ pos_of) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  uint32_t o = perm[k];
+  const float* p = xyz + static_cast<int64_t>(o) * stride;
+  pts[k] = make_float4(p[0], p[1], p[2], __int_as_float(static_cast<int>(o)));
+  pos_of[o] = k;
+}
+
+__global__ void __launch_bounds__(kThreads) k_set_normals(const float* __restrict__ nrm, int stride,
+                                                          const float4* __restrict__ pts, int n,
+                                                          float4* __restrict__ out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int o = __float_as_int(pts[k].w);
+  const float* q = nrm + static_cast<int64_t>(o) * stride;
+  out[k] = make_float4(q[0], q[1], q[2], 0.f);
+}
+
+inline int blocks_for(int64_t n, int per_block) {
+  int64_t b = (n + per_block - 1) / per_block;
+  return static_cast<int>(b < 1 ? 1 : b);
+}
+
+// ------------------------------------------ spatially coherent point order
+
+// Order-preserving map of a float to an int (for atomicMin / atomicMax).
+__device__ __forceinline__ int ordered_int(float f) {
+  const int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ordered_float(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+
+__global__ void k_fbox_init(int* aux) {
+  if (threadIdx.x < 3) aux[threadIdx.x] = INT_MAX;
+  else if (threadIdx.x < 6) aux[threadIdx.x] = INT_MIN;
+  else if (threadIdx.x == 6) aux[6] = 0;
+}
+
+__global__ void __launch_bounds__(kThreads) k_fbox(const float* __restrict__ xyz, int n, int stride,
+                                                   int* __restrict__ aux) {
+  int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
+  int bad = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float* p = xyz + static_cast<int64_t>(i) * stride;
+    const float v[3] = {p[0], p[1], p[2]};
+    if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) {
+      bad = 1;
+      continue;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      mn[a] = min(mn[a], ordered_int(v[a]));
+      mx[a] = max(mx[a], ordered_int(v[a]));
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    mn[a] = __reduce_min_sync(0xffffffffu, mn[a]);
+    mx[a] = __reduce_max_sync(0xffffffffu, mx[a]);
+  }
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (mn[a] != INT_MAX) atomicMin(aux + a, mn[a]);
+      if (mx[a] != INT_MIN) atomicMax(aux + 3 + a, mx[a]);
+    }
+    if (bad) atomicOr(aux + 6, 1);
+  }
+}
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+// 30-bit Morton code of the point quantised to 1024 steps per axis of the box.
+__global__ void __launch_bounds__(kThreads) k_morton(const float* __restrict__ xyz, int n, int stride,
+                                                     const int* __restrict__ aux, uint32_t* __restrict__ keys,
+                                                     uint32_t* __restrict__ vals) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* p = xyz + static_cast<int64_t>(i) * stride;
+  uint32_t q[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float lo = aux[a] == INT_MAX ? 0.f : ordered_float(aux[a]);
+    const float hi = aux[3 + a] == INT_MIN ? 0.f : ordered_float(aux[3 + a]);
+    const float ext = fmaxf(hi - lo, 1e-30f);
+    const float u = fminf(fmaxf((p[a] - lo) * (1023.0f / ext), 0.f), 1023.f);  // NaN -> 0
+    q[a] = static_cast<uint32_t>(u);
+  }
+  keys[i] = spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2);
+  vals[i] = static_cast<uint32_t>(i);
+}
+
+__global__ void __launch_bounds__(kThreads) k_gather4(const float* __restrict__ xyz, int n, int stride,
+                                                      const uint32_t* __restrict__ perm, float4* __restrict__ pts) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const uint32_t o = perm[k];
+  const float* p = xyz + static_cast<int64_t>(o) * stride;
+  pts[k] = make_float4(p[0], p[1], p[2], __int_as_float(static_cast<int>(o)));
+}
+
+}  // namespace
+
+int32_t sort_cloud(const float* d_xyz, int64_t n64, int32_t stride, cudaStream_t s, SortedCloud* out) {
+  const int n = static_cast<int>(n64);
+  O3G_TRY(out->buf.alloc(sizeof(float4) * (n > 0 ? n : 1)));
+  O3G_TRY(out->aux.alloc(8 * sizeof(int)));
+  out->pts = out->buf.as<float4>();
+  k_fbox_init<<<1, 32, 0, s>>>(out->aux.as<int>());
+  count_launch();
+  if (n == 0) return O3G_OK;
+  int nb = blocks_for(n, kThreads);
+  if (nb > kNumSMs * 8) nb = kNumSMs * 8;
+  k_fbox<<<nb, kThreads, 0, s>>>(d_xyz, n, stride, out->aux.as<int>());
+  DevBuf keys(s), vals(s), tk(s), tv(s);
+  O3G_TRY(keys.alloc(sizeof(uint32_t) * n));
+  O3G_TRY(vals.alloc(sizeof(uint32_t) * n));
+  O3G_TRY(tk.alloc(sizeof(uint32_t) * n));
+  O3G_TRY(tv.alloc(sizeof(uint32_t) * n));
+  k_morton<<<blocks_for(n, kThreads), kThreads, 0, s>>>(d_xyz, n, stride, out->aux.as<int>(), keys.as<uint32_t>(),
+                                                        vals.as<uint32_t>());
+  count_launch(2);
+  O3G_TRY(cudaGetLastError());
+  O3G_TRY_STATUS(radix_sort_pairs(keys.as<uint32_t>(), vals.as<uint32_t>(), tk.as<uint32_t>(), tv.as<uint32_t>(), n,
+                                  30, s));
+  k_gather4<<<blocks_for(n, kThreads), kThreads, 0, s>>>(d_xyz, n, stride, vals.as<uint32_t>(), out->pts);
+  count_launch();
+  O3G_TRY(cudaGetLastError());
+  return O3G_OK;
+}
+
+// Exclusive scan of m uint32 values (in may equal out).
+int32_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t m, cudaStream_t s) {
+  if (m <= 0) return O3G_OK;
+  int nb = blocks_for(m, kScanTile);
+  DevBuf bsum(s);
+  O3G_TRY(bsum.alloc(sizeof(uint32_t) * nb));
+  k_scan_reduce<<<nb, kThreads, 0, s>>>(in, m, bsum.as<uint32_t>());
+  k_scan_top<<<1, kThreads, 0, s>>>(bsum.as<uint32_t>(), nb);
+  k_scan_down<<<nb, kThreads, 0, s>>>(in, out, m, bsum.as<uint32_t>());
+  count_launch(3);
+  O3G_TRY(cudaGetLastError());
+  return O3G_OK;
+}
+
+// Stable sort of (keys, vals) by the low `bits` bits of the keys.  The sorted
+// pairs end in (keys, vals); tmp_k/tmp_v are scratch of the same size.
+int32_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* tmp_k, uint32_t* tmp_v, int n, int bits,
+                         cudaStream_t s) {
+  if (n <= 1 || bits <= 0) return O3G_OK;
+  int nblk = blocks_for(n, kRsTile);
+  DevBuf hist(s);
+  O3G_TRY(hist.alloc(sizeof(uint32_t) * 256 * static_cast<size_t>(nblk)));
+  uint32_t *ka = keys, *va = vals, *kb = tmp_k, *vb = tmp_v;
+  int passes = (bits + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    int shift = 8 * p;
+    k_rs_hist<<<nblk, kThreads, 0, s>>>(ka, n, shift, hist.as<uint32_t>(), nblk);
+    O3G_TRY_STATUS(exclusive_scan_u32(hist.as<uint32_t>(), hist.as<uint32_t>(), 256LL * nblk, s));
+    k_rs_scatter<<<nblk, kThreads, 0, s>>>(ka, va, kb, vb, n, shift, hist.as<uint32_t>(), nblk);
+    count_launch(2);
+    O3G_TRY(cudaGetLastError());
+    uint32_t* t = ka;
+    ka = kb;
+    kb = t;
+    t = va;
+    va = vb;
+    vb = t;
+  }
+  if (ka != keys) {
+    O3G_TRY(cudaMemcpyAsync(keys, ka, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    O3G_TRY(cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+  }
+  return O3G_OK;
+}
+
+static void release(o3g_grid* g) {
+  dfree(g->pts, g->stream);
+  dfree(g->nrm, g->stream);
+  dfree(g->cell_start, g->stream);
+  dfree(g->pos_of, g->stream);
+  g->pts = nullptr;
+  g->nrm = nullptr;
+  g->cell_start = nullptr;
+  g->pos_of = nullptr;
+}
+
+static int32_t build_impl(const float* d_xyz, int64_t n64, int stride, float cell, cudaStream_t s, o3g_grid* g) {
+  const int n = static_cast<int>(n64);
+  g->n = n64;
+  g->stream = s;
+  if (n == 0) {
+    g->cell = cell;
+    g->inv_cell = 1.0f / cell;
+    g->cells = 1;
+    O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->cell_start), 2 * sizeof(uint32_t), s));
+    O3G_TRY(cudaMemsetAsync(g->cell_start, 0, 2 * sizeof(uint32_t), s));
+    O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->pts), sizeof(float4), s));
+    O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->nrm), sizeof(float4), s));
+    O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->pos_of), sizeof(int32_t), s));
+    return O3G_OK;
+  }
+  // 1. bounding box; enlarge the cell while the dense table would be too big.
+  DevBuf bb(s);
+  O3G_TRY(bb.alloc(8 * sizeof(int)));
+  const int64_t cap = std::min<int64_t>(32LL * n + (1LL << 20), (1LL << 31) - 2);
+  int h[7];
+  int64_t span[3], cells = 0;
+  float inv = 0.f;
+  for (int attempt = 0;; ++attempt) {
+    inv = 1.0f / cell;
+    if (!(inv > 0.f) || !std::isfinite(inv)) {
+      set_error("o3g_build_grid: cell size %g gives no usable grid", static_cast<double>(cell));
+      return O3G_ERR_ARG;
+    }
+    k_bbox_init<<<1, 32, 0, s>>>(bb.as<int>());
+    int nb = blocks_for(n, kThreads);
+    if (nb > kNumSMs * 8) nb = kNumSMs * 8;
+    k_bbox<<<nb, kThreads, 0, s>>>(d_xyz, n, stride, inv, bb.as<int>());
+    count_launch(2);
+    O3G_TRY(cudaGetLastError());
+    O3G_TRY(cudaMemcpyAsync(h, bb.p, 7 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    O3G_TRY(cudaStreamSynchronize(s));
+    if (h[6]) {
+      set_error("o3g_build_grid: non-finite point coordinate");
+      return O3G_ERR_NONFINITE;
+    }
+    cells = 1;
+    for (int a = 0; a < 3; ++a) {
+      span[a] = static_cast<int64_t>(h[3 + a]) - h[a] + 1;
+      cells *= span[a];
+    }
+    if (cells <= cap) break;
+    if (attempt >= 24) {
+      set_error("o3g_build_grid: could not bound the grid size");
+      return O3G_ERR_ARG;
+    }
+    cell = static_cast<float>(cell * std::cbrt(static_cast<double>(cells) / static_cast<double>(cap)) * 1.05);
+  }
+  g->cell = cell;
+  g->inv_cell = inv;
+  for (int a = 0; a < 3; ++a) {
+    g->lo[a] = h[a];
+    g->span[a] = static_cast<int>(span[a]);
+  }
+  g->cells = cells;
+
+  // 2-3. keys and stable sort
+  DevBuf keys(s), vals(s), tk(s), tv(s);
+  O3G_TRY(keys.alloc(sizeof(uint32_t) * n));
+  O3G_TRY(vals.alloc(sizeof(uint32_t) * n));
+  O3G_TRY(tk.alloc(sizeof(uint32_t) * n));
+  O3G_TRY(tv.alloc(sizeof(uint32_t) * n));
+  k_keys<<<blocks_for(n, kThreads), kThreads, 0, s>>>(d_xyz, n, stride, inv, h[0], h[1], h[2],
+                                                      static_cast<uint32_t>(span[1]), static_cast<uint32_t>(span[2]),
+                                                      keys.as<uint32_t>(), vals.as<uint32_t>());
+  count_launch();
+  O3G_TRY(cudaGetLastError());
+  int bits = 0;
+  while (bits < 32 && (static_cast<uint64_t>(cells - 1) >> bits) != 0) ++bits;
+  O3G_TRY_STATUS(radix_sort_pairs(keys.as<uint32_t>(), vals.as<uint32_t>(), tk.as<uint32_t>(), tv.as<uint32_t>(), n,
+                                  bits, s));
+
+  // 4-5. cell table and sorted points
+  O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->cell_start), sizeof(uint32_t) * (cells + 1), s));
+  O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->pts), sizeof(float4) * n, s));
+  O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->nrm), sizeof(float4) * n, s));
+  O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->pos_of), sizeof(int32_t) * n, s));
+  int nbc = blocks_for(cells + 1, kThreads);
+  if (nbc > kNumSMs * 16) nbc = kNumSMs * 16;
+  k_cell_start<<<nbc, kThreads, 0, s>>>(keys.as<uint32_t>(), n, g->cell_start, cells);
+  k_gather<<<blocks_for(n, kThreads), kThreads, 0, s>>>(d_xyz, n, stride, vals.as<uint32_t>(), g->pts, g->pos_of);
+  count_launch(2);
+  O3G_TRY(cudaGetLastError());
+  return O3G_OK;
+}
+
+}  // namespace o3g
+
+using namespace o3g;
+
+extern "C" int32_t o3g_build_grid(const float* d_xyz, int64_t n, int32_t stride, float cell_size, void* stream,
+                                  o3g_grid** out) {
+  if (!out) {
+    set_error("o3g_build_grid: out is null");
+    return O3G_ERR_ARG;
+  }
+  *out = nullptr;
+  if (n < 0 || n > INT32_MAX - kRsTile || (n > 0 && !d_xyz) || stride < 3 || !(cell_size > 0.f) ||
+      !std::isfinite(cell_size)) {
+    set_error("o3g_build_grid: invalid argument (n=%lld stride=%d cell=%g)", static_cast<long long>(n), stride,
+              static_cast<double>(cell_size));
+    return O3G_ERR_ARG;
+  }
+  o3g_grid* g = new (std::nothrow) o3g_grid();
+  if (!g) {
+    set_error("o3g_build_grid: host allocation failed");
+    return O3G_ERR_OOM;
+  }
+  int32_t st;
+  {
+    TimedRegion tr(O3G_KERNEL_GRID, static_cast<cudaStream_t>(stream));
+    st = build_impl(d_xyz, n, stride, cell_size, static_cast<cudaStream_t>(stream), g);
+  }
+  if (st < 0) {
+    release(g);
+    delete g;
+    return st;
+  }
+  *out = g;
+  return O3G_OK;
+}
+
+extern "C" int32_t o3g_free_grid(o3g_grid* g) {
+  if (!g) return O3G_OK;
+  release(g);
+  delete g;
+  return O3G_OK;
+}
+
+extern "C" int32_t o3g_grid_info(const o3g_grid* g, int64_t* n, float* cell_size) {
+  if (!g) {
+    set_error("o3g_grid_info: grid is null");
+    return O3G_ERR_ARG;
+  }
+  if (n) *n = g->n;
+  if (cell_size) *cell_size = g->cell;
+  return O3G_OK;
+}
+
+extern "C" int32_t o3g_grid_set_normals(o3g_grid* g, const float* d_nrm, int64_t n, int32_t stride, void* stream) {
+  if (!g || (n > 0 && !d_nrm) || stride < 3) {
+    set_error("o3g_grid_set_normals: invalid argument");
+    return O3G_ERR_ARG;
+  }
+  if (n != g->n) {
+    set_error("o3g_grid_set_normals: %lld normals for %lld points (normals must match the points one to one)",
+              static_cast<long long>(n), static_cast<long long>(g->n));
+    return O3G_ERR_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n > 0) {
+    k_set_normals<<<blocks_for(n, kThreads), kThreads, 0, s>>>(d_nrm, stride, g->pts, static_cast<int>(n), g->nrm);
+    count_launch();
+    O3G_TRY(cudaGetLastError());
+  }
+  g->has_normals = true;
+  return O3G_OK;
+}

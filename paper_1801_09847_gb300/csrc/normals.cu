@@ -1,0 +1,474 @@
+// Hybrid kNN search and normal estimation on the GPU:
+// estimate_normals(pc, KDTreeSearchParamHybrid(radius, max_nn)) of the Open3D
+// paper (Fig. 1, Sec. 3.3), parallel across data samples (Sec. 4).
+//
+// Per point: the at most max_nn grid points with float32 d2 <= fl(radius)^2 in
+// (d2, original index) order; the covariance of the neighbourhood about its mean
+// (float32, offsets taken from the query point first); its smallest-eigenvalue
+// eigenvector by cyclic Jacobi rotations; orientation toward the viewpoint.
+// max_nn <= 32 (the paper's 30 included) runs one warp per point (coalesced
+// candidate loads, bitonic top-k across the lanes); larger max_nn runs one
+// thread per point with an insertion-sorted list in local memory.
+#include <cmath>
+
+#include "o3g_internal.cuh"
+
+namespace o3g {
+
+namespace {
+
+constexpr int kThreads = 128;
+
+// Inserts the grid points within r of q into keys/pos (ascending 64-bit keys
+// (d2 bits << 32 | original index)); returns how many were kept (<= max_nn).
+template <int KMAX>
+__device__ int knn_select(const GridView& g, float qx, float qy, float qz, float r, int max_nn, uint64_t* keys,
+                          int* pos) {
+  const float r2 = __fmul_rn(r, r);
+  int ax, bx, ay, by, az, bz;
+  axis_range(qx, r, g.inv_cell, g.lo_x, g.sx, ax, bx);
+  axis_range(qy, r, g.inv_cell, g.lo_y, g.sy, ay, by);
+  axis_range(qz, r, g.inv_cell, g.lo_z, g.sz, az, bz);
+  int m = 0;
+  if (az > bz) return 0;
+  for (int x = ax; x <= bx; ++x) {
+    for (int y = ay; y <= by; ++y) {
+      const int col = (x * g.sy + y) * g.sz;
+      const uint32_t beg = g.cell_start[col + az], end = g.cell_start[col + bz + 1];
+      for (uint32_t k = beg; k < end; ++k) {
+        const float4 q = g.pts[k];
+        const float d2 = dist2_rn(qx, qy, qz, q);
+        if (!(d2 <= r2)) continue;
+        const uint64_t key = (static_cast<uint64_t>(__float_as_uint(d2)) << 32) |
+                             static_cast<uint32_t>(__float_as_int(q.w));
+        if (m == max_nn && key >= keys[m - 1]) continue;
+        int j = m < max_nn ? m++ : m - 1;
+        while (j > 0 && keys[j - 1] > key) {
+          keys[j] = keys[j - 1];
+          pos[j] = pos[j - 1];
+          --j;
+        }
+        keys[j] = key;
+        pos[j] = static_cast<int>(k);
+      }
+    }
+  }
+  return m;
+}
+
+// One Jacobi rotation in the (p, q) plane of the symmetric a (row-major 3x3),
+// accumulated into V, chosen so that the new a_pq is zero.
+template <int P, int Q>
+__device__ __forceinline__ void jacobi_rotate(float a[3][3], float V[3][3]) {
+  const float apq = a[P][Q];
+  if (apq == 0.f) return;
+  const float theta = (a[Q][Q] - a[P][P]) / (2.f * apq);
+  const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+  const float c = rsqrtf(t * t + 1.f);
+  const float s = t * c;
+  constexpr int R = 3 - P - Q;
+  const float arp = a[R][P], arq = a[R][Q];
+  a[P][P] -= t * apq;
+  a[Q][Q] += t * apq;
+  a[P][Q] = a[Q][P] = 0.f;
+  a[R][P] = a[P][R] = c * arp - s * arq;
+  a[R][Q] = a[Q][R] = s * arp + c * arq;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float vp = V[k][P], vq = V[k][Q];
+    V[k][P] = c * vp - s * vq;
+    V[k][Q] = s * vp + c * vq;
+  }
+}
+
+// Unit eigenvector of the smallest eigenvalue of the symmetric a.
+__device__ float3 smallest_eigvec(float a[3][3]) {
+  float V[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
+  for (int sweep = 0; sweep < 10; ++sweep) {
+    const float off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+    const float dg = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+    if (!(off > 1e-14f * dg)) break;
+    jacobi_rotate<0, 1>(a, V);
+    jacobi_rotate<0, 2>(a, V);
+    jacobi_rotate<1, 2>(a, V);
+  }
+  int k = 0;
+  if (a[1][1] < a[k][k]) k = 1;
+  if (a[2][2] < a[k][k]) k = 2;
+  float3 n = make_float3(V[0][k], V[1][k], V[2][k]);
+  const float inv = rsqrtf(n.x * n.x + n.y * n.y + n.z * n.z);
+  n.x *= inv;
+  n.y *= inv;
+  n.z *= inv;
+  return n;
+}
+
+// Unit eigenvector of the smallest eigenvalue of the symmetric a, closed form:
+// the eigenvalues of a 3x3 symmetric matrix from its characteristic cubic in
+// trigonometric form (lambda = m + 2 s cos(phi + 2 pi k / 3) with m = tr/3,
+// s^2 = |a - m I|_F^2 / 6, cos(3 phi) = det((a - m I) / s) / 2), then the null
+// vector of a - lambda_min I as the largest cross product of two of its rows.
+// When the smallest eigenvalue is (nearly) repeated, any unit vector orthogonal
+// to the remaining direction is a smallest eigenvector; one such is returned.
+__device__ float3 smallest_eigvec_closed(const float a[3][3]) {
+  const float m = (a[0][0] + a[1][1] + a[2][2]) * (1.f / 3.f);
+  const float b00 = a[0][0] - m, b11 = a[1][1] - m, b22 = a[2][2] - m;
+  const float b01 = a[0][1], b02 = a[0][2], b12 = a[1][2];
+  const float off = b01 * b01 + b02 * b02 + b12 * b12;
+  const float s2 = (b00 * b00 + b11 * b11 + b22 * b22 + 2.f * off) * (1.f / 6.f);
+  if (!(s2 > 0.f)) return make_float3(0.f, 0.f, 1.f);  // a = m I: every direction is an eigenvector
+  const float s = sqrtf(s2);
+  const float is = 1.f / s;
+  const float c00 = b00 * is, c11 = b11 * is, c22 = b22 * is, c01 = b01 * is, c02 = b02 * is, c12 = b12 * is;
+  const float det = c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) + c02 * (c01 * c12 - c11 * c02);
+  const float h = fminf(fmaxf(0.5f * det, -1.f), 1.f);
+  const float phi = acosf(h) * (1.f / 3.f);
+  const float lmin = m + 2.f * s * cosf(phi + 2.0943951023931957f);  // + 2 pi / 3: the smallest root
+  const float3 r0 = make_float3(a[0][0] - lmin, a[0][1], a[0][2]);
+  const float3 r1 = make_float3(a[1][0], a[1][1] - lmin, a[1][2]);
+  const float3 r2 = make_float3(a[2][0], a[2][1], a[2][2] - lmin);
+  auto cross = [](float3 u, float3 v) {
+    return make_float3(u.y * v.z - u.z * v.y, u.z * v.x - u.x * v.z, u.x * v.y - u.y * v.x);
+  };
+  auto dot = [](float3 u, float3 v) { return u.x * v.x + u.y * v.y + u.z * v.z; };
+  const float3 x01 = cross(r0, r1), x02 = cross(r0, r2), x12 = cross(r1, r2);
+  const float d01 = dot(x01, x01), d02 = dot(x02, x02), d12 = dot(x12, x12);
+  float3 n = x01;
+  float dn = d01;
+  if (d02 > dn) { n = x02; dn = d02; }
+  if (d12 > dn) { n = x12; dn = d12; }
+  const float rr = fmaxf(fmaxf(dot(r0, r0), dot(r1, r1)), dot(r2, r2));
+  if (!(dn > 1e-12f * rr * rr)) {
+    // rank <= 1: take the largest row and any direction orthogonal to it
+    float3 r = r0;
+    if (dot(r1, r1) > dot(r, r)) r = r1;
+    if (dot(r2, r2) > dot(r, r)) r = r2;
+    const float ax = fabsf(r.x), ay = fabsf(r.y), az = fabsf(r.z);
+    const float3 e = (ax <= ay && ax <= az) ? make_float3(1.f, 0.f, 0.f)
+                     : (ay <= az)           ? make_float3(0.f, 1.f, 0.f)
+                                            : make_float3(0.f, 0.f, 1.f);
+    n = cross(r, e);
+    dn = dot(n, n);
+    if (!(dn > 0.f)) return make_float3(0.f, 0.f, 1.f);
+  }
+  const float inv = rsqrtf(dn);
+  return make_float3(n.x * inv, n.y * inv, n.z * inv);
+}
+
+// ---------------------------------------------------------------------------
+// Warp-cooperative hybrid search (max_nn <= 32): one warp per query.  Lanes
+// load consecutive points of a cell column (coalesced), keep those within the
+// radius and below the current k-th key, compact them into a 64-entry staging
+// buffer in shared memory, and whenever 32 are staged sort them with a bitonic
+// network across the lanes and merge them into the running list (lane j holds
+// the j-th smallest key).  Keys are (d2 bits << 32 | original index), so the
+// order is (d2, index) and the result is the exact set the definition gives.
+constexpr uint64_t kNoKey = ~0ull;
+
+__device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
+  return __shfl_xor_sync(0xffffffffu, v, m);
+}
+
+// Ascending bitonic sort of one key per lane.
+__device__ __forceinline__ uint64_t warp_sort32(uint64_t v, int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const uint64_t o = shfl_xor64(v, j);
+      const bool up = (lane & k) == 0;
+      const bool low = (lane & j) == 0;
+      v = (low == up) ? (v < o ? v : o) : (v < o ? o : v);
+    }
+  }
+  return v;
+}
+
+// list (ascending) <- the 32 smallest of list and batch (ascending).
+__device__ __forceinline__ uint64_t warp_merge32(uint64_t list, uint64_t batch, int lane) {
+  const uint64_t rev = __shfl_sync(0xffffffffu, batch, 31 - lane);
+  uint64_t v = list < rev ? list : rev;  // bitonic
+#pragma unroll
+  for (int j = 16; j > 0; j >>= 1) {
+    const uint64_t o = shfl_xor64(v, j);
+    v = ((lane & j) == 0) ? (v < o ? v : o) : (v < o ? o : v);
+  }
+  return v;
+}
+
+// Returns lane `lane`'s entry of the sorted list of the <= max_nn nearest keys.
+__device__ uint64_t warp_knn(const GridView& g, float qx, float qy, float qz, float r, int max_nn, uint64_t* stage) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  const float r2 = __fmul_rn(r, r);
+  int ax, bx, ay, by, az, bz;
+  axis_range(qx, r, g.inv_cell, g.lo_x, g.sx, ax, bx);
+  axis_range(qy, r, g.inv_cell, g.lo_y, g.sy, ay, by);
+  axis_range(qz, r, g.inv_cell, g.lo_z, g.sz, az, bz);
+  uint64_t list = kNoKey;
+  uint64_t thr = kNoKey;  // current max_nn-th key (keys must be < thr to matter)
+  int staged = 0;
+  if (ax > bx || ay > by || az > bz) return list;
+  for (int x = ax; x <= bx; ++x) {
+    for (int y = ay; y <= by; ++y) {
+      const int col = (x * g.sy + y) * g.sz;
+      const uint32_t beg = g.cell_start[col + az], end = g.cell_start[col + bz + 1];
+      for (uint32_t k0 = beg; k0 < end; k0 += 32) {
+        const uint32_t k = k0 + lane;
+        uint64_t key = kNoKey;
+        if (k < end) {
+          const float4 q = g.pts[k];
+          const float d2 = dist2_rn(qx, qy, qz, q);
+          if (d2 <= r2)
+            key = (static_cast<uint64_t>(__float_as_uint(d2)) << 32) | static_cast<uint32_t>(__float_as_int(q.w));
+        }
+        const bool keep = key < thr;
+        const uint32_t mask = __ballot_sync(0xffffffffu, keep);
+        if (mask == 0u) continue;
+        if (keep) stage[staged + __popc(mask & lt)] = key;
+        staged += __popc(mask);
+        __syncwarp();
+        if (staged >= 32) {
+          const uint64_t batch = warp_sort32(stage[lane], lane);
+          list = warp_merge32(list, batch, lane);
+          thr = __shfl_sync(0xffffffffu, list, max_nn - 1);
+          __syncwarp();
+          const int rest = staged - 32;
+          const uint64_t carry = lane < rest ? stage[32 + lane] : kNoKey;
+          __syncwarp();
+          if (lane < rest) stage[lane] = carry;
+          staged = rest;
+          __syncwarp();
+        }
+      }
+    }
+  }
+  if (staged > 0) {
+    const uint64_t batch = warp_sort32(lane < staged ? stage[lane] : kNoKey, lane);
+    list = warp_merge32(list, batch, lane);
+    __syncwarp();
+  }
+  return lane < max_nn ? list : kNoKey;
+}
+
+constexpr int kWarpsPerBlock = kThreads / 32;
+
+// Warp-sum of a float (fixed shuffle tree; every lane gets the total).
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(kThreads) k_normals_warp(GridView g, const int32_t* __restrict__ pos_of,
+                                                           float radius, int max_nn, float vx, float vy, float vz,
+                                                           float4* __restrict__ nrm_sorted, float* __restrict__ out,
+                                                           int out_stride) {
+  __shared__ uint64_t stage_all[kWarpsPerBlock][64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * kWarpsPerBlock + warp;
+  if (k >= g.n) return;
+  const float4 q = g.pts[k];
+  const uint64_t key = warp_knn(g, q.x, q.y, q.z, radius, max_nn, stage_all[warp]);
+  const bool have = key != kNoKey;
+  const int m = __popc(__ballot_sync(0xffffffffu, have));
+  float3 n = make_float3(0.f, 0.f, 1.f);
+  if (m >= 3) {
+    float ox = 0.f, oy = 0.f, oz = 0.f;
+    if (have) {
+      const float4 p = g.pts[pos_of[static_cast<uint32_t>(key & 0xffffffffu)]];
+      ox = p.x - q.x;
+      oy = p.y - q.y;
+      oz = p.z - q.z;
+    }
+    const float inv_m = 1.f / static_cast<float>(m);
+    const float mx = warp_sum(ox) * inv_m, my = warp_sum(oy) * inv_m, mz = warp_sum(oz) * inv_m;
+    const float dx = have ? ox - mx : 0.f, dy = have ? oy - my : 0.f, dz = have ? oz - mz : 0.f;
+    float a[3][3];
+    a[0][0] = warp_sum(dx * dx) * inv_m;
+    a[0][1] = a[1][0] = warp_sum(dx * dy) * inv_m;
+    a[0][2] = a[2][0] = warp_sum(dx * dz) * inv_m;
+    a[1][1] = warp_sum(dy * dy) * inv_m;
+    a[1][2] = a[2][1] = warp_sum(dy * dz) * inv_m;
+    a[2][2] = warp_sum(dz * dz) * inv_m;
+    if (lane != 0) return;
+    n = smallest_eigvec_closed(a);
+    const float facing = n.x * (vx - q.x) + n.y * (vy - q.y) + n.z * (vz - q.z);
+    if (facing < 0.f) {
+      n.x = -n.x;
+      n.y = -n.y;
+      n.z = -n.z;
+    }
+  } else if (lane != 0) {
+    return;
+  }
+  nrm_sorted[k] = make_float4(n.x, n.y, n.z, 0.f);
+  if (out) {
+    float* o = out + static_cast<int64_t>(__float_as_int(q.w)) * out_stride;
+    o[0] = n.x;
+    o[1] = n.y;
+    o[2] = n.z;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_knn_warp(GridView g, const float* __restrict__ qry, int nq, int stride,
+                                                       float radius, int max_nn, int32_t* __restrict__ idx,
+                                                       float* __restrict__ dd, int32_t* __restrict__ cnt) {
+  __shared__ uint64_t stage_all[kWarpsPerBlock][64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kWarpsPerBlock + warp;
+  if (i >= nq) return;
+  const float* q = qry + static_cast<int64_t>(i) * stride;
+  const uint64_t key = warp_knn(g, q[0], q[1], q[2], radius, max_nn, stage_all[warp]);
+  const bool have = key != kNoKey;
+  const int m = __popc(__ballot_sync(0xffffffffu, have));
+  if (lane < max_nn) {
+    idx[static_cast<int64_t>(i) * max_nn + lane] = have ? static_cast<int32_t>(key & 0xffffffffu) : -1;
+    dd[static_cast<int64_t>(i) * max_nn + lane] = have ? __uint_as_float(static_cast<uint32_t>(key >> 32)) : 0.f;
+  }
+  if (lane == 0) cnt[i] = m;
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(kThreads) k_normals(GridView g, float radius, int max_nn, float vx, float vy,
+                                                      float vz, float4* __restrict__ nrm_sorted,
+                                                      float* __restrict__ out, int out_stride) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= g.n) return;
+  uint64_t keys[KMAX];
+  int pos[KMAX];
+  const float4 q = g.pts[k];
+  const int m = knn_select<KMAX>(g, q.x, q.y, q.z, radius, max_nn, keys, pos);
+  float3 n = make_float3(0.f, 0.f, 1.f);
+  if (m >= 3) {
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    for (int j = 0; j < m; ++j) {
+      const float4 p = g.pts[pos[j]];
+      sx += p.x - q.x;
+      sy += p.y - q.y;
+      sz += p.z - q.z;
+    }
+    const float inv_m = 1.f / static_cast<float>(m);
+    const float mx = sx * inv_m, my = sy * inv_m, mz = sz * inv_m;
+    float c00 = 0.f, c01 = 0.f, c02 = 0.f, c11 = 0.f, c12 = 0.f, c22 = 0.f;
+    for (int j = 0; j < m; ++j) {
+      const float4 p = g.pts[pos[j]];
+      const float dx = (p.x - q.x) - mx, dy = (p.y - q.y) - my, dz = (p.z - q.z) - mz;
+      c00 += dx * dx;
+      c01 += dx * dy;
+      c02 += dx * dz;
+      c11 += dy * dy;
+      c12 += dy * dz;
+      c22 += dz * dz;
+    }
+    float a[3][3] = {{c00 * inv_m, c01 * inv_m, c02 * inv_m},
+                     {c01 * inv_m, c11 * inv_m, c12 * inv_m},
+                     {c02 * inv_m, c12 * inv_m, c22 * inv_m}};
+    n = smallest_eigvec(a);
+    const float facing = n.x * (vx - q.x) + n.y * (vy - q.y) + n.z * (vz - q.z);
+    if (facing < 0.f) {
+      n.x = -n.x;
+      n.y = -n.y;
+      n.z = -n.z;
+    }
+  }
+  nrm_sorted[k] = make_float4(n.x, n.y, n.z, 0.f);
+  if (out) {
+    float* o = out + static_cast<int64_t>(__float_as_int(q.w)) * out_stride;
+    o[0] = n.x;
+    o[1] = n.y;
+    o[2] = n.z;
+  }
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(kThreads) k_knn(GridView g, const float* __restrict__ qry, int nq, int stride,
+                                                  float radius, int max_nn, int32_t* __restrict__ idx,
+                                                  float* __restrict__ dd, int32_t* __restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  uint64_t keys[KMAX];
+  int pos[KMAX];
+  const float* q = qry + static_cast<int64_t>(i) * stride;
+  const int m = knn_select<KMAX>(g, q[0], q[1], q[2], radius, max_nn, keys, pos);
+  int32_t* oi = idx + static_cast<int64_t>(i) * max_nn;
+  float* od = dd + static_cast<int64_t>(i) * max_nn;
+  for (int j = 0; j < max_nn; ++j) {
+    oi[j] = j < m ? static_cast<int32_t>(keys[j] & 0xffffffffu) : -1;
+    od[j] = j < m ? __uint_as_float(static_cast<uint32_t>(keys[j] >> 32)) : 0.f;
+  }
+  cnt[i] = m;
+}
+
+int blocks_for(int64_t n) {
+  int64_t b = (n + kThreads - 1) / kThreads;
+  return static_cast<int>(b < 1 ? 1 : b);
+}
+
+int warp_blocks(int64_t n) {
+  int64_t b = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  return static_cast<int>(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+int32_t estimate_normals_impl(o3g_grid* g, float radius, int32_t max_nn, const float* viewpoint, float* d_out,
+                              int32_t out_stride, cudaStream_t s) {
+  const char* fn = "o3g_estimate_normals";
+  if (!g || !(radius >= 0.f) || !std::isfinite(radius) || max_nn < 1 || max_nn > O3G_MAX_NN ||
+      (d_out && out_stride < 3)) {
+    set_error("%s: invalid argument", fn);
+    return O3G_ERR_ARG;
+  }
+  float v[3] = {0.f, 0.f, 0.f};
+  if (viewpoint)
+    for (int a = 0; a < 3; ++a) v[a] = viewpoint[a];
+  if (!std::isfinite(v[0]) || !std::isfinite(v[1]) || !std::isfinite(v[2])) {
+    set_error("%s: viewpoint is not finite", fn);
+    return O3G_ERR_NONFINITE;
+  }
+  if (g->n > 0) {
+    const GridView gv = g->view();
+    TimedRegion tr(O3G_KERNEL_NORMALS, s);
+    count_launch();
+    if (max_nn <= 32)
+      k_normals_warp<<<warp_blocks(g->n), kThreads, 0, s>>>(gv, g->pos_of, radius, max_nn, v[0], v[1], v[2], g->nrm,
+                                                            d_out, out_stride);
+    else
+      k_normals<O3G_MAX_NN><<<blocks_for(g->n), kThreads, 0, s>>>(gv, radius, max_nn, v[0], v[1], v[2], g->nrm,
+                                                                  d_out, out_stride);
+    O3G_TRY(cudaGetLastError());
+  }
+  g->has_normals = true;
+  return O3G_OK;
+}
+
+}  // namespace o3g
+
+using namespace o3g;
+
+extern "C" int32_t o3g_estimate_normals(o3g_grid* g, float radius, int32_t max_nn, const float* viewpoint,
+                                        float* d_nrm_out, int32_t nrm_stride, void* stream) {
+  return estimate_normals_impl(g, radius, max_nn, viewpoint, d_nrm_out, nrm_stride, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int32_t o3g_knn_hybrid(const o3g_grid* g, const float* d_qry, int64_t nq, int32_t stride, float radius,
+                                  int32_t max_nn, int32_t* d_idx, float* d_d2, int32_t* d_cnt, void* stream) {
+  if (!g || nq < 0 || nq > 0x7fffffffLL - kThreads || (nq > 0 && (!d_qry || !d_idx || !d_d2 || !d_cnt)) ||
+      stride < 3 || !(radius >= 0.f) || !std::isfinite(radius) || max_nn < 1 || max_nn > O3G_MAX_NN) {
+    set_error("o3g_knn_hybrid: invalid argument");
+    return O3G_ERR_ARG;
+  }
+  if (nq == 0) return O3G_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const GridView gv = g->view();
+  count_launch();
+  if (max_nn <= 32)
+    k_knn_warp<<<warp_blocks(nq), kThreads, 0, s>>>(gv, d_qry, static_cast<int>(nq), stride, radius, max_nn, d_idx,
+                                                    d_d2, d_cnt);
+  else
+    k_knn<O3G_MAX_NN><<<blocks_for(nq), kThreads, 0, s>>>(gv, d_qry, static_cast<int>(nq), stride, radius, max_nn,
+                                                          d_idx, d_d2, d_cnt);
+  O3G_TRY(cudaGetLastError());
+  return O3G_OK;
+}

@@ -1,0 +1,308 @@
+"""Thin ctypes binding of libo3g.so (C ABI in include/o3g.h).
+
+Argument marshalling only: every step of the registration path runs in the
+library's CUDA kernels.  PyTorch provides device memory and the current
+stream.  There is no CPU fallback: if libo3g.so is missing or cannot be loaded,
+every call raises.
+
+Names follow the C ABI and the paper's API (Sec. 3.3 of arXiv 1801.09847):
+``build_grid`` (the kd-tree's replacement), ``estimate_normals``,
+``knn_hybrid``, ``correspondences``, ``normal_equations``,
+``icp_point_to_plane_grid``, ``icp_point_to_plane`` and
+``register_point_to_plane_host``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libo3g.so")
+
+OK, WARN_DEGENERATE, WARN_FEW_CORR = 0, 1, 2
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT = -1, -2, -3, -4, -5
+MAX_NN = 64
+STATUS_NAMES = {0: "OK", 1: "WARN_DEGENERATE", 2: "WARN_FEW_CORR", -1: "ERR_ARG", -2: "ERR_OOM",
+                -3: "ERR_CUDA", -4: "ERR_NONFINITE", -5: "ERR_TIMEOUT"}
+
+
+class O3GError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+_vp, _i64, _i32, _f32, _f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_double
+_f64p = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+
+_SIGNATURES = {
+    "o3g_last_error": ([], ctypes.c_char_p),
+    "o3g_abi_version": ([], _i32),
+    "o3g_build_grid": ([_vp, _i64, _i32, _f32, _vp, ctypes.POINTER(_vp)], _i32),
+    "o3g_free_grid": ([_vp], _i32),
+    "o3g_grid_info": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_f32)], _i32),
+    "o3g_grid_set_normals": ([_vp, _vp, _i64, _i32, _vp], _i32),
+    "o3g_knn_hybrid": ([_vp, _vp, _i64, _i32, _f32, _i32, _vp, _vp, _vp, _vp], _i32),
+    "o3g_estimate_normals": ([_vp, _f32, _i32, _vp, _vp, _i32, _vp], _i32),
+    "o3g_correspondences": ([_vp, _vp, _i64, _i32, _f64p, _f32, _vp, _vp, _vp], _i32),
+    "o3g_normal_equations": ([_vp, _vp, _i64, _i32, _f64p, _f32, _f64p, _f64p, _f64p, _vp], _i32),
+    "o3g_icp_point_to_plane_grid": ([_vp, _vp, _i64, _i32, _f64p, _f64, _i32, _f64, _f64p, _f64p, _f64p, _i32p, _vp],
+                                    _i32),
+    "o3g_icp_point_to_plane": ([_vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64, _i32, _f64p, _f64, _i32, _f64p, _f64p,
+                                _f64p], _i32),
+    "o3g_register_point_to_plane_host": ([_vp, _i64, _vp, _i64, _vp, _f32, _i32, _f64p, _f64, _i32, _f64, _f64p,
+                                          _f64p, _f64p, _i32p, _vp], _i32),
+    "o3g_launch_count": ([], _i64),
+    "o3g_timing_enable": ([_i32], _i32),
+    "o3g_timing_read": ([_i32, _f64p, ctypes.POINTER(_i64), _i32], _i32),
+}
+
+KERNEL_ICP_CORR, KERNEL_ICP_SOLVE, KERNEL_NORMALS, KERNEL_GRID = 0, 1, 2, 3
+
+
+def launch_count() -> int:
+    """Kernels libo3g.so has launched since it was loaded."""
+    return int(lib().o3g_launch_count())
+
+
+def timing_enable(on: bool = True) -> None:
+    """Bracket each launch of the timed kernels with CUDA events on their launching stream."""
+    lib().o3g_timing_enable(1 if on else 0)
+
+
+def timing_read(kind: int, reset: bool = True) -> tuple[float, int]:
+    """(summed device milliseconds, launches) recorded for one kernel kind since the last reset."""
+    ms, n = _f64(), _i64()
+    _check(lib().o3g_timing_read(int(kind), ctypes.byref(ms), ctypes.byref(n), 1 if reset else 0),
+           "o3g_timing_read")
+    return ms.value, n.value
+
+
+def lib():
+    """Loads libo3g.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libo3g.so not built ({LIB_PATH}); run __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().o3g_last_error().decode(errors="replace")
+
+
+def _check(st: int, where: str) -> int:
+    if st < 0:
+        raise O3GError(st, where, last_error())
+    return st
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _cloud(t, name: str):
+    """(device pointer, n, stride) of an N x k (k >= 3) float32 CUDA tensor with unit inner stride."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+        raise TypeError(f"{name} must be a float32 CUDA tensor")
+    if t.dim() != 2 or t.shape[1] < 3 or (t.shape[0] > 1 and t.stride(1) != 1):
+        raise ValueError(f"{name} must be N x k (k >= 3) with contiguous rows")
+    stride = t.stride(0) if t.shape[0] > 1 else max(3, t.shape[1])
+    return ctypes.c_void_p(t.data_ptr() if t.numel() else 0), t.shape[0], stride
+
+
+def _pose(T) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(16))
+
+
+def _pp(a: np.ndarray):
+    return a.ctypes.data_as(_f64p)
+
+
+class Grid:
+    """Device uniform grid over one cloud (o3g_build_grid); freed with the object."""
+
+    def __init__(self, handle: int, n: int, stream):
+        self._h = ctypes.c_void_p(handle)
+        self.n = n
+        self._stream = stream
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if not self._h:
+            raise RuntimeError("grid already freed")
+        return self._h
+
+    def info(self):
+        n, cell = _i64(), _f32()
+        _check(lib().o3g_grid_info(self.handle, ctypes.byref(n), ctypes.byref(cell)), "o3g_grid_info")
+        return n.value, cell.value
+
+    def free(self):
+        if self._h:
+            lib().o3g_free_grid(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def set_normals(self, nrm, stream=None):
+        p, n, stride = _cloud(nrm, "normals")
+        _check(lib().o3g_grid_set_normals(self.handle, p, n, stride, _stream(stream)), "o3g_grid_set_normals")
+
+    def estimate_normals(self, radius: float, max_nn: int, viewpoint=(0.0, 0.0, 0.0), out=None, stream=None):
+        """estimate_normals(pc, KDTreeSearchParamHybrid(radius, max_nn)); returns N x 3 normals (input order).
+
+        out=None allocates the result; out=False keeps the normals in the grid only and returns None.
+        """
+        torch = _torch()
+        if out is False:
+            p, stride = _vp(0), 3
+        else:
+            if out is None:
+                out = torch.empty((self.n, 3), dtype=torch.float32, device="cuda")
+            p, n, stride = _cloud(out, "out")
+            if n != self.n:
+                raise ValueError("out must have one row per grid point")
+        vp = (ctypes.c_float * 3)(*[float(v) for v in viewpoint])
+        _check(lib().o3g_estimate_normals(self.handle, float(radius), int(max_nn), ctypes.cast(vp, _vp), p, stride,
+                                          _stream(stream)), "o3g_estimate_normals")
+        return None if out is False else out
+
+
+def build_grid(xyz, cell_size: float, stream=None) -> Grid:
+    p, n, stride = _cloud(xyz, "xyz")
+    h = ctypes.c_void_p()
+    _check(lib().o3g_build_grid(p, n, stride, float(cell_size), _stream(stream), ctypes.byref(h)), "o3g_build_grid")
+    return Grid(h.value, n, stream)
+
+
+def knn_hybrid(grid: Grid, queries, radius: float, max_nn: int, stream=None):
+    """KDTreeSearchParamHybrid(radius, max_nn) search: (idx int32 [nq, max_nn], d2 [nq, max_nn], count [nq])."""
+    torch = _torch()
+    p, nq, stride = _cloud(queries, "queries")
+    idx = torch.empty((nq, max_nn), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((nq, max_nn), dtype=torch.float32, device="cuda")
+    cnt = torch.empty((nq,), dtype=torch.int32, device="cuda")
+    _check(lib().o3g_knn_hybrid(grid.handle, p, nq, stride, float(radius), int(max_nn), _vp(idx.data_ptr()),
+                                _vp(d2.data_ptr()), _vp(cnt.data_ptr()), _stream(stream)), "o3g_knn_hybrid")
+    return idx, d2, cnt
+
+
+def correspondences(grid: Grid, src, T, max_corr_dist: float, stream=None):
+    """Transform + fixed-radius NN at pose T: (corr int32 [ns], d2 float32 [ns])."""
+    torch = _torch()
+    p, ns, stride = _cloud(src, "src")
+    corr = torch.empty((ns,), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((ns,), dtype=torch.float32, device="cuda")
+    Tp = _pose(T)
+    _check(lib().o3g_correspondences(grid.handle, p, ns, stride, _pp(Tp), float(max_corr_dist), _vp(corr.data_ptr()),
+                                     _vp(d2.data_ptr()), _stream(stream)), "o3g_correspondences")
+    return corr, d2
+
+
+def normal_equations(grid: Grid, src, T, max_corr_dist: float, stream=None):
+    """J^T J (6x6), J^T r (6), (sum r^2, sum d2, |C|) at pose T (Eq. 2)."""
+    p, ns, stride = _cloud(src, "src")
+    A = np.zeros(36)
+    b = np.zeros(6)
+    stats = np.zeros(3)
+    Tp = _pose(T)
+    _check(lib().o3g_normal_equations(grid.handle, p, ns, stride, _pp(Tp), float(max_corr_dist), _pp(A), _pp(b),
+                                      _pp(stats), _stream(stream)), "o3g_normal_equations")
+    return A.reshape(6, 6), b, stats
+
+
+def _result(st, T, fit, rmse, iters):
+    return dict(status=st, T=T.reshape(4, 4), fitness=fit.value, rmse=rmse.value,
+                iters=iters.value if iters is not None else None)
+
+
+def icp_point_to_plane_grid(grid: Grid, src, init_T, max_corr_dist: float, max_iter: int, eps: float = 0.0,
+                            stream=None) -> dict:
+    """registration_icp(..., TransformationEstimationPointToPlane()) against a resident target grid."""
+    p, ns, stride = _cloud(src, "src")
+    T0 = _pose(init_T)
+    T = np.zeros(16)
+    fit, rmse, iters = _f64(), _f64(), _i32()
+    st = _check(lib().o3g_icp_point_to_plane_grid(grid.handle, p, ns, stride, _pp(T0), float(max_corr_dist),
+                                                  int(max_iter), float(eps), _pp(T), ctypes.byref(fit),
+                                                  ctypes.byref(rmse), ctypes.byref(iters), _stream(stream)),
+                "o3g_icp_point_to_plane_grid")
+    return _result(st, T, fit, rmse, iters)
+
+
+def icp_point_to_plane(src, tgt, tgt_nrm, init_T, max_corr_dist: float, max_iter: int) -> dict:
+    """One-shot point-to-plane ICP on device clouds (builds and frees the target grid)."""
+    _torch().cuda.synchronize()
+    ps, ns, ss = _cloud(src, "src")
+    pt, nt, stt = _cloud(tgt, "tgt")
+    pn, nn, sn = _cloud(tgt_nrm, "tgt_nrm")
+    T0 = _pose(init_T)
+    T = np.zeros(16)
+    fit, rmse = _f64(), _f64()
+    st = _check(lib().o3g_icp_point_to_plane(ps, ns, ss, pt, nt, stt, pn, nn, sn, _pp(T0), float(max_corr_dist),
+                                             int(max_iter), _pp(T), ctypes.byref(fit), ctypes.byref(rmse)),
+                "o3g_icp_point_to_plane")
+    return _result(st, T, fit, rmse, None)
+
+
+def register_point_to_plane_host(src, tgt, tgt_nrm, init_T, max_corr_dist: float, max_iter: int, eps: float = 0.0,
+                                 normal_radius: float = 0.1, normal_max_nn: int = 30, stream=None) -> dict:
+    """Whole refinement from host arrays (N x 3 float32, C-contiguous; page-locked tensors copy asynchronously).
+
+    `src`, `tgt`, `tgt_nrm` may be numpy arrays or CPU torch tensors; `tgt_nrm=None`
+    estimates the target normals on the GPU with (normal_radius, normal_max_nn).
+    """
+    def host_ptr(a, name):
+        if a is None:
+            return _vp(0), 0
+        torch = _torch()
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous() or (a.numel() and a.shape[-1] != 3):
+                raise TypeError(f"{name} must be a contiguous N x 3 float32 host tensor")
+            return _vp(a.data_ptr() if a.numel() else 0), a.shape[0]
+        arr = np.asarray(a)
+        if arr.dtype != np.float32 or not arr.flags.c_contiguous or (arr.size and arr.shape[-1] != 3):
+            raise TypeError(f"{name} must be a C-contiguous N x 3 float32 array")
+        return _vp(arr.ctypes.data if arr.size else 0), arr.shape[0] if arr.ndim == 2 else 0
+
+    ps, ns = host_ptr(src, "src")
+    pt, nt = host_ptr(tgt, "tgt")
+    pn, nn = host_ptr(tgt_nrm, "tgt_nrm")
+    if tgt_nrm is not None and nn != nt:
+        raise O3GError(ERR_ARG, "register_point_to_plane_host", "normals must match the target points one to one")
+    T0 = _pose(init_T)
+    T = np.zeros(16)
+    fit, rmse, iters = _f64(), _f64(), _i32()
+    st = _check(lib().o3g_register_point_to_plane_host(ps, ns, pt, nt, pn, float(normal_radius), int(normal_max_nn),
+                                                       _pp(T0), float(max_corr_dist), int(max_iter), float(eps),
+                                                       _pp(T), ctypes.byref(fit), ctypes.byref(rmse),
+                                                       ctypes.byref(iters), _stream(stream)),
+                "o3g_register_point_to_plane_host")
+    return _result(st, T, fit, rmse, iters)

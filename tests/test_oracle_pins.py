@@ -393,8 +393,8 @@ def test_normals_on_sphere_are_radial_and_oriented(ora):
     v /= np.linalg.norm(v, axis=1, keepdims=True)
     pts = v.astype(np.float32)
     nrm = ora.estimate_normals(pts, 0.1, 30, viewpoint=(0.0, 0.0, 0.0))
-    cosang = np.abs(np.sum(nrm.astype(np.float64) * v, axis=1))
-    ang = np.arccos(np.clip(cosang, -1, 1))
+    n64 = nrm.astype(np.float64)
+    ang = np.arctan2(np.linalg.norm(np.cross(n64, v), axis=1), np.abs(np.sum(n64 * v, axis=1)))
     # a plane fitted to a cap of angular radius 0.1 tilts by at most about half of it when the
     # neighbours are lopsided; a wrong eigenvector would be off by ~90 degrees
     assert np.all(ang < 0.05) and np.median(ang) < 1e-2
