@@ -188,6 +188,35 @@ O3G_API int32_t o3g_register_point_to_plane_host(const float* h_src, int64_t ns,
                                          void* stream);
 
 /*
+ * Allocation-free form of o3g_icp_point_to_plane_grid.  The paper has no
+ * counterpart: this entry point exists for callers that must not allocate device
+ * memory once they are running - for example a tracking loop that registers
+ * every incoming frame under a fixed memory budget and cannot afford allocator
+ * latency or failure mid-run, or a host program that hands all device memory to
+ * its own allocator.  Such a caller builds the target grid (o3g_build_grid,
+ * which allocates) during set-up and then calls this in its loop.
+ *
+ * Same arguments, results and status codes as o3g_icp_point_to_plane_grid, with
+ * two differences: the source is processed in the caller's order (the sums of
+ * J^T J and J^T r therefore round differently, within the usual tolerances),
+ * and all working memory is one library-owned static device array of
+ * 4,736,256 bytes (4.5 MiB) that every GPU loading the library holds until the
+ * process exits.
+ *   - ns > O3G_NOALLOC_MAX_POINTS gives O3G_ERR_ARG; nothing is allocated.
+ *   - The first call on a device looks up that array's device address for the
+ *     current device (cudaGetSymbolAddress); make that first call before any
+ *     stream capture.
+ *   - Every call uses the same array.  Calls whose work overlaps on the GPU
+ *     (other streams, other host threads) race and corrupt each other's state:
+ *     serialise them.  Each call clears what must start at zero.
+ */
+#define O3G_NOALLOC_MAX_POINTS 262144
+O3G_API int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* tgt, const float* d_src, int64_t ns,
+                                                    int32_t stride, const double* init_T, double max_corr_dist,
+                                                    int32_t max_iter, double eps, double* out_T, double* out_fitness,
+                                                    double* out_rmse, int32_t* out_iters, void* stream);
+
+/*
  * Instrumentation (no counterpart in the paper; used by benchmarks and tests).
  * o3g_launch_count: kernels this library has launched since it was loaded.
  * o3g_timing_enable(1): from then on, each launch of the kernels listed below

@@ -17,6 +17,7 @@
 //      device.  The next launch reads the new pose.
 // The pose never leaves the device between iterations.
 #include <cmath>
+#include <mutex>
 
 #include "o3g_internal.cuh"
 
@@ -672,4 +673,141 @@ extern "C" int32_t o3g_icp_point_to_plane(const float* d_src, int64_t ns, int32_
                  nullptr);
   o3g_free_grid(g);
   return st;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free ICP: the same iteration kernel, with every scratch buffer
+// carved out of one static device array instead of the memory pool.  For
+// callers that cannot allocate once running (see o3g.h).
+
+namespace o3g {
+namespace {
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+constexpr int kNaMaxBlocks = (O3G_NOALLOC_MAX_POINTS + kThreads * kPPT - 1) / (kThreads * kPPT);
+constexpr int kNaMaxGroups = (kNaMaxBlocks + kGroup - 1) / kGroup;
+constexpr size_t kNaOffSrc = 0;
+constexpr size_t kNaOffState = align256(kNaOffSrc + sizeof(float4) * static_cast<size_t>(O3G_NOALLOC_MAX_POINTS));
+constexpr size_t kNaOffPartials = align256(kNaOffState + sizeof(IcpState));
+constexpr size_t kNaOffCounters =
+    align256(kNaOffPartials + sizeof(double) * kPartial * static_cast<size_t>(kNaMaxBlocks + kNaMaxGroups));
+constexpr size_t kNaOffFlag = align256(kNaOffCounters + sizeof(unsigned) * kNaMaxGroups);
+constexpr size_t kNaBytes = align256(kNaOffFlag + sizeof(int));
+static_assert(kNaBytes == 4736256, "update the size stated in o3g.h");
+
+// The working memory of o3g_icp_point_to_plane_grid_noalloc, shared by every call.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+std::mutex g_noalloc_mutex;
+constexpr int kNaMaxDevices = 64;
+void* g_noalloc_addr[kNaMaxDevices] = {};
+
+// Source rows (caller order) -> float4 (x, y, z, index bits); flags non-finite coordinates.
+__global__ void __launch_bounds__(kThreads) k_pack_src(const float* __restrict__ src, int n, int stride,
+                                                       float4* __restrict__ out, int* __restrict__ bad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* p = src + static_cast<int64_t>(i) * stride;
+  const float x = p[0], y = p[1], z = p[2];
+  if (!isfinite(x) || !isfinite(y) || !isfinite(z)) *bad = 1;
+  out[i] = make_float4(x, y, z, __int_as_float(i));
+}
+
+// Device address of the static array on the current device (looked up once per device).
+int32_t noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  O3G_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNaMaxDevices) {
+    set_error("o3g_icp_point_to_plane_grid_noalloc: device %d out of range", dev);
+    return O3G_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    O3G_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  return O3G_OK;
+}
+
+}  // namespace
+}  // namespace o3g
+
+extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const float* d_src, int64_t ns,
+                                                       int32_t stride, const double* init_T, double max_corr_dist,
+                                                       int32_t max_iter, double eps, double* out_T,
+                                                       double* out_fitness, double* out_rmse, int32_t* out_iters,
+                                                       void* stream) {
+  using namespace o3g;
+  const char* fn = "o3g_icp_point_to_plane_grid_noalloc";
+  if (!g || !out_T || !out_fitness || !out_rmse || max_iter < 0 || !(max_corr_dist >= 0.0) ||
+      !std::isfinite(max_corr_dist)) {
+    set_error("%s: invalid argument", fn);
+    return O3G_ERR_ARG;
+  }
+  O3G_TRY_STATUS(check_src(fn, d_src, ns, stride));
+  if (ns > O3G_NOALLOC_MAX_POINTS) {
+    set_error("%s: %lld source points exceed the fixed working memory (at most %d points)", fn,
+              static_cast<long long>(ns), O3G_NOALLOC_MAX_POINTS);
+    return O3G_ERR_ARG;
+  }
+  if (!g->has_normals) {
+    set_error("%s: the target grid carries no normals (attach or estimate them first)", fn);
+    return O3G_ERR_ARG;
+  }
+  if (!pose_ok(init_T)) {
+    set_error("%s: init_T is null or not finite", fn);
+    return O3G_ERR_NONFINITE;
+  }
+  unsigned char* base = nullptr;
+  O3G_TRY_STATUS(noalloc_scratch(&base));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float4* src4 = reinterpret_cast<float4*>(base + kNaOffSrc);
+  IcpState* st = reinterpret_cast<IcpState*>(base + kNaOffState);
+  double* partials = reinterpret_cast<double*>(base + kNaOffPartials);
+  unsigned* counters = reinterpret_cast<unsigned*>(base + kNaOffCounters);
+  int* bad = reinterpret_cast<int*>(base + kNaOffFlag);
+  const int n = static_cast<int>(ns);
+  const int nblk = iter_blocks(ns);
+  const int ngroups = (nblk + kGroup - 1) / kGroup;
+  // the arrival counters and the input flag must start at zero; the state is rewritten by k_init_state
+  O3G_TRY(cudaMemsetAsync(counters, 0, sizeof(unsigned) * ngroups, s));
+  O3G_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  if (n > 0) {
+    k_pack_src<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(d_src, n, stride, src4, bad);
+    count_launch();
+  }
+  k_init_state<<<1, 32, 0, s>>>(st, to_pose(init_T));
+  count_launch();
+  const float r = static_cast<float>(max_corr_dist);
+  const GridView gv = g->view();
+  double* gsums = partials + static_cast<size_t>(kPartial) * nblk;
+  for (int it = 0; it <= max_iter; ++it) {
+    const int mode = it < max_iter ? kIterate : kEvaluate;
+    k_icp_iter<<<nblk, kThreads, 0, s>>>(gv, g->cell, src4, n, st, r, partials, gsums, counters, eps, mode, nullptr,
+                                         nullptr);
+    count_launch();
+  }
+  O3G_TRY(cudaGetLastError());
+  IcpState h;
+  int h_bad = 0;
+  O3G_TRY(cudaMemcpyAsync(&h, st, sizeof(IcpState), cudaMemcpyDeviceToHost, s));
+  O3G_TRY(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  O3G_TRY(cudaStreamSynchronize(s));
+  if (h_bad) {
+    set_error("%s: non-finite source coordinate", fn);
+    return O3G_ERR_NONFINITE;
+  }
+  if (h.nonfinite) {
+    set_error("%s: the normal equations became non-finite (check the target normals)", fn);
+    return O3G_ERR_NONFINITE;
+  }
+  for (int k = 0; k < 16; ++k) out_T[k] = h.T[k];
+  *out_fitness = h.fitness;
+  *out_rmse = h.rmse;
+  if (out_iters) *out_iters = h.iters;
+  if (h.few_corr) return O3G_WARN_FEW_CORR;
+  if (h.degenerate) return O3G_WARN_DEGENERATE;
+  return O3G_OK;
 }

@@ -58,6 +58,8 @@ _SIGNATURES = {
                                 _f64p], _i32),
     "o3g_register_point_to_plane_host": ([_vp, _i64, _vp, _i64, _vp, _f32, _i32, _f64p, _f64, _i32, _f64, _f64p,
                                           _f64p, _f64p, _i32p, _vp], _i32),
+    "o3g_icp_point_to_plane_grid_noalloc": ([_vp, _vp, _i64, _i32, _f64p, _f64, _i32, _f64, _f64p, _f64p, _f64p,
+                                             _i32p, _vp], _i32),
     "o3g_launch_count": ([], _i64),
     "o3g_timing_enable": ([_i32], _i32),
     "o3g_timing_read": ([_i32, _f64p, ctypes.POINTER(_i64), _i32], _i32),

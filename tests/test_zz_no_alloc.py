@@ -1,0 +1,89 @@
+"""The allocation-free ICP entry point against the regular one (GPU).
+
+o3g_icp_point_to_plane_grid_noalloc is for callers that cannot allocate device
+memory once running (a per-frame tracking loop under a fixed memory budget, a
+host that gives all device memory to its own allocator).  It keeps its working
+memory in one static device array shared by every call, so this test calls it
+twice in a row and checks both results against o3g_icp_point_to_plane_grid on a
+well-conditioned problem run to convergence, within the 1e-6 pose tolerance the
+other ICP parity tests use for such problems.  The file name sorts last so that
+a run stopping at the first failure has already run every other test.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1801_09847_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+POSE_TOL = 1e-6
+
+
+def _corner_scene(g, spacing=0.01):
+    u = np.arange(0.0, 1.0, spacing)
+    a, b = np.meshgrid(u, u)
+    a, b = a.ravel(), b.ravel()
+    z0 = np.zeros_like(a)
+    P = [np.column_stack([a, b, z0]), np.column_stack([a, z0, b]), np.column_stack([z0, a, b])]
+    N = [np.tile([0, 0, 1.0], (len(a), 1)), np.tile([0, 1.0, 0], (len(a), 1)), np.tile([1.0, 0, 0], (len(a), 1))]
+    return np.vstack(P), np.vstack(N)
+
+
+@pytest.fixture(scope="module")
+def o3g():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1801_09847_gb300 import build, o3g as mod
+    build.build()
+    mod.lib()
+    return mod
+
+
+def _call_noalloc(o3g, grid, src, init_T, r, max_iter, eps):
+    import torch
+    p, ns, stride = o3g._cloud(src, "src")
+    T0 = np.ascontiguousarray(np.asarray(init_T, np.float64).reshape(16))
+    T = np.zeros(16)
+    fit, rmse, iters = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    st = o3g.lib().o3g_icp_point_to_plane_grid_noalloc(
+        grid.handle, p, ns, stride, T0.ctypes.data_as(o3g._f64p), float(r), int(max_iter), float(eps),
+        T.ctypes.data_as(o3g._f64p), ctypes.byref(fit), ctypes.byref(rmse), ctypes.byref(iters),
+        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return st, T.reshape(4, 4), fit.value, rmse.value, iters.value
+
+
+def test_noalloc_matches_regular_entry_point_twice(o3g):
+    import torch
+    g = synth.rng(77)
+    tgt, nrm = _corner_scene(g)
+    T_gt = synth.perturbation(g, 3.0, 0.03)
+    src = (synth.apply_T(synth.inv_T(T_gt), tgt) + g.normal(0, 0.002, tgt.shape)).astype(np.float32)
+    grid = o3g.build_grid(torch.from_numpy(tgt.astype(np.float32)).cuda(), 0.05)
+    grid.set_normals(torch.from_numpy(nrm.astype(np.float32)).cuda())
+    d_src = torch.from_numpy(src).cuda()
+    ref = o3g.icp_point_to_plane_grid(grid, d_src, np.eye(4), 0.05, 100, eps=1e-7)
+    assert ref["status"] == o3g.OK and ref["iters"] < 100
+    for _ in range(2):
+        st, T, fit, rmse, iters = _call_noalloc(o3g, grid, d_src, np.eye(4), 0.05, 100, 1e-7)
+        assert st == ref["status"] and iters == ref["iters"]
+        ang, dt = synth.pose_error(T, ref["T"])
+        assert ang <= POSE_TOL and dt <= POSE_TOL, (ang, dt)
+        assert fit == ref["fitness"]
+        assert rmse == pytest.approx(ref["rmse"], rel=1e-6)
+
+
+def test_noalloc_rejects_sizes_beyond_its_fixed_memory(o3g):
+    import torch
+    limit = 262144
+    tgt = torch.zeros((10, 3), dtype=torch.float32, device="cuda")
+    grid = o3g.build_grid(tgt, 0.1)
+    grid.set_normals(tgt)
+    big = torch.zeros((limit + 1, 3), dtype=torch.float32, device="cuda")
+    st, *_ = _call_noalloc(o3g, grid, big, np.eye(4), 0.1, 1, 0.0)
+    assert st == o3g.ERR_ARG
+    assert "exceed" in o3g.last_error()
