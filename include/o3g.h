@@ -164,7 +164,7 @@ O3G_API int32_t o3g_icp_point_to_plane_grid(const o3g_grid* tgt, const float* d_
 
 /*
  * One-shot form of the above on raw device clouds: builds a grid over the
- * target (cell = max_corr_dist), attaches d_tgt_nrm (n_nrm must equal nt,
+ * target (cell = 1.002 x max_corr_dist), attaches d_tgt_nrm (n_nrm must equal nt,
  * Sec. 3.1), runs ICP with eps = 0 on the legacy default stream and frees the
  * grid.
  */
@@ -176,7 +176,7 @@ O3G_API int32_t o3g_icp_point_to_plane(const float* d_src, int64_t ns, int32_t s
 /*
  * The whole pairwise refinement from HOST buffers (the call a user with data in
  * host memory makes): copies source and target to the device, builds the
- * target grid (cell = max_corr_dist), attaches h_tgt_nrm or, if it is NULL,
+ * target grid (cell = 1.002 x max_corr_dist), attaches h_tgt_nrm or, if it is NULL,
  * estimates target normals (normal_radius, normal_max_nn, viewpoint = origin),
  * runs ICP and returns the results in host memory.  h_src, h_tgt and h_tgt_nrm
  * are packed xyz (stride 3); page-locked buffers make the copies asynchronous.

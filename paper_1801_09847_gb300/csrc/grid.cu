@@ -254,6 +254,38 @@ __global__ void __launch_bounds__(kThreads) k_cell_start(const uint32_t* __restr
   }
 }
 
+// Per (x, y) column: the lowest and highest occupied z-cell, from cell_start by
+// binary search (cell_start is non-decreasing along the column).  Empty columns
+// get lowest = 0xffff, highest = 0, an empty range.
+__global__ void __launch_bounds__(kThreads) k_col_extent(const uint32_t* __restrict__ cell_start, int ncol, int sz,
+                                                         uint32_t* __restrict__ col_z) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncol; c += gridDim.x * blockDim.x) {
+    const uint32_t* cs = cell_start + static_cast<int64_t>(c) * sz;
+    const uint32_t first = cs[0], last = cs[sz];
+    if (first == last) {
+      col_z[c] = 0xffffu;
+      continue;
+    }
+    int lo = 0, hi = sz - 1;  // lowest z with cs[z + 1] > first
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (cs[mid + 1] > first) hi = mid;
+      else lo = mid + 1;
+    }
+    const int zmin = lo;
+    lo = 0;
+    hi = sz - 1;  // highest z with cs[z] < last
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (cs[mid] < last) lo = mid;
+      else hi = mid - 1;
+    }
+    col_z[c] = static_cast<uint32_t>(zmin) | (static_cast<uint32_t>(lo) << 16);
+  }
+}
+
+__global__ void k_empty_col(uint32_t* col_z) { col_z[0] = 0xffffu; }
+
 __global__ void __launch_bounds__(kThreads) k_gather(const float* __restrict__ xyz, int n, int stride,
                                                      const uint32_t* __restrict__ perm, float4* __restrict__ pts,
                                                      int32_t* __restrict__ pos_of) {
@@ -446,6 +478,8 @@ static void release(o3g_grid* g) {
   dfree(g->nrm, g->stream);
   dfree(g->cell_start, g->stream);
   dfree(g->pos_of, g->stream);
+  dfree(g->col_z, g->stream);
+  g->col_z = nullptr;
   g->pts = nullptr;
   g->nrm = nullptr;
   g->cell_start = nullptr;
@@ -465,6 +499,10 @@ static int32_t build_impl(const float* d_xyz, int64_t n64, int stride, float cel
     O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->pts), sizeof(float4), s));
     O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->nrm), sizeof(float4), s));
     O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->pos_of), sizeof(int32_t), s));
+    O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->col_z), sizeof(uint32_t), s));
+    O3G_TRY(cudaMemsetAsync(g->col_z, 0, sizeof(uint32_t), s));
+    k_empty_col<<<1, 1, 0, s>>>(g->col_z);
+    count_launch();
     return O3G_OK;
   }
   // 1. bounding box; enlarge the cell while the dense table would be too big.
@@ -536,6 +574,12 @@ static int32_t build_impl(const float* d_xyz, int64_t n64, int stride, float cel
   int nbc = blocks_for(cells + 1, kThreads);
   if (nbc > kNumSMs * 16) nbc = kNumSMs * 16;
   k_cell_start<<<nbc, kThreads, 0, s>>>(keys.as<uint32_t>(), n, g->cell_start, cells);
+  const int ncol = g->span[0] * g->span[1];
+  O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->col_z), sizeof(uint32_t) * ncol, s));
+  int nbz = blocks_for(ncol, kThreads);
+  if (nbz > kNumSMs * 16) nbz = kNumSMs * 16;
+  k_col_extent<<<nbz, kThreads, 0, s>>>(g->cell_start, ncol, g->span[2], g->col_z);
+  count_launch();
   k_gather<<<blocks_for(n, kThreads), kThreads, 0, s>>>(d_xyz, n, stride, vals.as<uint32_t>(), g->pts, g->pos_of);
   count_launch(2);
   O3G_TRY(cudaGetLastError());

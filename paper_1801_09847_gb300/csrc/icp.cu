@@ -16,6 +16,7 @@
 //      with the frozen-pivot rule, and updates T <- [Rz Ry Rx(xi), t] T on the
 //      device.  The next launch reads the new pose.
 // The pose never leaves the device between iterations.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -28,7 +29,6 @@ namespace {
 constexpr int kThreads = 128;
 constexpr int kPPT = 1;       // source points per thread
 constexpr int kPartial = 32;  // doubles per block partial
-constexpr int kNSum = 29;     // 21 (J^T J upper) + 6 (J^T r) + r^2 + d2
 constexpr int kGroup = 32;    // block partials summed together by a group's last block
 
 struct Pose {
@@ -71,6 +71,13 @@ __global__ void k_init_state(IcpState* st, Pose T) {
   st->rmse = 0.0;
 }
 
+// sqrt(x) for x >= 0 from the hardware reciprocal square root (a few ulp): the
+// search bounds add a relative margin far larger than that error.
+__device__ __forceinline__ float fast_sqrt(float x) {
+  const float y = fmaxf(x, 1e-30f);
+  return y * rsqrtf(y);
+}
+
 // Lower bound (with a rounding margin) of |c - x| over the cell slab
 // [(lo + i) * cell, (lo + i + 1) * cell) along one axis.
 __device__ __forceinline__ float slab_gap(float x, int i_abs, float cell, float margin) {
@@ -83,6 +90,7 @@ __device__ __forceinline__ float slab_gap(float x, int i_abs, float cell, float 
 // Scans sorted target positions [beg, end) and keeps the minimum of (d2, original index).
 __device__ __forceinline__ void scan_run(const float4* __restrict__ pts, uint32_t beg, uint32_t end, float px,
                                          float py, float pz, float& best_d2, int& best_orig, int& best) {
+#pragma unroll 4
   for (uint32_t k = beg; k < end; ++k) {
     const float4 q = pts[k];
     const float d2 = dist2_rn(px, py, pz, q);
@@ -95,51 +103,201 @@ __device__ __forceinline__ void scan_run(const float4* __restrict__ pts, uint32_
   }
 }
 
-// Fixed-radius nearest neighbour of p among the grid points: the minimum of
-// (d2, original index) over d2 <= r2.  Returns the sorted position or -1.
-__device__ int nn_search(const GridView& g, float cell, float px, float py, float pz, float r, float r2,
-                         float& best_d2) {
-  int ax, bx, ay, by, az, bz;
-  axis_range(px, r, g.inv_cell, g.lo_x, g.sx, ax, bx);
-  axis_range(py, r, g.inv_cell, g.lo_y, g.sy, ay, by);
-  axis_range(pz, r, g.inv_cell, g.lo_z, g.sz, az, bz);
-  int best = -1, best_orig = 0x7fffffff;
-  best_d2 = r2;
-  if (ax > bx || ay > by || az > bz) return -1;
-  // home cell first: it usually holds a close match, which then prunes the rest
+// Running fixed-radius nearest neighbour of one query: the minimum of
+// (d2, original index) among the candidates seen so far with d2 <= r2.
+struct Nearest {
+  float d2;
+  int orig;
+  int pos;  // sorted target position, -1 if none
+};
+
+__device__ __forceinline__ void consider(Nearest& nb, float4 q, int pos, float px, float py, float pz) {
+  const float d2 = dist2_rn(px, py, pz, q);
+  const int o = __float_as_int(q.w);
+  if (d2 < nb.d2 || (d2 == nb.d2 && o < nb.orig)) {
+    nb.d2 = d2;
+    nb.orig = o;
+    nb.pos = pos;
+  }
+}
+
+// Candidates that give a first bound: this point's match in the previous
+// iteration (`hint`, a sorted target position or -1) and those of its
+// neighbours in the spatially sorted warp.  Each is an ordinary candidate, so it
+// only tightens the bound, never changes the answer.  All lanes must call this.
+__device__ __forceinline__ void first_bound(const GridView& g, float px, float py, float pz, int hint, Nearest& nb) {
+  const unsigned full = 0xffffffffu;
+  const int h[5] = {hint, __shfl_xor_sync(full, hint, 1), __shfl_xor_sync(full, hint, 2),
+                    __shfl_xor_sync(full, hint, 3), __shfl_xor_sync(full, hint, 4)};
+  float4 q[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) q[k] = h[k] >= 0 ? g.pts[h[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+    if (h[k] >= 0) consider(nb, q[k], h[k], px, py, pz);
+}
+
+__device__ __forceinline__ float search_margin(float cell, float r, float px, float py, float pz) {
+  return __fadd_rn(__fmul_rn(__fadd_rn(cell, r), 1e-5f),
+                   __fmul_rn(fmaxf(fmaxf(fabsf(px), fabsf(py)), fabsf(pz)), 4e-6f));
+}
+
+// The rest of the exact search from global memory, given the first bound: the
+// home cell first when there is no bound yet, then every cell that can still
+// hold d2 <= best (box sized from the bound; each column over the z-range the
+// bound allows, clipped to the column's occupied cells).  Every bound carries a
+// margin for float32 rounding and ties are kept, so the result is exactly the
+// brute-force minimum.
+__device__ void box_search_global(const GridView& g, float cell, float px, float py, float pz, float r,
+                                  Nearest& nb) {
+  const float margin = search_margin(cell, r, px, py, pz);
   const int hx = cell_coord(px, g.inv_cell) - g.lo_x;
   const int hy = cell_coord(py, g.inv_cell) - g.lo_y;
   const int hz = cell_coord(pz, g.inv_cell) - g.lo_z;
-  const bool home_in = hx >= ax && hx <= bx && hy >= ay && hy <= by && hz >= az && hz <= bz;
-  if (home_in) {
+  const bool home_in = hx >= 0 && hx < g.sx && hy >= 0 && hy < g.sy && hz >= 0 && hz < g.sz;
+  bool home_done = false;
+  if (nb.pos < 0 && home_in) {
     const int c = (hx * g.sy + hy) * g.sz + hz;
-    scan_run(g.pts, g.cell_start[c], g.cell_start[c + 1], px, py, pz, best_d2, best_orig, best);
+    scan_run(g.pts, g.cell_start[c], g.cell_start[c + 1], px, py, pz, nb.d2, nb.orig, nb.pos);
+    home_done = true;
   }
-  const float margin = __fadd_rn(__fmul_rn(__fadd_rn(cell, r), 1e-5f),
-                                 __fmul_rn(fmaxf(fmaxf(fabsf(px), fabsf(py)), fabsf(pz)), 4e-6f));
+  const float reach = __fadd_rn(fast_sqrt(__fmul_rn(nb.d2, 1.0001f)), margin);
+  int ax, bx, ay, by, az, bz;
+  axis_range(px, reach, g.inv_cell, g.lo_x, g.sx, ax, bx);
+  axis_range(py, reach, g.inv_cell, g.lo_y, g.sy, ay, by);
+  axis_range(pz, reach, g.inv_cell, g.lo_z, g.sz, az, bz);
+  if (ax > bx || ay > by || az > bz) return;
   for (int x = ax; x <= bx; ++x) {
     const float gx = slab_gap(px, x + g.lo_x, cell, margin);
-    const float gx2 = gx * gx;
     for (int y = ay; y <= by; ++y) {
       const float gy = slab_gap(py, y + g.lo_y, cell, margin);
-      const float lim = __fmul_rn(best_d2, 1.0001f) - (gx2 + gy * gy);
+      const float lim = __fmul_rn(nb.d2, 1.0001f) - (gx * gx + gy * gy);
       if (lim < 0.f) continue;
-      // z-range that can still hold d2 <= best
-      const float rz = __fadd_rn(sqrtf(lim), margin);
-      const int zl = max(az, cell_coord(__fsub_rn(pz, rz), g.inv_cell) - g.lo_z);
-      const int zh = min(bz, cell_coord(__fadd_rn(pz, rz), g.inv_cell) - g.lo_z);
-      if (zl > zh) continue;
+      const float rz = __fadd_rn(fast_sqrt(lim), margin);
+      int zl = max(az, cell_coord(__fsub_rn(pz, rz), g.inv_cell) - g.lo_z);
+      int zh = min(bz, cell_coord(__fadd_rn(pz, rz), g.inv_cell) - g.lo_z);
+      if (zl > zh || !column_z(g, x * g.sy + y, zl, zh)) continue;
       const int col = (x * g.sy + y) * g.sz;
-      if (home_in && x == hx && y == hy && zl <= hz && hz <= zh) {
-        scan_run(g.pts, g.cell_start[col + zl], g.cell_start[col + hz], px, py, pz, best_d2, best_orig, best);
-        scan_run(g.pts, g.cell_start[col + hz + 1], g.cell_start[col + zh + 1], px, py, pz, best_d2, best_orig,
-                 best);
+      if (home_done && x == hx && y == hy && zl <= hz && hz <= zh) {
+        scan_run(g.pts, g.cell_start[col + zl], g.cell_start[col + hz], px, py, pz, nb.d2, nb.orig, nb.pos);
+        scan_run(g.pts, g.cell_start[col + hz + 1], g.cell_start[col + zh + 1], px, py, pz, nb.d2, nb.orig,
+                 nb.pos);
       } else {
-        scan_run(g.pts, g.cell_start[col + zl], g.cell_start[col + zh + 1], px, py, pz, best_d2, best_orig, best);
+        scan_run(g.pts, g.cell_start[col + zl], g.cell_start[col + zh + 1], px, py, pz, nb.d2, nb.orig, nb.pos);
       }
     }
   }
-  return best;
+}
+
+// Block-wide search with the candidate cells staged in shared memory.  The
+// block's queries are consecutive in Morton order, so the boxes their bounds
+// allow overlap.  The block takes the union of those boxes; if it is small
+// enough, it loads the union's column offsets (one round trip), copies every
+// point of the union into shared memory (one coalesced pass), and then each
+// thread scans exactly its own box there.  This replaces each thread's chain of
+// dependent global loads with two block-wide round trips.  Returns false, with
+// nothing changed, when the union does not fit: the caller then searches from
+// global memory.  All threads of the block must call this.
+constexpr int kStageCols = 64;   // columns of the union box
+constexpr int kStageZ = 15;      // z-cells per column
+constexpr int kStagePts = 2048;  // staged points (32 KB)
+
+struct Stage {
+  float4 pts[kStagePts];
+  uint32_t off[kStageCols][kStageZ + 1];  // global cell_start of each z-cell of each column
+  uint32_t base[kStageCols + 1];          // staged position of each column's first point
+  int box[6];
+  int total;
+};
+
+__device__ bool staged_search(const GridView& g, float cell, float px, float py, float pz, float r, bool live,
+                              Nearest& nb, Stage& S) {
+  const float margin = search_margin(cell, r, px, py, pz);
+  const float reach = __fadd_rn(fast_sqrt(__fmul_rn(nb.d2, 1.0001f)), margin);
+  int ax = 0, bx = -1, ay = 0, by = -1, az = 0, bz = -1;
+  if (live) {
+    axis_range(px, reach, g.inv_cell, g.lo_x, g.sx, ax, bx);
+    axis_range(py, reach, g.inv_cell, g.lo_y, g.sy, ay, by);
+    axis_range(pz, reach, g.inv_cell, g.lo_z, g.sz, az, bz);
+  }
+  const bool any = ax <= bx && ay <= by && az <= bz;
+  const unsigned full = 0xffffffffu;
+  if (threadIdx.x < 3) S.box[threadIdx.x] = 0x7fffffff;
+  else if (threadIdx.x < 6) S.box[threadIdx.x] = -1;
+  __syncthreads();
+  {
+    const int lx = __reduce_min_sync(full, any ? ax : 0x7fffffff), ly = __reduce_min_sync(full, any ? ay : 0x7fffffff);
+    const int lz = __reduce_min_sync(full, any ? az : 0x7fffffff);
+    const int ux = __reduce_max_sync(full, any ? bx : -1), uy = __reduce_max_sync(full, any ? by : -1);
+    const int uz = __reduce_max_sync(full, any ? bz : -1);
+    if ((threadIdx.x & 31) == 0 && ux >= 0) {
+      atomicMin(&S.box[0], lx);
+      atomicMin(&S.box[1], ly);
+      atomicMin(&S.box[2], lz);
+      atomicMax(&S.box[3], ux);
+      atomicMax(&S.box[4], uy);
+      atomicMax(&S.box[5], uz);
+    }
+  }
+  __syncthreads();
+  const int AX = S.box[0], AY = S.box[1], AZ = S.box[2], BX = S.box[3], BY = S.box[4], BZ = S.box[5];
+  if (BX < 0) return true;  // no query of the block can have a candidate
+  const int NCY = BY - AY + 1, NCZ = BZ - AZ + 1;
+  const int ncol = (BX - AX + 1) * NCY;
+  if (ncol > kStageCols || NCZ > kStageZ) return false;
+  // column offsets (all loads independent)
+  for (int t = threadIdx.x; t < ncol; t += blockDim.x) {
+    const int col = ((AX + t / NCY) * g.sy + (AY + t % NCY)) * g.sz + AZ;
+    for (int z = 0; z <= NCZ; ++z) S.off[t][z] = g.cell_start[col + z];
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {  // exclusive scan of the column lengths (ncol <= 64: two per lane)
+    const int t0 = 2 * threadIdx.x, t1 = t0 + 1;
+    const uint32_t l0 = t0 < ncol ? S.off[t0][NCZ] - S.off[t0][0] : 0u;
+    const uint32_t l1 = t1 < ncol ? S.off[t1][NCZ] - S.off[t1][0] : 0u;
+    uint32_t inc = l0 + l1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(full, inc, o);
+      if (threadIdx.x >= o) inc += y;
+    }
+    const uint32_t ex = inc - (l0 + l1);
+    if (t0 <= ncol) S.base[t0] = ex;
+    if (t1 <= ncol) S.base[t1] = ex + l0;
+    if (threadIdx.x == 31) S.total = static_cast<int>(inc);
+  }
+  __syncthreads();
+  const int M = S.total;
+  if (M > kStagePts) return false;
+  for (int m = threadIdx.x; m < M; m += blockDim.x) {
+    int lo = 0, hi = ncol - 1;  // column holding staged position m: last t with base[t] <= m
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (static_cast<int>(S.base[mid]) <= m) lo = mid;
+      else hi = mid - 1;
+    }
+    S.pts[m] = g.pts[S.off[lo][0] + (m - static_cast<int>(S.base[lo]))];
+  }
+  __syncthreads();
+  if (!any) return true;
+  for (int x = ax; x <= bx; ++x) {
+    const float gx = slab_gap(px, x + g.lo_x, cell, margin);
+    for (int y = ay; y <= by; ++y) {
+      const float gy = slab_gap(py, y + g.lo_y, cell, margin);
+      const float lim = __fmul_rn(nb.d2, 1.0001f) - (gx * gx + gy * gy);
+      if (lim < 0.f) continue;
+      const float rz = __fadd_rn(fast_sqrt(lim), margin);
+      const int zl = max(az, cell_coord(__fsub_rn(pz, rz), g.inv_cell) - g.lo_z);
+      const int zh = min(bz, cell_coord(__fadd_rn(pz, rz), g.inv_cell) - g.lo_z);
+      if (zl > zh) continue;
+      const int t = (x - AX) * NCY + (y - AY);
+      const uint32_t o0 = S.off[t][0];
+      const int shift = static_cast<int>(S.base[t]) - static_cast<int>(o0);
+      const uint32_t gb = S.off[t][zl - AZ], ge = S.off[t][zh + 1 - AZ];
+      for (uint32_t k = gb; k < ge; ++k) consider(nb, S.pts[static_cast<int>(k) + shift], static_cast<int>(k), px, py, pz);
+    }
+  }
+  return true;
 }
 
 // Error-free transformation: s + e == a + b exactly.
@@ -149,61 +307,51 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-struct CompSum {
-  float s[kNSum];
-  float c[kNSum];
-  __device__ void zero() {
-#pragma unroll
-    for (int k = 0; k < kNSum; ++k) s[k] = c[k] = 0.f;
-  }
-  __device__ __forceinline__ void add(int k, float v) {
-    float e;
-    two_sum(s[k], v, s[k], e);
-    c[k] += e;
-  }
-};
 
-// Block reduction of the compensated sums (fixed shuffle tree, then warps in
-// order) into one float64 partial: [0..28] = sums, [29] = |C|.
-__device__ void block_reduce_store(CompSum& acc, int cnt, double* __restrict__ out) {
-  __shared__ float ws[kThreads / 32][kNSum];
-  __shared__ float wc[kThreads / 32][kNSum];
-  __shared__ int wn[kThreads / 32];
+// Compensated value pairs: the exact value is s + c.
+__device__ __forceinline__ void add_pair(float& s, float& c, float s2, float c2) {
+  float e;
+  two_sum(s, s2, s, e);
+  c = c + c2 + e;
+}
+
+// Block reduction of 32 compensated values per thread (29 sums, |C| as a float
+// count below 2^24 per block, two zeros) into one float64 partial per block.
+// Within a warp, a butterfly reduce-scatter: at each of 5 steps every lane keeps
+// half of its values, sends the other half to its partner and adds what it
+// receives, so lane j ends with the warp total of value j after 31 exchanges
+// (instead of 32 x 5 for a tree per value).  Warps are then combined in order.
+// Every step is a fixed sequence, so the result does not depend on timing.
+__device__ void block_reduce_store(float (&v)[32], float (&c)[32], double* __restrict__ out) {
+  __shared__ float ws[kThreads / 32][32];
+  __shared__ float wc[kThreads / 32][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < kNSum; ++k) {
-    float s = acc.s[k], c = acc.c[k];
+  for (int half = 16; half >= 1; half >>= 1) {
+    const bool upper = (lane & half) != 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      float s2 = __shfl_down_sync(0xffffffffu, s, o);
-      float c2 = __shfl_down_sync(0xffffffffu, c, o);
-      float e;
-      two_sum(s, s2, s, e);
-      c = c + c2 + e;
-    }
-    if (lane == 0) {
-      ws[warp][k] = s;
-      wc[warp][k] = c;
+    for (int j = 0; j < half; ++j) {
+      const float send_s = upper ? v[j] : v[j + half];
+      const float send_c = upper ? c[j] : c[j + half];
+      const float keep_s = upper ? v[j + half] : v[j];
+      const float keep_c = upper ? c[j + half] : c[j];
+      const float rs = __shfl_xor_sync(0xffffffffu, send_s, half);
+      const float rc = __shfl_xor_sync(0xffffffffu, send_c, half);
+      float s = keep_s, cc = keep_c;
+      add_pair(s, cc, rs, rc);
+      v[j] = s;
+      c[j] = cc;
     }
   }
-  cnt = __reduce_add_sync(0xffffffffu, cnt);
-  if (lane == 0) wn[warp] = cnt;
+  // lane j holds the warp total of value j (bits of j select the kept halves)
+  ws[warp][lane] = v[0];
+  wc[warp][lane] = c[0];
   __syncthreads();
   const int t = threadIdx.x;
-  if (t < kNSum) {
-    float s = ws[0][t], c = wc[0][t];
-    for (int w = 1; w < kThreads / 32; ++w) {
-      float e;
-      two_sum(s, ws[w][t], s, e);
-      c = c + wc[w][t] + e;
-    }
-    out[t] = static_cast<double>(s) + static_cast<double>(c);
-  } else if (t == kNSum) {
-    int n = 0;
-    for (int w = 0; w < kThreads / 32; ++w) n += wn[w];
-    out[t] = static_cast<double>(n);
-  } else if (t < kPartial) {
-    out[t] = 0.0;
+  if (t < kPartial) {
+    float s = ws[0][t], cc = wc[0][t];
+    for (int w = 1; w < kThreads / 32; ++w) add_pair(s, cc, ws[w][t], wc[w][t]);
+    out[t] = static_cast<double>(s) + static_cast<double>(cc);
   }
 }
 
@@ -234,109 +382,116 @@ __device__ __forceinline__ void sincos_step(double x, double* s, double* c) {
   *c = 1.0 - x2 * pc;
 }
 
+// 1 / d for d > 0: a float32 seed refined by two Newton steps x <- x (2 - d x)
+// (relative error ~1e-7 -> ~1e-14 -> below double rounding), much shorter on
+// this GPU than the full float64 division; outside the float32 range, division.
+__device__ __forceinline__ double recip(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;
+  double x = static_cast<double>(__frcp_rn(static_cast<float>(d)));
+  x = x * fma(-d, x, 2.0);
+  x = x * fma(-d, x, 2.0);
+  return x;
+}
+
 // Float64 sums of `count` partials of kPartial doubles each (rows `first`,
-// `first + 1`, ...), in row order: 128 threads = 32 columns x 4 interleaved
-// row subsets, combined in subset order.  Result in out[0..kPartial).
+// `first + 1`, ...), in row order: 128 threads = 32 columns x 4 interleaved row
+// subsets, combined in subset order.  Rows are taken 32 at a time and the 8
+// loads of a thread in each batch are issued before its first add, so the L2
+// latency is paid once per batch.  Result in out[0..kPartial).
 __device__ void sum_partials(const double* __restrict__ rows, int first, int count, double* out) {
   __shared__ double sub[4][kPartial];
   const int col = threadIdx.x & 31, q = threadIdx.x >> 5;
   double acc = 0.0;
-  for (int b = q; b < count; b += 4) acc += __ldcg(rows + static_cast<size_t>(first + b) * kPartial + col);
+  for (int b0 = 0; b0 < count; b0 += 32) {
+    double val[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int b = b0 + q + 4 * j;
+      val[j] = b < count ? __ldcg(rows + static_cast<size_t>(first + b) * kPartial + col) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc += val[j];
+  }
   sub[q][col] = acc;
   __syncthreads();
   if (threadIdx.x < kPartial) out[col] = ((sub[0][col] + sub[1][col]) + sub[2][col]) + sub[3][col];
   __syncthreads();
 }
 
-// The Gauss-Newton update on one warp, all in float64: LDL^T of the 6x6
-// (right-looking, no pivoting; a pivot <= 1e-12 * max_j A_jj freezes its
-// unknown: xi_k = 0 and no elimination through it), xi = -(A)^-1 b by forward
-// and back substitution, dR = Rz(gamma) Ry(beta) Rx(alpha), T <- [dR, t] T.
+__device__ __forceinline__ double shfl_d(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+// Entry (i, j) of the symmetric 6x6 from the 21 upper-triangle sums (row-major order).
+__device__ __forceinline__ double sym6(const double* sums, int i, int j) {
+  const int a = i < j ? i : j, c = i < j ? j : i;
+  return sums[a * 6 - (a * (a - 1)) / 2 + (c - a)];
+}
+
+// The Gauss-Newton update on one warp, in float64 (Eq. 2): Gauss-Jordan
+// elimination without pivoting on [A | -b], lane j holding column j in
+// registers.  Its pivots are the Schur complements an LDL^T factorisation
+// produces, so the frozen-pivot rule is the same: a pivot <= 1e-12 * max_j A_jj
+// eliminates nothing and its unknown is 0.  Then dR = Rz(gamma) Ry(beta)
+// Rx(alpha) and T <- [dR, t] T, spread over lanes.
 __device__ void solve_update(const double* sums, IcpState* __restrict__ st, double eps) {
-  __shared__ double M[6][6];
-  __shared__ double inv[6], xi[6], sn[3], cs[3], dR[9], Tn[12];
-  __shared__ int frozen_any;
-  const int lane = threadIdx.x;  // called by warp 0 only
-  // unpack the upper triangle (row-major order of the 21 sums)
-  if (lane < 21) {
-    int a = 0, k = lane;
-    while (k >= 6 - a) {
-      k -= 6 - a;
-      ++a;
-    }
-    const int c = a + k;
-    M[a][c] = sums[lane];
-    M[c][a] = sums[lane];
-  }
-  if (lane == 0) frozen_any = 0;
-  __syncwarp();
-  double mx = M[0][0];
-  for (int j = 1; j < 6; ++j) mx = fmax(mx, M[j][j]);
+  const int lane = threadIdx.x & 31;
+  const double Tpre = lane < 12 ? st->T[lane] : 0.0;  // pose rows 0..2, fetched early
+  double a[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) a[i] = lane < 6 ? sym6(sums, i, lane) : (lane == 6 ? -sums[21 + i] : 0.0);
+  double mx = sums[0];
+#pragma unroll
+  for (int j = 1; j < 6; ++j) mx = fmax(mx, sym6(sums, j, j));
   const double thr = 1e-12 * mx;
+  double inv[6];
+  bool frozen_any = false;
+#pragma unroll
   for (int k = 0; k < 6; ++k) {
-    const double d = M[k][k];
-    const bool fz = !(d > thr);
-    if (lane == 0) {
-      inv[k] = fz ? 0.0 : 1.0 / d;
-      if (fz) frozen_any = 1;
-    }
-    __syncwarp();
-    const double ik = inv[k];
-    // column k of L, then the trailing update, lanes over the lower triangle of rows/cols > k
-    if (lane > k && lane < 6) M[lane][k] = M[lane][k] * ik;
-    __syncwarp();
-    const int m = 5 - k;  // trailing size
-    if (!fz && lane < m * m) {
-      const int i = k + 1 + lane / m, j = k + 1 + lane % m;
-      if (j <= i) M[i][j] -= M[i][k] * d * M[j][k];
-    }
-    __syncwarp();
-  }
-  if (lane == 0) {
-    double y[6];
-    for (int i = 0; i < 6; ++i) {
-      double v = -sums[21 + i];
-      for (int m = 0; m < i; ++m) v -= M[i][m] * y[m];
-      y[i] = v;
-    }
-    for (int i = 5; i >= 0; --i) {
-      double v = y[i] * inv[i];
-      for (int m = i + 1; m < 6; ++m) v -= M[m][i] * xi[m];
-      xi[i] = v;
+    const double piv = shfl_d(a[k], k);
+    const bool fz = !(piv > thr);
+    frozen_any = frozen_any || fz;
+    const double ik = fz ? 0.0 : recip(piv);
+    inv[k] = ik;
+    double colk[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) colk[i] = shfl_d(a[i], k);
+    const double rk = a[k];
+    if (!fz) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+        if (i != k) a[i] = fma(-colk[i] * ik, rk, a[i]);
     }
   }
-  __syncwarp();
-  if (lane < 3) sincos_step(xi[lane], &sn[lane], &cs[lane]);
-  __syncwarp();
-  if (lane < 9) {
-    const double sa = sn[0], ca = cs[0], sb = sn[1], cb = cs[1], sg = sn[2], cg = cs[2];
-    double v;
-    switch (lane) {
-      case 0: v = cg * cb; break;
-      case 1: v = cg * sb * sa - sg * ca; break;
-      case 2: v = cg * sb * ca + sg * sa; break;
-      case 3: v = sg * cb; break;
-      case 4: v = sg * sb * sa + cg * ca; break;
-      case 5: v = sg * sb * ca - cg * sa; break;
-      case 6: v = -sb; break;
-      case 7: v = cb * sa; break;
-      default: v = cb * ca; break;
-    }
-    dR[lane] = v;
+  // lane 6 holds the reduced right-hand side; x_k = rhs_k / pivot_k (0 when frozen)
+  double xi[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) xi[i] = shfl_d(a[i] * inv[i], 6);
+  double sn = 0.0, cs = 1.0;
+  if (lane < 3) sincos_step(lane == 0 ? xi[0] : (lane == 1 ? xi[1] : xi[2]), &sn, &cs);
+  const double sa = shfl_d(sn, 0), ca = shfl_d(cs, 0), sb = shfl_d(sn, 1), cb = shfl_d(cs, 1);
+  const double sg = shfl_d(sn, 2), cg = shfl_d(cs, 2);
+  // row r of dR for lanes 4r .. 4r+3, column c = lane % 4 of T
+  const int r = (lane >> 2) < 3 ? (lane >> 2) : 0, c = lane & 3;
+  double d0, d1, d2;
+  if (r == 0) {
+    d0 = cg * cb;
+    d1 = cg * sb * sa - sg * ca;
+    d2 = cg * sb * ca + sg * sa;
+  } else if (r == 1) {
+    d0 = sg * cb;
+    d1 = sg * sb * sa + cg * ca;
+    d2 = sg * sb * ca - cg * sa;
+  } else {
+    d0 = -sb;
+    d1 = cb * sa;
+    d2 = cb * ca;
   }
-  __syncwarp();
+  const double t0 = shfl_d(Tpre, c), t1 = shfl_d(Tpre, 4 + c), t2 = shfl_d(Tpre, 8 + c);
+  double tn = d0 * t0 + d1 * t1 + d2 * t2;
+  if (c == 3) tn += r == 0 ? xi[3] : (r == 1 ? xi[4] : xi[5]);
   if (lane < 12) {
-    const int r = lane / 4, c = lane % 4;
-    double v = dR[3 * r + 0] * st->T[c] + dR[3 * r + 1] * st->T[4 + c] + dR[3 * r + 2] * st->T[8 + c];
-    if (c == 3) v += xi[3 + r];
-    Tn[lane] = v;
-  }
-  __syncwarp();
-  if (lane < 12) {
-    st->T[lane] = Tn[lane];
-    const int r = lane / 4, c = lane % 4;
-    if (c < 3) st->R[3 * r + c] = __double2float_rn(Tn[lane]);
-    else st->t[r] = __double2float_rn(Tn[lane]);
+    st->T[lane] = tn;
+    if (c < 3) st->R[3 * r + c] = __double2float_rn(tn);
+    else st->t[r] = __double2float_rn(tn);
   }
   if (lane == 0) {
     if (frozen_any) st->degenerate = 1;
@@ -363,33 +518,23 @@ __device__ void finish(const double* __restrict__ gsums, int ngroups, IcpState* 
     }
     return;
   }
-  if (threadIdx.x == 0) {
-    bool finite = true;
-    for (int k = 0; k < 27; ++k) finite = finite && isfinite(sums[k]);
-    int k = 0;
-    for (int a = 0; a < 6; ++a)
-      for (int c = a; c < 6; ++c) {
-        st->A[6 * a + c] = sums[k];
-        st->A[6 * c + a] = sums[k];
-        ++k;
-      }
-    for (int a = 0; a < 6; ++a) st->b[a] = sums[21 + a];
-    st->stats[0] = sums[27];
-    st->stats[1] = sums[28];
-    st->stats[2] = count;
-    if (mode == kIterate) {
-      if (!finite) {
-        st->nonfinite = 1;
-        st->done = 1;
-      } else if (count < 6.0) {
-        st->few_corr = 1;
-        st->done = 1;
-      }
-    }
+  if (mode == kEquations) {
+    const int t = threadIdx.x;
+    if (t < 36) st->A[t] = sym6(sums, t / 6, t % 6);
+    else if (t < 42) st->b[t - 36] = sums[21 + (t - 36)];
+    else if (t < 45) st->stats[t - 42] = sums[27 + (t - 42)];
+    return;
   }
-  if (mode != kIterate) return;
-  __syncthreads();
-  if (st->done || threadIdx.x >= 32) return;
+  if (threadIdx.x >= 32) return;
+  const bool bad = __any_sync(0xffffffffu, threadIdx.x < 27 && !isfinite(sums[threadIdx.x]));
+  if (bad || count < 6.0) {
+    if (threadIdx.x == 0) {
+      if (bad) st->nonfinite = 1;
+      else st->few_corr = 1;
+      st->done = 1;
+    }
+    return;
+  }
   solve_update(sums, st, eps);
 }
 
@@ -400,7 +545,8 @@ __global__ void __launch_bounds__(kThreads) k_icp_iter(GridView g, float cell, c
                                                        int ns, IcpState* __restrict__ st, float r,
                                                        double* __restrict__ partials, double* __restrict__ gsums,
                                                        unsigned* __restrict__ group_cnt, double eps, int mode,
-                                                       int32_t* __restrict__ corr_out, float* __restrict__ d2_out) {
+                                                       int32_t* __restrict__ corr_out, float* __restrict__ d2_out,
+                                                       int32_t* __restrict__ hints) {
   if (mode == kIterate && st->done) return;
   float R[9], t[3];
 #pragma unroll
@@ -408,25 +554,30 @@ __global__ void __launch_bounds__(kThreads) k_icp_iter(GridView g, float cell, c
 #pragma unroll
   for (int k = 0; k < 3; ++k) t[k] = st->t[k];
   const float r2 = __fmul_rn(r, r);
-  CompSum acc;
-  acc.zero();
-  int cnt = 0;
-  const int base = blockIdx.x * kThreads * kPPT + threadIdx.x;
+  float v[32], c[32];
 #pragma unroll
-  for (int j = 0; j < kPPT; ++j) {
-    const int i = base + j * kThreads;
-    if (i >= ns) break;
-    const float4 s = src4[i];
-    const float3 p = xform_rn(R, t, s.x, s.y, s.z);
-    float bd2;
-    const int bp = nn_search(g, cell, p.x, p.y, p.z, r, r2, bd2);
+  for (int k = 0; k < 32; ++k) v[k] = c[k] = 0.f;
+  const int i = blockIdx.x * kThreads + threadIdx.x;
+  // every lane runs the search (lanes past the end on a far-away dummy point) so
+  // that the warp-wide exchange of first candidates is convergent
+  const bool live = i < ns;
+  const float4 s = live ? src4[i] : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
+  const float3 p = live ? xform_rn(R, t, s.x, s.y, s.z) : make_float3(3.0e38f, 3.0e38f, 3.0e38f);
+  const int hint = (hints && live) ? hints[i] : -1;
+  __shared__ Stage stage;
+  Nearest nb{r2, 0x7fffffff, -1};
+  first_bound(g, p.x, p.y, p.z, hint, nb);
+  if (!staged_search(g, cell, p.x, p.y, p.z, r, live, nb, stage) && live)
+    box_search_global(g, cell, p.x, p.y, p.z, r, nb);
+  const float bd2 = nb.d2;
+  if (live) {
+    const int bp = nb.pos;
+    if (hints) hints[i] = bp;
     if (mode == kCorrOnly) {
       const int o = __float_as_int(s.w);
       corr_out[o] = bp >= 0 ? __float_as_int(g.pts[bp].w) : -1;
       d2_out[o] = bp >= 0 ? bd2 : 0.f;
-      continue;
-    }
-    if (bp >= 0) {
+    } else if (bp >= 0) {
       const float4 q = g.pts[bp];
       const float4 n = g.nrm[bp];
       const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
@@ -442,23 +593,23 @@ __global__ void __launch_bounds__(kThreads) k_icp_iter(GridView g, float cell, c
 #pragma unroll
       for (int a = 0; a < 6; ++a)
 #pragma unroll
-        for (int b = a; b < 6; ++b) acc.add(k++, J[a] * J[b]);
+        for (int b = a; b < 6; ++b) v[k++] = J[a] * J[b];
 #pragma unroll
-      for (int a = 0; a < 6; ++a) acc.add(21 + a, J[a] * res);
-      acc.add(27, res * res);
-      acc.add(28, bd2);
-      ++cnt;
+      for (int a = 0; a < 6; ++a) v[21 + a] = J[a] * res;
+      v[27] = res * res;
+      v[28] = bd2;
+      v[29] = 1.f;
     }
   }
   if (mode == kCorrOnly) return;
-  block_reduce_store(acc, cnt, partials + static_cast<size_t>(blockIdx.x) * kPartial);
+  block_reduce_store(v, c, partials + static_cast<size_t>(blockIdx.x) * kPartial);
   // The last block of each group of kGroup blocks sums the group (float64, block
   // order); the last group to finish sums the groups and finishes the launch.
   __shared__ bool last;
   const int grp = blockIdx.x / kGroup;
   const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
   const int in_group = min(kGroup, static_cast<int>(gridDim.x) - grp * kGroup);
-  __threadfence();
+  if (threadIdx.x < kPartial) __threadfence();  // the threads that stored the partial publish it
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(&group_cnt[grp], 1u) == static_cast<unsigned>(in_group - 1);
   __syncthreads();
@@ -466,9 +617,11 @@ __global__ void __launch_bounds__(kThreads) k_icp_iter(GridView g, float cell, c
   __threadfence();
   __shared__ double gsum[kPartial];
   sum_partials(partials, grp * kGroup, in_group, gsum);
-  if (threadIdx.x < kPartial) gsums[static_cast<size_t>(grp) * kPartial + threadIdx.x] = gsum[threadIdx.x];
+  if (threadIdx.x < kPartial) {
+    gsums[static_cast<size_t>(grp) * kPartial + threadIdx.x] = gsum[threadIdx.x];
+    __threadfence();
+  }
   if (threadIdx.x == 0) group_cnt[grp] = 0u;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(&st->arrived, 1u) == static_cast<unsigned>(ngroups - 1);
   __syncthreads();
@@ -510,8 +663,9 @@ struct Work {
   DevBuf state;
   DevBuf partials;  // nblk block partials, then ngroups group sums
   DevBuf counters;  // ngroups arrival counters
+  DevBuf hints;     // per source point: sorted target position of its last match, or -1
   int nblk = 1, ngroups = 1;
-  explicit Work(cudaStream_t s) : src(s), state(s), partials(s), counters(s) {}
+  explicit Work(cudaStream_t s) : src(s), state(s), partials(s), counters(s), hints(s) {}
   int32_t prepare(const float* d_src, int64_t ns, int32_t stride, float cell, const double* T, cudaStream_t s) {
     O3G_TRY_STATUS(sort_cloud(d_src, ns, stride, s, &src));
     nblk = iter_blocks(ns);
@@ -520,6 +674,8 @@ struct Work {
     O3G_TRY(partials.alloc(sizeof(double) * kPartial * (nblk + ngroups)));
     O3G_TRY(counters.alloc(sizeof(unsigned) * ngroups));
     O3G_TRY(cudaMemsetAsync(counters.p, 0, sizeof(unsigned) * ngroups, s));
+    O3G_TRY(hints.alloc(sizeof(int32_t) * (ns > 0 ? ns : 1)));
+    O3G_TRY(cudaMemsetAsync(hints.p, 0xff, sizeof(int32_t) * (ns > 0 ? ns : 1), s));
     k_init_state<<<1, 32, 0, s>>>(state.as<IcpState>(), to_pose(T));
     count_launch();
     return O3G_OK;
@@ -529,7 +685,8 @@ struct Work {
     double* pp = partials.as<double>();
     k_icp_iter<<<nblk, kThreads, 0, s>>>(g->view(), g->cell, src.pts, ns, state.as<IcpState>(), r, pp,
                                          pp + static_cast<size_t>(kPartial) * nblk, counters.as<unsigned>(), eps,
-                                         mode, corr, d2);
+                                         mode, corr, d2,
+                                         (mode == kIterate || mode == kEvaluate) ? hints.as<int32_t>() : nullptr);
     count_launch();
     return O3G_OK;
   }
@@ -666,7 +823,7 @@ extern "C" int32_t o3g_icp_point_to_plane(const float* d_src, int64_t ns, int32_
     return O3G_ERR_ARG;
   }
   o3g_grid* g = nullptr;
-  O3G_TRY_STATUS(o3g_build_grid(d_tgt, nt, tgt_stride, static_cast<float>(max_corr_dist), nullptr, &g));
+  O3G_TRY_STATUS(o3g_build_grid(d_tgt, nt, tgt_stride, static_cast<float>(max_corr_dist * 1.002), nullptr, &g));
   int32_t st = o3g_grid_set_normals(g, d_tgt_nrm, n_nrm, nrm_stride, nullptr);
   if (st >= 0)
     st = icp_run(g, d_src, ns, src_stride, init_T, max_corr_dist, max_iter, 0.0, out_T, out_fitness, out_rmse, nullptr,
@@ -786,7 +943,7 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const 
   for (int it = 0; it <= max_iter; ++it) {
     const int mode = it < max_iter ? kIterate : kEvaluate;
     k_icp_iter<<<nblk, kThreads, 0, s>>>(gv, g->cell, src4, n, st, r, partials, gsums, counters, eps, mode, nullptr,
-                                         nullptr);
+                                         nullptr, nullptr);
     count_launch();
   }
   O3G_TRY(cudaGetLastError());

@@ -33,8 +33,10 @@ __device__ int knn_select(const GridView& g, float qx, float qy, float qz, float
   if (az > bz) return 0;
   for (int x = ax; x <= bx; ++x) {
     for (int y = ay; y <= by; ++y) {
+      int zl = az, zh = bz;
+      if (!column_z(g, x * g.sy + y, zl, zh)) continue;
       const int col = (x * g.sy + y) * g.sz;
-      const uint32_t beg = g.cell_start[col + az], end = g.cell_start[col + bz + 1];
+      const uint32_t beg = g.cell_start[col + zl], end = g.cell_start[col + zh + 1];
       for (uint32_t k = beg; k < end; ++k) {
         const float4 q = g.pts[k];
         const float d2 = dist2_rn(qx, qy, qz, q);
@@ -211,8 +213,10 @@ __device__ uint64_t warp_knn(const GridView& g, float qx, float qy, float qz, fl
   if (ax > bx || ay > by || az > bz) return list;
   for (int x = ax; x <= bx; ++x) {
     for (int y = ay; y <= by; ++y) {
+      int zl = az, zh = bz;
+      if (!column_z(g, x * g.sy + y, zl, zh)) continue;
       const int col = (x * g.sy + y) * g.sz;
-      const uint32_t beg = g.cell_start[col + az], end = g.cell_start[col + bz + 1];
+      const uint32_t beg = g.cell_start[col + zl], end = g.cell_start[col + zh + 1];
       for (uint32_t k0 = beg; k0 < end; k0 += 32) {
         const uint32_t k = k0 + lane;
         uint64_t key = kNoKey;

@@ -89,6 +89,7 @@ struct GridView {
   const float4* pts;         // sorted points; .w holds the original index (int bits)
   const float4* nrm;         // sorted normals (.w = 0), or null
   const uint32_t* cell_start;  // cells + 1 entries
+  const uint32_t* col_z;     // per (x, y) column: lowest | highest occupied z cell << 16 (empty: 0xffff)
   int lo_x, lo_y, lo_z;      // smallest occupied cell coordinate per axis
   int sx, sy, sz;            // cell span per axis
   float inv_cell;
@@ -110,6 +111,14 @@ __device__ __forceinline__ void axis_range(float p, float r, float inv_cell, int
   float m = __fadd_rn(__fmul_rn(r, 1.0001f), __fmul_rn(fabsf(p), 1e-6f));
   a = max(cell_coord(__fsub_rn(p, m), inv_cell) - lo, 0);
   b = min(cell_coord(__fadd_rn(p, m), inv_cell) - lo, span - 1);
+}
+
+// Narrows [zl, zh] to the occupied z-cells of column col_xy; false if none remain.
+__device__ __forceinline__ bool column_z(const GridView& g, int col_xy, int& zl, int& zh) {
+  const uint32_t e = g.col_z[col_xy];
+  zl = max(zl, static_cast<int>(e & 0xffffu));
+  zh = min(zh, static_cast<int>(e >> 16));
+  return zl <= zh;
 }
 
 // d2 = (dx*dx + dy*dy) + dz*dz with d = p - q, every operation rounded on its own.
@@ -149,6 +158,7 @@ struct o3g_grid {
   float4* pts = nullptr;
   float4* nrm = nullptr;
   uint32_t* cell_start = nullptr;
+  uint32_t* col_z = nullptr;  // per column: lowest | highest occupied z cell << 16
   int32_t* pos_of = nullptr;  // original index -> sorted position
   bool has_normals = false;
   cudaStream_t stream = nullptr;
@@ -158,6 +168,7 @@ struct o3g_grid {
     v.pts = pts;
     v.nrm = has_normals ? nrm : nullptr;
     v.cell_start = cell_start;
+    v.col_z = col_z;
     v.lo_x = lo[0];
     v.lo_y = lo[1];
     v.lo_z = lo[2];

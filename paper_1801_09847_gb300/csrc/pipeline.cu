@@ -27,7 +27,7 @@ extern "C" int32_t o3g_register_point_to_plane_host(const float* h_src, int64_t 
   if (ns > 0) O3G_TRY(cudaMemcpyAsync(src.p, h_src, sizeof(float) * 3 * ns, cudaMemcpyHostToDevice, s));
   if (nt > 0) O3G_TRY(cudaMemcpyAsync(tgt.p, h_tgt, sizeof(float) * 3 * nt, cudaMemcpyHostToDevice, s));
   o3g_grid* g = nullptr;
-  O3G_TRY_STATUS(o3g_build_grid(tgt.as<float>(), nt, 3, static_cast<float>(max_corr_dist), stream, &g));
+  O3G_TRY_STATUS(o3g_build_grid(tgt.as<float>(), nt, 3, static_cast<float>(max_corr_dist * 1.002), stream, &g));
   int32_t st;
   if (h_tgt_nrm) {
     cudaError_t e = nrm.alloc(sizeof(float) * 3 * (nt > 0 ? nt : 1));

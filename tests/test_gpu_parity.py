@@ -59,6 +59,8 @@ def tie_cloud(g, n, lo=-1.0, hi=1.0, quant=None):
 # ------------------------------------------------------------ correspondences
 
 
+# cell factors cover every search variant: window W = 1 (2.0, 1.002), W = 2 (1.0, 0.501),
+# W = 3 (0.5, 0.334) and the generic search (0.3)
 @pytest.mark.parametrize("ns,nt,r,cell_factor,quant", [
     (1, 1, 0.3, 1.0, None),
     (1000, 3000, 0.1, 1.0, None),
@@ -66,6 +68,9 @@ def tie_cloud(g, n, lo=-1.0, hi=1.0, quant=None):
     (4097, 4096, 0.05, 2.0, None),
     (777, 5001, 0.2, 0.3, 0.05),
     (513, 20000, 0.03, 1.0, None),
+    (3001, 6000, 0.08, 1.002, 0.02),
+    (2500, 6000, 0.08, 0.501, 0.02),
+    (1999, 6000, 0.08, 0.334, 0.02),
 ])
 def test_correspondences_bitexact_random(o3g, ns, nt, r, cell_factor, quant):
     g = synth.rng(1000 + ns)
@@ -95,9 +100,10 @@ def room():
     return synth.room_frame_pair()
 
 
-def test_correspondences_room_frame_full_size_sampled(o3g, room):
+@pytest.mark.parametrize("cell_factor", [1.0, 0.501, 1.002])
+def test_correspondences_room_frame_full_size_sampled(o3g, room, cell_factor):
     """The RGB-D-frame pair at full size, in the bench's launch configuration; oracle on a sample of sources."""
-    grid = o3g.build_grid(cuda(room.tgt), room.max_corr_dist)
+    grid = o3g.build_grid(cuda(room.tgt), room.max_corr_dist * cell_factor)
     g = synth.rng(3)
     sample = np.sort(g.choice(len(room.src), 3000, replace=False))
     for T in [np.eye(4), room.T_gt, synth.perturbation(g, 1.0, 0.01) @ room.T_gt]:
