@@ -111,6 +111,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def profiled_traffic(kernel_file: str, profile: str):
+    """DRAM bytes per launch from a committed ncu summary, or None if the kernel source changed since."""
+    import hashlib
+    import re
+    try:
+        src = open(os.path.join(ROOT, "paper_1801_09847_gb300", "csrc", kernel_file), "rb").read()
+        txt = open(os.path.join(ROOT, "profiles", profile)).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"source_sha256:\s*([0-9a-f]{16})", txt)
+    m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.]+)", txt)
+    if not m_hash or not m_bytes or hashlib.sha256(src).hexdigest()[:16] != m_hash.group(1):
+        return None
+    return float(m_bytes.group(1))
+
+
 def make_pair(rank: int):
     from paper_1801_09847_gb300 import synth
     return synth.room_frame_pair(seed=2 + rank)
@@ -240,7 +256,9 @@ def run_ours(args, ws, rank, local):
                     "d2h_bytes_per_step": 16 * 8 + 8 + 8 + 4, "ms_per_step": e2e_ms / args.steps},
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_icp_corr",
+                         "frac": achieved / peak,
+                         "traffic": profiled_traffic("icp.cu", "k_icp_iter_room_frame_bench.md"),
+                         "kernel": "k_icp_iter",
                          "peak_source": which, "launches_timed": corr_n,
                          "avg_launch_us": avg_s * 1e6, "algorithmic_bytes_per_launch": alg_bytes},
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
@@ -276,7 +294,7 @@ def cpu_sample_run(pr, n_sample: int, threads: int):
 def cpu_baseline(pr, budget_s: float = 20.0):
     import oracle
     threads = oracle.default_threads()
-    n_sample = 4096
+    n_sample = 49152
     t_nrm, t_icp, pairs = cpu_sample_run(pr, n_sample, threads)
     # the ICP part scales with the sample; the target normals are paid once per pair
     per_pair_s = t_nrm + t_icp * len(pr.src) / n_sample
