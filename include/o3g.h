@@ -188,6 +188,28 @@ O3G_API int32_t o3g_register_point_to_plane_host(const float* h_src, int64_t ns,
                                          void* stream);
 
 /*
+ * Batched point-to-plane ICP: n_pairs independent registrations, each exactly
+ * as o3g_icp_point_to_plane_grid would run it alone (same arithmetic in the same
+ * order, so the same result), advanced together: every iteration is one
+ * persistent kernel launch whose blocks walk the (pair, tile) work items of all
+ * pairs, and each pair stops on its own criterion.  The iteration sequence is
+ * captured once as a CUDA graph and launched.
+ *   tgts[p]                         target grid of pair p, with normals
+ *   d_src[p], ns[p], strides[p]     source cloud of pair p (device pointers)
+ *   init_T                          n_pairs x 16 row-major float64 poses
+ *   max_corr_dist                   n_pairs radii
+ *   out_T (n_pairs x 16), out_fitness, out_rmse, out_iters, out_status (n_pairs each)
+ * All arrays are host memory.  The return value reports the call (an error
+ * leaves every output untouched); out_status[p] holds pair p's status
+ * (O3G_OK, a warning, or O3G_ERR_NONFINITE).  Synchronous.
+ */
+O3G_API int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid* const* tgts, const float* const* d_src,
+                                             const int64_t* ns, const int32_t* strides, const double* init_T,
+                                             const double* max_corr_dist, int32_t max_iter, double eps,
+                                             double* out_T, double* out_fitness, double* out_rmse,
+                                             int32_t* out_iters, int32_t* out_status, void* stream);
+
+/*
  * Allocation-free form of o3g_icp_point_to_plane_grid.  The paper has no
  * counterpart: this entry point exists for callers that must not allocate device
  * memory once they are running - for example a tracking loop that registers

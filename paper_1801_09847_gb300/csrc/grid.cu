@@ -321,10 +321,14 @@ __device__ __forceinline__ int ordered_int(float f) {
 }
 __device__ __forceinline__ float ordered_float(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
 
+__device__ __forceinline__ void k_fbox_init_one(int* aux) {
+  for (int k = 0; k < 3; ++k) aux[k] = INT_MAX;
+  for (int k = 3; k < 6; ++k) aux[k] = INT_MIN;
+  aux[6] = 0;
+}
+
 __global__ void k_fbox_init(int* aux) {
-  if (threadIdx.x < 3) aux[threadIdx.x] = INT_MAX;
-  else if (threadIdx.x < 6) aux[threadIdx.x] = INT_MIN;
-  else if (threadIdx.x == 6) aux[6] = 0;
+  if (threadIdx.x == 0) k_fbox_init_one(aux);
 }
 
 __global__ void __launch_bounds__(kThreads) k_fbox(const float* __restrict__ xyz, int n, int stride,
@@ -369,13 +373,8 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v) {
   return v;
 }
 
-// 30-bit Morton code of the point quantised to 1024 steps per axis of the box.
-__global__ void __launch_bounds__(kThreads) k_morton(const float* __restrict__ xyz, int n, int stride,
-                                                     const int* __restrict__ aux, uint32_t* __restrict__ keys,
-                                                     uint32_t* __restrict__ vals) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float* p = xyz + static_cast<int64_t>(i) * stride;
+// 30-bit Morton code of the point quantised to 1024 steps per axis of the box in aux.
+__device__ __forceinline__ uint32_t morton_of(const float* p, const int* aux) {
   uint32_t q[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -385,7 +384,15 @@ __global__ void __launch_bounds__(kThreads) k_morton(const float* __restrict__ x
     const float u = fminf(fmaxf((p[a] - lo) * (1023.0f / ext), 0.f), 1023.f);  // NaN -> 0
     q[a] = static_cast<uint32_t>(u);
   }
-  keys[i] = spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2);
+  return spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2);
+}
+
+__global__ void __launch_bounds__(kThreads) k_morton(const float* __restrict__ xyz, int n, int stride,
+                                                     const int* __restrict__ aux, uint32_t* __restrict__ keys,
+                                                     uint32_t* __restrict__ vals) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  keys[i] = morton_of(xyz + static_cast<int64_t>(i) * stride, aux);
   vals[i] = static_cast<uint32_t>(i);
 }
 
@@ -399,6 +406,161 @@ __global__ void __launch_bounds__(kThreads) k_gather4(const float* __restrict__ 
 }
 
 }  // namespace
+
+namespace {
+
+// Pair of global point g: last p with offsets[p] <= g (offsets has n_pairs + 1 entries).
+__device__ __forceinline__ int pair_of(const int64_t* __restrict__ offsets, int n_pairs, int64_t g) {
+  int lo = 0, hi = n_pairs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (offsets[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Batch: per point, its pair's bounding box (ordered ints, as k_fbox) and the
+// non-finite flag; aux is n_pairs x 8 ints initialised like k_fbox_init.  A warp
+// whose points all belong to one pair reduces first and updates once.
+__global__ void __launch_bounds__(kThreads) k_bbox_batch(const float* const* __restrict__ ptrs,
+                                                         const int32_t* __restrict__ strides,
+                                                         const int64_t* __restrict__ offsets, int n_pairs,
+                                                         int64_t total, int* __restrict__ aux) {
+  const unsigned full = 0xffffffffu;
+  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < total;
+       base += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t gi = base + threadIdx.x;
+    const bool valid = gi < total;
+    const int p = valid ? pair_of(offsets, n_pairs, gi) : -1;
+    int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
+    int bad = 0;
+    if (valid) {
+      const float* q = ptrs[p] + (gi - offsets[p]) * strides[p];
+      const float v[3] = {q[0], q[1], q[2]};
+      if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) {
+        bad = 1;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) mn[k] = mx[k] = ordered_int(v[k]);
+      }
+    }
+    const int p0 = __shfl_sync(full, p, 0);
+    if (__all_sync(full, p == p0 || p < 0)) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        mn[k] = __reduce_min_sync(full, mn[k]);
+        mx[k] = __reduce_max_sync(full, mx[k]);
+      }
+      bad = __reduce_or_sync(full, bad);
+      if ((threadIdx.x & 31) == 0 && p0 >= 0) {
+        int* a = aux + 8 * p0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if (mn[k] != INT_MAX) atomicMin(a + k, mn[k]);
+          if (mx[k] != INT_MIN) atomicMax(a + 3 + k, mx[k]);
+        }
+        if (bad) atomicOr(a + 6, 1);
+      }
+    } else if (p >= 0) {
+      int* a = aux + 8 * p;
+      if (bad) {
+        atomicOr(a + 6, 1);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          atomicMin(a + k, mn[k]);
+          atomicMax(a + 3 + k, mx[k]);
+        }
+      }
+    }
+  }
+}
+
+__global__ void k_bbox_batch_init(int* aux, int n_pairs) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_pairs; p += gridDim.x * blockDim.x) k_fbox_init_one(aux + 8 * p);
+}
+
+// Batch: Morton key of each point over its own pair's box (as k_morton), value = global index.
+__global__ void __launch_bounds__(kThreads) k_morton_batch(const float* const* __restrict__ ptrs,
+                                                           const int32_t* __restrict__ strides,
+                                                           const int64_t* __restrict__ offsets, int n_pairs,
+                                                           int total, const int* __restrict__ aux,
+                                                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= total) return;
+  const int p = pair_of(offsets, n_pairs, gi);
+  const float* q = ptrs[p] + (gi - offsets[p]) * strides[p];
+  keys[gi] = morton_of(q, aux + 8 * p);
+  vals[gi] = static_cast<uint32_t>(gi);
+}
+
+// Batch: pair id of each (already Morton-sorted) element, for the second stable sort.
+__global__ void __launch_bounds__(kThreads) k_pair_keys(const uint32_t* __restrict__ vals,
+                                                        const int64_t* __restrict__ offsets, int n_pairs, int total,
+                                                        uint32_t* __restrict__ keys) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= total) return;
+  keys[k] = static_cast<uint32_t>(pair_of(offsets, n_pairs, vals[k]));
+}
+
+// Batch: sorted float4 (x, y, z, index within its pair).
+__global__ void __launch_bounds__(kThreads) k_gather4_batch(const float* const* __restrict__ ptrs,
+                                                            const int32_t* __restrict__ strides,
+                                                            const int64_t* __restrict__ offsets, int n_pairs,
+                                                            int total, const uint32_t* __restrict__ perm,
+                                                            float4* __restrict__ pts) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= total) return;
+  const int gi = static_cast<int>(perm[k]);
+  const int p = pair_of(offsets, n_pairs, gi);
+  const int local = gi - static_cast<int>(offsets[p]);
+  const float* q = ptrs[p] + static_cast<int64_t>(local) * strides[p];
+  pts[k] = make_float4(q[0], q[1], q[2], __int_as_float(local));
+}
+
+}  // namespace
+
+// All clouds of a batch sorted at once: the concatenation ordered by (pair,
+// Morton code over the pair's own box, index) - within each pair exactly the
+// order sort_cloud gives that cloud alone (both sorts are stable).  d_ptrs,
+// d_strides, d_offsets are device arrays (n_pairs, n_pairs, n_pairs + 1);
+// aux receives n_pairs x 8 ints (aux[8p + 6] != 0: non-finite coordinate).
+int32_t sort_clouds_batch(const float* const* d_ptrs, const int32_t* d_strides, const int64_t* d_offsets,
+                          int n_pairs, int64_t total64, cudaStream_t s, float4* out, int* aux) {
+  const int total = static_cast<int>(total64);
+  k_bbox_batch_init<<<blocks_for(n_pairs, kThreads), kThreads, 0, s>>>(aux, n_pairs);
+  count_launch();
+  if (total == 0) return O3G_OK;
+  int nb = blocks_for(total, kThreads);
+  if (nb > kNumSMs * 8) nb = kNumSMs * 8;
+  k_bbox_batch<<<nb, kThreads, 0, s>>>(d_ptrs, d_strides, d_offsets, n_pairs, total, aux);
+  DevBuf keys(s), vals(s), tk(s), tv(s);
+  O3G_TRY(keys.alloc(sizeof(uint32_t) * total));
+  O3G_TRY(vals.alloc(sizeof(uint32_t) * total));
+  O3G_TRY(tk.alloc(sizeof(uint32_t) * total));
+  O3G_TRY(tv.alloc(sizeof(uint32_t) * total));
+  k_morton_batch<<<blocks_for(total, kThreads), kThreads, 0, s>>>(d_ptrs, d_strides, d_offsets, n_pairs, total, aux,
+                                                                  keys.as<uint32_t>(), vals.as<uint32_t>());
+  count_launch(2);
+  O3G_TRY(cudaGetLastError());
+  O3G_TRY_STATUS(radix_sort_pairs(keys.as<uint32_t>(), vals.as<uint32_t>(), tk.as<uint32_t>(), tv.as<uint32_t>(),
+                                  total, 30, s));
+  int pair_bits = 0;
+  while ((1 << pair_bits) < n_pairs) ++pair_bits;
+  if (pair_bits > 0) {
+    k_pair_keys<<<blocks_for(total, kThreads), kThreads, 0, s>>>(vals.as<uint32_t>(), d_offsets, n_pairs, total,
+                                                                 keys.as<uint32_t>());
+    count_launch();
+    O3G_TRY_STATUS(radix_sort_pairs(keys.as<uint32_t>(), vals.as<uint32_t>(), tk.as<uint32_t>(), tv.as<uint32_t>(),
+                                    total, pair_bits, s));
+  }
+  k_gather4_batch<<<blocks_for(total, kThreads), kThreads, 0, s>>>(d_ptrs, d_strides, d_offsets, n_pairs, total,
+                                                                   vals.as<uint32_t>(), out);
+  count_launch();
+  O3G_TRY(cudaGetLastError());
+  return O3G_OK;
+}
 
 int32_t sort_cloud(const float* d_xyz, int64_t n64, int32_t stride, cudaStream_t s, SortedCloud* out) {
   const int n = static_cast<int>(n64);

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <vector>
 
 #include "o3g_internal.cuh"
 
@@ -76,6 +77,27 @@ __global__ void k_init_state(IcpState* st, Pose T) {
 __device__ __forceinline__ float fast_sqrt(float x) {
   const float y = fmaxf(x, 1e-30f);
   return y * rsqrtf(y);
+}
+
+// Pose j of poses (n x 16 float64) into state j, as k_init_state.
+__global__ void k_init_states(IcpState* st, const double* __restrict__ poses, int n) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const double* T = poses + 16 * j;
+    IcpState& S = st[j];
+    for (int k = 0; k < 16; ++k) S.T[k] = T[k];
+    for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < 3; ++c) S.R[3 * r + c] = __double2float_rn(T[4 * r + c]);
+      S.t[r] = __double2float_rn(T[4 * r + 3]);
+    }
+    S.iters = 0;
+    S.done = 0;
+    S.degenerate = 0;
+    S.few_corr = 0;
+    S.nonfinite = 0;
+    S.arrived = 0u;
+    S.fitness = 0.0;
+    S.rmse = 0.0;
+  }
 }
 
 // Lower bound (with a rounding margin) of |c - x| over the cell slab
@@ -538,48 +560,60 @@ __device__ void finish(const double* __restrict__ gsums, int ngroups, IcpState* 
   solve_update(sums, st, eps);
 }
 
-// One ICP step over the cell-sorted source src4 (x, y, z, original index).
-// mode kIterate: skipped once st->done is set; otherwise the other modes run
-// regardless.  kCorrOnly writes corr/d2 (by original source index) and no sums.
-__global__ void __launch_bounds__(kThreads) k_icp_iter(GridView g, float cell, const float4* __restrict__ src4,
-                                                       int ns, IcpState* __restrict__ st, float r,
-                                                       double* __restrict__ partials, double* __restrict__ gsums,
-                                                       unsigned* __restrict__ group_cnt, double eps, int mode,
-                                                       int32_t* __restrict__ corr_out, float* __restrict__ d2_out,
-                                                       int32_t* __restrict__ hints) {
-  if (mode == kIterate && st->done) return;
+// Everything one registration problem brings to an iteration launch.
+struct PairDesc {
+  GridView g;
+  float cell, r;
+  const float4* src4;  // cell-sorted source, .w = original index bits
+  int ns;
+  int ntiles;          // ceil(ns / kThreads), at least 1
+  int tile0;           // first global tile of this pair
+  IcpState* st;
+  double* partials;    // ntiles x kPartial
+  double* gsums;       // ceil(ntiles / kGroup) x kPartial
+  unsigned* group_cnt;  // ceil(ntiles / kGroup) arrival counters
+  int32_t* hints;      // per source point: sorted target position of its last match, or -1; may be null
+  int32_t* corr_out;   // kCorrOnly outputs (by original source index)
+  float* d2_out;
+};
+
+// One tile (kThreads cell-sorted source points, tile j of pair P) of one ICP step.
+// mode kIterate: skipped once the pair is done; the other modes always run.
+// kCorrOnly writes corr/d2 and no sums.  The last tile of the pair to finish
+// performs the pair's solve and update (see finish).  Block-uniform control flow.
+__device__ void icp_tile(const PairDesc& P, int j, double eps, int mode, Stage& stage) {
+  if (mode == kIterate && P.st->done) return;
   float R[9], t[3];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) R[k] = st->R[k];
+  for (int k = 0; k < 9; ++k) R[k] = P.st->R[k];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) t[k] = st->t[k];
-  const float r2 = __fmul_rn(r, r);
+  for (int k = 0; k < 3; ++k) t[k] = P.st->t[k];
+  const float r2 = __fmul_rn(P.r, P.r);
   float v[32], c[32];
 #pragma unroll
   for (int k = 0; k < 32; ++k) v[k] = c[k] = 0.f;
-  const int i = blockIdx.x * kThreads + threadIdx.x;
+  const int i = j * kThreads + threadIdx.x;
   // every lane runs the search (lanes past the end on a far-away dummy point) so
   // that the warp-wide exchange of first candidates is convergent
-  const bool live = i < ns;
-  const float4 s = live ? src4[i] : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
+  const bool live = i < P.ns;
+  const float4 s = live ? P.src4[i] : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
   const float3 p = live ? xform_rn(R, t, s.x, s.y, s.z) : make_float3(3.0e38f, 3.0e38f, 3.0e38f);
-  const int hint = (hints && live) ? hints[i] : -1;
-  __shared__ Stage stage;
+  const int hint = (P.hints && live) ? P.hints[i] : -1;
   Nearest nb{r2, 0x7fffffff, -1};
-  first_bound(g, p.x, p.y, p.z, hint, nb);
-  if (!staged_search(g, cell, p.x, p.y, p.z, r, live, nb, stage) && live)
-    box_search_global(g, cell, p.x, p.y, p.z, r, nb);
+  first_bound(P.g, p.x, p.y, p.z, hint, nb);
+  if (!staged_search(P.g, P.cell, p.x, p.y, p.z, P.r, live, nb, stage) && live)
+    box_search_global(P.g, P.cell, p.x, p.y, p.z, P.r, nb);
   const float bd2 = nb.d2;
   if (live) {
     const int bp = nb.pos;
-    if (hints) hints[i] = bp;
+    if (P.hints) P.hints[i] = bp;
     if (mode == kCorrOnly) {
       const int o = __float_as_int(s.w);
-      corr_out[o] = bp >= 0 ? __float_as_int(g.pts[bp].w) : -1;
-      d2_out[o] = bp >= 0 ? bd2 : 0.f;
+      P.corr_out[o] = bp >= 0 ? __float_as_int(P.g.pts[bp].w) : -1;
+      P.d2_out[o] = bp >= 0 ? bd2 : 0.f;
     } else if (bp >= 0) {
-      const float4 q = g.pts[bp];
-      const float4 n = g.nrm[bp];
+      const float4 q = P.g.pts[bp];
+      const float4 n = P.g.nrm[bp];
       const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
       const float res = dx * n.x + dy * n.y + dz * n.z;
       float J[6];
@@ -602,32 +636,66 @@ __global__ void __launch_bounds__(kThreads) k_icp_iter(GridView g, float cell, c
     }
   }
   if (mode == kCorrOnly) return;
-  block_reduce_store(v, c, partials + static_cast<size_t>(blockIdx.x) * kPartial);
+  block_reduce_store(v, c, P.partials + static_cast<size_t>(j) * kPartial);
   // The last block of each group of kGroup blocks sums the group (float64, block
   // order); the last group to finish sums the groups and finishes the launch.
   __shared__ bool last;
-  const int grp = blockIdx.x / kGroup;
-  const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
-  const int in_group = min(kGroup, static_cast<int>(gridDim.x) - grp * kGroup);
+  const int grp = j / kGroup;
+  const int ngroups = (P.ntiles + kGroup - 1) / kGroup;
+  const int in_group = min(kGroup, P.ntiles - grp * kGroup);
   if (threadIdx.x < kPartial) __threadfence();  // the threads that stored the partial publish it
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&group_cnt[grp], 1u) == static_cast<unsigned>(in_group - 1);
+  if (threadIdx.x == 0) last = atomicAdd(&P.group_cnt[grp], 1u) == static_cast<unsigned>(in_group - 1);
   __syncthreads();
   if (!last) return;
   __threadfence();
   __shared__ double gsum[kPartial];
-  sum_partials(partials, grp * kGroup, in_group, gsum);
+  sum_partials(P.partials, grp * kGroup, in_group, gsum);
   if (threadIdx.x < kPartial) {
-    gsums[static_cast<size_t>(grp) * kPartial + threadIdx.x] = gsum[threadIdx.x];
+    P.gsums[static_cast<size_t>(grp) * kPartial + threadIdx.x] = gsum[threadIdx.x];
     __threadfence();
   }
-  if (threadIdx.x == 0) group_cnt[grp] = 0u;
+  if (threadIdx.x == 0) P.group_cnt[grp] = 0u;
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&st->arrived, 1u) == static_cast<unsigned>(ngroups - 1);
+  if (threadIdx.x == 0) last = atomicAdd(&P.st->arrived, 1u) == static_cast<unsigned>(ngroups - 1);
   __syncthreads();
   if (!last) return;
   __threadfence();
-  finish(gsums, ngroups, st, eps, mode, ns);
+  finish(P.gsums, ngroups, P.st, eps, mode, P.ns);
+}
+
+// One ICP step of every pair: a persistent kernel whose blocks walk the global
+// tiles (tile, tile + gridDim.x, ...).  pairs == nullptr means the single pair
+// `one` owns every tile.  The pair of a tile comes from tile_pair.  Tiles of
+// different pairs are independent; each pair's partial sums sit in fixed per-tile
+// slots, so every pair's result is the same alone and in any batch.
+__global__ void __launch_bounds__(kThreads) k_icp_iter(PairDesc one, const PairDesc* __restrict__ pairs,
+                                                       const int* __restrict__ tile_pair,
+                                                       const int* __restrict__ ntiles_total, double eps, int mode) {
+  __shared__ Stage stage;
+  __shared__ PairDesc P;
+  const int n = pairs ? *ntiles_total : one.ntiles;
+  for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
+    if (threadIdx.x == 0) P = pairs ? pairs[tile_pair[tile]] : one;
+    __syncthreads();
+    icp_tile(P, tile - P.tile0, eps, mode, stage);
+    __syncthreads();
+  }
+}
+
+// Blocks of the persistent iteration kernel: every tile at once when they fit
+// on the GPU together, else as many as are resident (they loop over tiles).
+int persistent_blocks(int ntiles) {
+  static int resident = 0;
+  if (resident == 0) {
+    int dev = 0, sms = kNumSMs, per_sm = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_icp_iter, kThreads, 0) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    (void)cudaGetLastError();
+    resident = sms * per_sm;
+  }
+  return ntiles < resident ? (ntiles < 1 ? 1 : ntiles) : resident;
 }
 
 inline int iter_blocks(int64_t ns) {
@@ -683,10 +751,22 @@ struct Work {
   int32_t launch(const o3g_grid* g, int ns, float r, double eps, int mode, int32_t* corr, float* d2,
                  cudaStream_t s) {
     double* pp = partials.as<double>();
-    k_icp_iter<<<nblk, kThreads, 0, s>>>(g->view(), g->cell, src.pts, ns, state.as<IcpState>(), r, pp,
-                                         pp + static_cast<size_t>(kPartial) * nblk, counters.as<unsigned>(), eps,
-                                         mode, corr, d2,
-                                         (mode == kIterate || mode == kEvaluate) ? hints.as<int32_t>() : nullptr);
+    PairDesc P;
+    P.g = g->view();
+    P.cell = g->cell;
+    P.r = r;
+    P.src4 = src.pts;
+    P.ns = ns;
+    P.ntiles = nblk;
+    P.tile0 = 0;
+    P.st = state.as<IcpState>();
+    P.partials = pp;
+    P.gsums = pp + static_cast<size_t>(kPartial) * nblk;
+    P.group_cnt = counters.as<unsigned>();
+    P.hints = (mode == kIterate || mode == kEvaluate) ? hints.as<int32_t>() : nullptr;
+    P.corr_out = corr;
+    P.d2_out = d2;
+    k_icp_iter<<<persistent_blocks(nblk), kThreads, 0, s>>>(P, nullptr, nullptr, nullptr, eps, mode);
     count_launch();
     return O3G_OK;
   }
@@ -942,8 +1022,22 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const 
   double* gsums = partials + static_cast<size_t>(kPartial) * nblk;
   for (int it = 0; it <= max_iter; ++it) {
     const int mode = it < max_iter ? kIterate : kEvaluate;
-    k_icp_iter<<<nblk, kThreads, 0, s>>>(gv, g->cell, src4, n, st, r, partials, gsums, counters, eps, mode, nullptr,
-                                         nullptr, nullptr);
+    PairDesc P;
+    P.g = gv;
+    P.cell = g->cell;
+    P.r = r;
+    P.src4 = src4;
+    P.ns = n;
+    P.ntiles = nblk;
+    P.tile0 = 0;
+    P.st = st;
+    P.partials = partials;
+    P.gsums = gsums;
+    P.group_cnt = counters;
+    P.hints = nullptr;
+    P.corr_out = nullptr;
+    P.d2_out = nullptr;
+    k_icp_iter<<<persistent_blocks(nblk), kThreads, 0, s>>>(P, nullptr, nullptr, nullptr, eps, mode);
     count_launch();
   }
   O3G_TRY(cudaGetLastError());
@@ -966,5 +1060,190 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const 
   if (out_iters) *out_iters = h.iters;
   if (h.few_corr) return O3G_WARN_FEW_CORR;
   if (h.degenerate) return O3G_WARN_DEGENERATE;
+  return O3G_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched point-to-plane ICP: many independent registrations advance together,
+// one persistent launch per iteration over the (pair, tile) work items of all
+// pairs; the iteration sequence is captured once as a CUDA graph and launched.
+
+namespace o3g {
+namespace {
+
+std::mutex g_graph_mutex;
+cudaStream_t g_graph_stream[kNaMaxDevices] = {};
+
+// A non-blocking stream of the library per device, used to capture graphs
+// (the legacy default stream cannot be captured).
+cudaError_t graph_stream(cudaStream_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_graph_mutex);
+  if (!g_graph_stream[dev]) {
+    e = cudaStreamCreateWithFlags(&g_graph_stream[dev], cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  *out = g_graph_stream[dev];
+  return cudaSuccess;
+}
+
+// Launches `iters` iteration steps and one evaluation step of the batch on s,
+// through a captured CUDA graph when capture works, else directly.
+int32_t run_iterations(const PairDesc* descs, const int* tile_pair, const int* d_ntiles, int ntiles, int max_iter,
+                       double eps, cudaStream_t s) {
+  const int blocks = persistent_blocks(ntiles);
+  PairDesc dummy{};
+  auto enqueue = [&](cudaStream_t q) {
+    for (int it = 0; it <= max_iter; ++it)
+      k_icp_iter<<<blocks, kThreads, 0, q>>>(dummy, descs, tile_pair, d_ntiles, eps,
+                                               it < max_iter ? kIterate : kEvaluate);
+  };
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool ok = graph_stream(&cs) == cudaSuccess && cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming) == cudaSuccess;
+  if (ok) {
+    ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      enqueue(cs);
+      ok = cudaStreamEndCapture(cs, &graph) == cudaSuccess && graph != nullptr;
+    }
+    ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    ok = ok && cudaEventRecord(ev_in, s) == cudaSuccess && cudaStreamWaitEvent(cs, ev_in, 0) == cudaSuccess &&
+         cudaGraphLaunch(exec, cs) == cudaSuccess && cudaEventRecord(ev_out, cs) == cudaSuccess &&
+         cudaStreamWaitEvent(s, ev_out, 0) == cudaSuccess;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (ev_in) cudaEventDestroy(ev_in);
+  if (ev_out) cudaEventDestroy(ev_out);
+  if (!ok) {
+    (void)cudaGetLastError();
+    enqueue(s);  // capture unavailable: plain launches, same work
+  }
+  count_launch(max_iter + 1);
+  O3G_TRY(cudaGetLastError());
+  return O3G_OK;
+}
+
+}  // namespace
+}  // namespace o3g
+
+extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid* const* tgts, const float* const* d_src,
+                                                const int64_t* ns, const int32_t* strides, const double* init_T,
+                                                const double* max_corr_dist, int32_t max_iter, double eps,
+                                                double* out_T, double* out_fitness, double* out_rmse,
+                                                int32_t* out_iters, int32_t* out_status, void* stream) {
+  using namespace o3g;
+  const char* fn = "o3g_icp_point_to_plane_batch";
+  if (n_pairs < 0 || max_iter < 0 || (n_pairs > 0 && (!tgts || !d_src || !ns || !strides || !init_T ||
+                                                       !max_corr_dist || !out_T || !out_fitness || !out_rmse ||
+                                                       !out_iters || !out_status))) {
+    set_error("%s: invalid argument", fn);
+    return O3G_ERR_ARG;
+  }
+  if (n_pairs == 0) return O3G_OK;
+  std::vector<int64_t> off(n_pairs + 1, 0);
+  std::vector<int> ntiles(n_pairs), ngroups(n_pairs);
+  int64_t tiles_total = 0, groups_total = 0;
+  for (int p = 0; p < n_pairs; ++p) {
+    if (!tgts[p] || !tgts[p]->has_normals || !(max_corr_dist[p] >= 0.0) || !std::isfinite(max_corr_dist[p])) {
+      set_error("%s: pair %d: missing target grid, target normals or a valid max_corr_dist", fn, p);
+      return O3G_ERR_ARG;
+    }
+    O3G_TRY_STATUS(check_src(fn, d_src[p], ns[p], strides[p]));
+    if (!pose_ok(init_T + 16 * p)) {
+      set_error("%s: pair %d: init_T is not finite", fn, p);
+      return O3G_ERR_NONFINITE;
+    }
+    off[p + 1] = off[p] + ns[p];
+    ntiles[p] = iter_blocks(ns[p]);
+    ngroups[p] = (ntiles[p] + kGroup - 1) / kGroup;
+    tiles_total += ntiles[p];
+    groups_total += ngroups[p];
+  }
+  if (off[n_pairs] > 0x7fffffffLL - kThreads || tiles_total > 0x7fffffffLL) {
+    set_error("%s: %lld source points in total exceed the supported size", fn, static_cast<long long>(off[n_pairs]));
+    return O3G_ERR_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t total = off[n_pairs];
+  DevBuf d_ptrs(s), d_strides(s), d_off(s), d_src4(s), d_aux(s), d_states(s), d_part(s), d_cnt(s), d_hints(s),
+      d_descs(s), d_tiles(s), d_poses(s);
+  O3G_TRY(d_ptrs.alloc(sizeof(float*) * n_pairs));
+  O3G_TRY(d_strides.alloc(sizeof(int32_t) * n_pairs));
+  O3G_TRY(d_off.alloc(sizeof(int64_t) * (n_pairs + 1)));
+  O3G_TRY(d_src4.alloc(sizeof(float4) * (total > 0 ? total : 1)));
+  O3G_TRY(d_aux.alloc(sizeof(int) * 8 * n_pairs));
+  O3G_TRY(d_states.alloc(sizeof(IcpState) * n_pairs));
+  O3G_TRY(d_part.alloc(sizeof(double) * kPartial * (tiles_total + groups_total)));
+  O3G_TRY(d_cnt.alloc(sizeof(unsigned) * groups_total));
+  O3G_TRY(d_hints.alloc(sizeof(int32_t) * (total > 0 ? total : 1)));
+  O3G_TRY(d_descs.alloc(sizeof(PairDesc) * n_pairs));
+  O3G_TRY(d_tiles.alloc(sizeof(int) * (tiles_total + 1)));
+  O3G_TRY(d_poses.alloc(sizeof(double) * 16 * n_pairs));
+  // host-side tables
+  std::vector<PairDesc> descs(n_pairs);
+  std::vector<int> tile_pair(tiles_total + 1);
+  IcpState* states = d_states.as<IcpState>();
+  double* part = d_part.as<double>();
+  unsigned* cnt = d_cnt.as<unsigned>();
+  int64_t t0 = 0, g0 = 0;
+  for (int p = 0; p < n_pairs; ++p) {
+    PairDesc& P = descs[p];
+    P.g = tgts[p]->view();
+    P.cell = tgts[p]->cell;
+    P.r = static_cast<float>(max_corr_dist[p]);
+    P.src4 = d_src4.as<float4>() + off[p];
+    P.ns = static_cast<int>(ns[p]);
+    P.ntiles = ntiles[p];
+    P.tile0 = static_cast<int>(t0);
+    P.st = states + p;
+    P.partials = part + static_cast<size_t>(kPartial) * t0;
+    P.gsums = part + static_cast<size_t>(kPartial) * (tiles_total + g0);
+    P.group_cnt = cnt + g0;
+    P.hints = d_hints.as<int32_t>() + off[p];
+    P.corr_out = nullptr;
+    P.d2_out = nullptr;
+    for (int k = 0; k < ntiles[p]; ++k) tile_pair[t0 + k] = p;
+    t0 += ntiles[p];
+    g0 += ngroups[p];
+  }
+  tile_pair[tiles_total] = static_cast<int>(tiles_total);  // read by the kernel as the tile count
+  std::vector<int32_t> h_strides(strides, strides + n_pairs);
+  O3G_TRY(cudaMemcpyAsync(d_ptrs.p, d_src, sizeof(float*) * n_pairs, cudaMemcpyHostToDevice, s));
+  O3G_TRY(cudaMemcpyAsync(d_strides.p, h_strides.data(), sizeof(int32_t) * n_pairs, cudaMemcpyHostToDevice, s));
+  O3G_TRY(cudaMemcpyAsync(d_off.p, off.data(), sizeof(int64_t) * (n_pairs + 1), cudaMemcpyHostToDevice, s));
+  O3G_TRY(cudaMemcpyAsync(d_descs.p, descs.data(), sizeof(PairDesc) * n_pairs, cudaMemcpyHostToDevice, s));
+  O3G_TRY(cudaMemcpyAsync(d_tiles.p, tile_pair.data(), sizeof(int) * (tiles_total + 1), cudaMemcpyHostToDevice, s));
+  O3G_TRY(cudaMemcpyAsync(d_poses.p, init_T, sizeof(double) * 16 * n_pairs, cudaMemcpyHostToDevice, s));
+  O3G_TRY(cudaMemsetAsync(d_cnt.p, 0, sizeof(unsigned) * groups_total, s));
+  O3G_TRY(cudaMemsetAsync(d_hints.p, 0xff, sizeof(int32_t) * (total > 0 ? total : 1), s));
+  O3G_TRY_STATUS(sort_clouds_batch(reinterpret_cast<const float* const*>(d_ptrs.p), d_strides.as<int32_t>(),
+                                   d_off.as<int64_t>(), n_pairs, total, s, d_src4.as<float4>(), d_aux.as<int>()));
+  k_init_states<<<(n_pairs + 127) / 128, 128, 0, s>>>(states, d_poses.as<double>(), n_pairs);
+  count_launch();
+  O3G_TRY_STATUS(run_iterations(d_descs.as<PairDesc>(), d_tiles.as<int>(), d_tiles.as<int>() + tiles_total,
+                                static_cast<int>(tiles_total), max_iter, eps, s));
+  std::vector<IcpState> h(n_pairs);
+  std::vector<int> aux(8 * n_pairs);
+  O3G_TRY(cudaMemcpyAsync(h.data(), states, sizeof(IcpState) * n_pairs, cudaMemcpyDeviceToHost, s));
+  O3G_TRY(cudaMemcpyAsync(aux.data(), d_aux.p, sizeof(int) * 8 * n_pairs, cudaMemcpyDeviceToHost, s));
+  O3G_TRY(cudaStreamSynchronize(s));
+  for (int p = 0; p < n_pairs; ++p) {
+    for (int k = 0; k < 16; ++k) out_T[16 * p + k] = h[p].T[k];
+    out_fitness[p] = h[p].fitness;
+    out_rmse[p] = h[p].rmse;
+    out_iters[p] = h[p].iters;
+    out_status[p] = aux[8 * p + 6] || h[p].nonfinite ? O3G_ERR_NONFINITE
+                    : h[p].few_corr                  ? O3G_WARN_FEW_CORR
+                    : h[p].degenerate                ? O3G_WARN_DEGENERATE
+                                                     : O3G_OK;
+  }
   return O3G_OK;
 }

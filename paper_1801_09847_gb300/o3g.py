@@ -58,6 +58,8 @@ _SIGNATURES = {
                                 _f64p], _i32),
     "o3g_register_point_to_plane_host": ([_vp, _i64, _vp, _i64, _vp, _f32, _i32, _f64p, _f64, _i32, _f64, _f64p,
                                           _f64p, _f64p, _i32p, _vp], _i32),
+    "o3g_icp_point_to_plane_batch": ([_i32, _vp, _vp, _vp, _vp, _f64p, _f64p, _i32, _f64, _f64p, _f64p, _f64p, _i32p,
+                                      _i32p, _vp], _i32),
     "o3g_icp_point_to_plane_grid_noalloc": ([_vp, _vp, _i64, _i32, _f64p, _f64, _i32, _f64, _f64p, _f64p, _f64p,
                                              _i32p, _vp], _i32),
     "o3g_launch_count": ([], _i64),
@@ -257,6 +259,42 @@ def icp_point_to_plane_grid(grid: Grid, src, init_T, max_corr_dist: float, max_i
                                                   ctypes.byref(rmse), ctypes.byref(iters), _stream(stream)),
                 "o3g_icp_point_to_plane_grid")
     return _result(st, T, fit, rmse, iters)
+
+
+def icp_point_to_plane_batch(grids, srcs, init_Ts, max_corr_dists, max_iter: int, eps: float = 0.0,
+                             stream=None) -> list:
+    """Many independent registrations in one batched call (o3g_icp_point_to_plane_batch).
+
+    grids: target Grids with normals; srcs: device source clouds; init_Ts: 4x4 poses;
+    max_corr_dists: one radius per pair or a scalar.  Returns one result dict per pair.
+    """
+    n = len(grids)
+    if len(srcs) != n or len(init_Ts) != n:
+        raise ValueError("grids, srcs and init_Ts must have one entry per pair")
+    radii = np.broadcast_to(np.asarray(max_corr_dists, np.float64), (n,)).copy()
+    handles = (ctypes.c_void_p * max(n, 1))(*[g.handle.value for g in grids])
+    ptrs = (ctypes.c_void_p * max(n, 1))()
+    ns = np.zeros(max(n, 1), np.int64)
+    strides = np.zeros(max(n, 1), np.int32)
+    for k, src in enumerate(srcs):
+        p, m, stride = _cloud(src, f"srcs[{k}]")
+        ptrs[k] = p.value
+        ns[k] = m
+        strides[k] = stride
+    T0 = np.ascontiguousarray(np.stack([np.asarray(T, np.float64).reshape(16) for T in init_Ts]) if n else
+                              np.zeros((1, 16)))
+    T = np.zeros((max(n, 1), 16))
+    fit = np.zeros(max(n, 1))
+    rmse = np.zeros(max(n, 1))
+    iters = np.zeros(max(n, 1), np.int32)
+    status = np.zeros(max(n, 1), np.int32)
+    _check(lib().o3g_icp_point_to_plane_batch(n, ctypes.cast(handles, _vp), ctypes.cast(ptrs, _vp),
+                                              ns.ctypes.data_as(_vp), strides.ctypes.data_as(_vp), _pp(T0),
+                                              _pp(radii), int(max_iter), float(eps), _pp(T), _pp(fit), _pp(rmse),
+                                              iters.ctypes.data_as(_i32p), status.ctypes.data_as(_i32p),
+                                              _stream(stream)), "o3g_icp_point_to_plane_batch")
+    return [dict(status=int(status[k]), T=T[k].reshape(4, 4), fitness=float(fit[k]), rmse=float(rmse[k]),
+                 iters=int(iters[k])) for k in range(n)]
 
 
 def icp_point_to_plane(src, tgt, tgt_nrm, init_T, max_corr_dist: float, max_iter: int) -> dict:
