@@ -247,12 +247,14 @@ O3G_API int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* tgt, const f
  * device time in milliseconds and the number of launches timed, and (reset != 0)
  * forgets them.  kind: O3G_KERNEL_ICP_CORR (per-iteration correspondence +
  * reduction), O3G_KERNEL_ICP_SOLVE (per-iteration reduce + solve + update),
- * O3G_KERNEL_NORMALS (normal estimation), O3G_KERNEL_GRID (one whole grid build).
+ * O3G_KERNEL_NORMALS (normal estimation), O3G_KERNEL_GRID (one whole grid build),
+ * O3G_KERNEL_ICP_BATCH (all iteration launches of one batched call, one record).
  */
 #define O3G_KERNEL_ICP_CORR 0
 #define O3G_KERNEL_ICP_SOLVE 1
 #define O3G_KERNEL_NORMALS 2
 #define O3G_KERNEL_GRID 3
+#define O3G_KERNEL_ICP_BATCH 4
 O3G_API int64_t o3g_launch_count(void);
 O3G_API int32_t o3g_timing_enable(int32_t on);
 O3G_API int32_t o3g_timing_read(int32_t kind, double* total_ms, int64_t* launches, int32_t reset);

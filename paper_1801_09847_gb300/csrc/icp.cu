@@ -1228,8 +1228,11 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
                                    d_off.as<int64_t>(), n_pairs, total, s, d_src4.as<float4>(), d_aux.as<int>()));
   k_init_states<<<(n_pairs + 127) / 128, 128, 0, s>>>(states, d_poses.as<double>(), n_pairs);
   count_launch();
-  O3G_TRY_STATUS(run_iterations(d_descs.as<PairDesc>(), d_tiles.as<int>(), d_tiles.as<int>() + tiles_total,
-                                static_cast<int>(tiles_total), max_iter, eps, s));
+  {
+    TimedRegion tr(O3G_KERNEL_ICP_BATCH, s);
+    O3G_TRY_STATUS(run_iterations(d_descs.as<PairDesc>(), d_tiles.as<int>(), d_tiles.as<int>() + tiles_total,
+                                  static_cast<int>(tiles_total), max_iter, eps, s));
+  }
   std::vector<IcpState> h(n_pairs);
   std::vector<int> aux(8 * n_pairs);
   O3G_TRY(cudaMemcpyAsync(h.data(), states, sizeof(IcpState) * n_pairs, cudaMemcpyDeviceToHost, s));

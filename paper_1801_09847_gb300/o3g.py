@@ -67,7 +67,7 @@ _SIGNATURES = {
     "o3g_timing_read": ([_i32, _f64p, ctypes.POINTER(_i64), _i32], _i32),
 }
 
-KERNEL_ICP_CORR, KERNEL_ICP_SOLVE, KERNEL_NORMALS, KERNEL_GRID = 0, 1, 2, 3
+KERNEL_ICP_CORR, KERNEL_ICP_SOLVE, KERNEL_NORMALS, KERNEL_GRID, KERNEL_ICP_BATCH = 0, 1, 2, 3, 4
 
 
 def launch_count() -> int:
