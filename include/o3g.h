@@ -210,6 +210,40 @@ O3G_API int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid* co
                                              int32_t* out_iters, int32_t* out_status, void* stream);
 
 /*
+ * Serving: registration requests of any size handled as a continuously batched
+ * loop on one stream.  Requests wait in a first-come-first-served queue until a
+ * slot (max_active) and the device-memory budget (hbm_budget_bytes, estimated
+ * per request from its sizes) allow their admission; admission copies the
+ * request's clouds to the device, builds its target grid (cell = 1.002 x
+ * max_corr_dist), attaches or estimates target normals and lays out its source.
+ * Each o3g_server_step then advances every admitted request by one ICP iteration
+ * in a single persistent launch, and retires the requests that have converged,
+ * stopped or used max_iter iterations (their results wait for
+ * o3g_server_poll).  Target grids and per-request pose state stay resident on
+ * the device between steps.  Each request's result is the one the single-pair
+ * entry points give for it (same arithmetic, order and tiling), whatever else is
+ * being served.  A server and its requests belong to one host thread at a time.
+ *   o3g_server_submit copies the host clouds (packed xyz; h_tgt_nrm may be NULL
+ *   to estimate normals with normal_radius / normal_max_nn) and returns an id;
+ *   a request larger than the whole budget gives O3G_ERR_OOM.
+ *   o3g_server_step reports active, waiting and completed-this-step counts.
+ *   o3g_server_poll sets *out_done; when done it fills the results (as
+ *   o3g_icp_point_to_plane_grid; out_status holds the request's status) and
+ *   forgets the request.
+ */
+typedef struct o3g_server o3g_server;
+O3G_API int32_t o3g_server_create(int32_t max_active, int64_t hbm_budget_bytes, void* stream, o3g_server** out);
+O3G_API int32_t o3g_server_destroy(o3g_server* server);
+O3G_API int32_t o3g_server_submit(o3g_server* server, const float* h_src, int64_t ns, const float* h_tgt, int64_t nt,
+                                  const float* h_tgt_nrm, float normal_radius, int32_t normal_max_nn,
+                                  const double* init_T, double max_corr_dist, int32_t max_iter, double eps,
+                                  int64_t* out_id);
+O3G_API int32_t o3g_server_step(o3g_server* server, int32_t* out_active, int32_t* out_waiting,
+                                int32_t* out_completed);
+O3G_API int32_t o3g_server_poll(o3g_server* server, int64_t id, int32_t* out_done, double* out_T,
+                                double* out_fitness, double* out_rmse, int32_t* out_iters, int32_t* out_status);
+
+/*
  * Allocation-free form of o3g_icp_point_to_plane_grid.  The paper has no
  * counterpart: this entry point exists for callers that must not allocate device
  * memory once they are running - for example a tracking loop that registers

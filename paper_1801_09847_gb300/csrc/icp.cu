@@ -18,7 +18,10 @@
 // The pose never leaves the device between iterations.
 #include <algorithm>
 #include <cmath>
+#include <deque>
+#include <map>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "o3g_internal.cuh"
@@ -564,6 +567,7 @@ __device__ void finish(const double* __restrict__ gsums, int ngroups, IcpState* 
 struct PairDesc {
   GridView g;
   float cell, r;
+  double eps;          // convergence threshold of this pair (<= 0: never)
   const float4* src4;  // cell-sorted source, .w = original index bits
   int ns;
   int ntiles;          // ceil(ns / kThreads), at least 1
@@ -581,7 +585,7 @@ struct PairDesc {
 // mode kIterate: skipped once the pair is done; the other modes always run.
 // kCorrOnly writes corr/d2 and no sums.  The last tile of the pair to finish
 // performs the pair's solve and update (see finish).  Block-uniform control flow.
-__device__ void icp_tile(const PairDesc& P, int j, double eps, int mode, Stage& stage) {
+__device__ void icp_tile(const PairDesc& P, int j, int mode, Stage& stage) {
   if (mode == kIterate && P.st->done) return;
   float R[9], t[3];
 #pragma unroll
@@ -661,7 +665,7 @@ __device__ void icp_tile(const PairDesc& P, int j, double eps, int mode, Stage& 
   __syncthreads();
   if (!last) return;
   __threadfence();
-  finish(P.gsums, ngroups, P.st, eps, mode, P.ns);
+  finish(P.gsums, ngroups, P.st, P.eps, mode, P.ns);
 }
 
 // One ICP step of every pair: a persistent kernel whose blocks walk the global
@@ -671,14 +675,14 @@ __device__ void icp_tile(const PairDesc& P, int j, double eps, int mode, Stage& 
 // slots, so every pair's result is the same alone and in any batch.
 __global__ void __launch_bounds__(kThreads) k_icp_iter(PairDesc one, const PairDesc* __restrict__ pairs,
                                                        const int* __restrict__ tile_pair,
-                                                       const int* __restrict__ ntiles_total, double eps, int mode) {
+                                                       const int* __restrict__ ntiles_total, int mode) {
   __shared__ Stage stage;
   __shared__ PairDesc P;
   const int n = pairs ? *ntiles_total : one.ntiles;
   for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
     if (threadIdx.x == 0) P = pairs ? pairs[tile_pair[tile]] : one;
     __syncthreads();
-    icp_tile(P, tile - P.tile0, eps, mode, stage);
+    icp_tile(P, tile - P.tile0, mode, stage);
     __syncthreads();
   }
 }
@@ -755,6 +759,7 @@ struct Work {
     P.g = g->view();
     P.cell = g->cell;
     P.r = r;
+    P.eps = eps;
     P.src4 = src.pts;
     P.ns = ns;
     P.ntiles = nblk;
@@ -766,7 +771,7 @@ struct Work {
     P.hints = (mode == kIterate || mode == kEvaluate) ? hints.as<int32_t>() : nullptr;
     P.corr_out = corr;
     P.d2_out = d2;
-    k_icp_iter<<<persistent_blocks(nblk), kThreads, 0, s>>>(P, nullptr, nullptr, nullptr, eps, mode);
+    k_icp_iter<<<persistent_blocks(nblk), kThreads, 0, s>>>(P, nullptr, nullptr, nullptr, mode);
     count_launch();
     return O3G_OK;
   }
@@ -1026,6 +1031,7 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const 
     P.g = gv;
     P.cell = g->cell;
     P.r = r;
+    P.eps = eps;
     P.src4 = src4;
     P.ns = n;
     P.ntiles = nblk;
@@ -1037,7 +1043,7 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const 
     P.hints = nullptr;
     P.corr_out = nullptr;
     P.d2_out = nullptr;
-    k_icp_iter<<<persistent_blocks(nblk), kThreads, 0, s>>>(P, nullptr, nullptr, nullptr, eps, mode);
+    k_icp_iter<<<persistent_blocks(nblk), kThreads, 0, s>>>(P, nullptr, nullptr, nullptr, mode);
     count_launch();
   }
   O3G_TRY(cudaGetLastError());
@@ -1098,8 +1104,7 @@ int32_t run_iterations(const PairDesc* descs, const int* tile_pair, const int* d
   PairDesc dummy{};
   auto enqueue = [&](cudaStream_t q) {
     for (int it = 0; it <= max_iter; ++it)
-      k_icp_iter<<<blocks, kThreads, 0, q>>>(dummy, descs, tile_pair, d_ntiles, eps,
-                                               it < max_iter ? kIterate : kEvaluate);
+      k_icp_iter<<<blocks, kThreads, 0, q>>>(dummy, descs, tile_pair, d_ntiles, it < max_iter ? kIterate : kEvaluate);
   };
   cudaStream_t cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -1199,6 +1204,7 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
     P.g = tgts[p]->view();
     P.cell = tgts[p]->cell;
     P.r = static_cast<float>(max_corr_dist[p]);
+    P.eps = eps;
     P.src4 = d_src4.as<float4>() + off[p];
     P.ns = static_cast<int>(ns[p]);
     P.ntiles = ntiles[p];
@@ -1248,5 +1254,368 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
                     : h[p].degenerate                ? O3G_WARN_DEGENERATE
                                                      : O3G_OK;
   }
+  return O3G_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Serving: a request loop with continuous batching.  Requests wait in a queue
+// until a slot and the device-memory budget allow their admission (host copy to
+// device, target grid, normals, source layout, state); every step advances all
+// admitted requests by one iteration in a single persistent launch and retires
+// the ones that have finished (evaluation launch, results kept for polling).
+// A request's arithmetic, order and tiling are those of the single-pair entry
+// points, so its result does not depend on what else is being served.
+
+struct o3g_server {
+  struct Request {
+    int64_t id;
+    std::vector<float> src, tgt, nrm;
+    float normal_radius;
+    int normal_max_nn;
+    double T0[16];
+    double r;
+    int max_iter;
+    double eps;
+  };
+  struct Slot {
+    bool used = false;
+    int64_t id = -1;
+    o3g_grid* grid = nullptr;
+    float4* src4 = nullptr;
+    int* src_aux = nullptr;
+    int32_t* hints = nullptr;
+    double* partials = nullptr;  // ntiles block partials, then ngroups group sums
+    unsigned* counters = nullptr;
+    int ns = 0, ntiles = 1, ngroups = 1;
+    int max_iter = 0;
+    double eps = 0.0;
+    float r = 0.f;
+    int64_t bytes = 0;
+    int iters = 0;
+    bool done = false;
+  };
+  struct Result {
+    int32_t status;
+    double T[16];
+    double fitness, rmse;
+    int32_t iters;
+  };
+  cudaStream_t s = nullptr;
+  int max_active = 0;
+  int64_t budget = 0, used = 0;
+  int64_t next_id = 0;
+  std::deque<Request> waiting;
+  std::vector<Slot> slots;
+  void* states = nullptr;   // max_active IcpState, slot-indexed
+  void* descs = nullptr;    // max_active PairDesc
+  int* tiles = nullptr;     // tile table (+1 count), grows
+  int64_t tiles_cap = 0;
+  std::map<int64_t, Result> finished;
+};
+
+namespace o3g {
+namespace {
+
+// Device memory a request will hold while admitted (upper bound before its grid exists).
+int64_t request_bytes(int64_t ns, int64_t nt) {
+  const int64_t tiles = iter_blocks(ns), groups = (tiles + kGroup - 1) / kGroup;
+  return ns * (16 + 4 + 12) + tiles * kPartial * 8 + groups * (kPartial * 8 + 4) + nt * (16 + 16 + 4 + 12 + 12) +
+         4 * (32 * nt + (1 << 20)) + sizeof(IcpState);
+}
+
+void release_slot(o3g_server* sv, o3g_server::Slot& sl) {
+  if (sl.grid) o3g_free_grid(sl.grid);
+  dfree(sl.src4, sv->s);
+  dfree(sl.src_aux, sv->s);
+  dfree(sl.hints, sv->s);
+  dfree(sl.partials, sv->s);
+  dfree(sl.counters, sv->s);
+  sv->used -= sl.bytes;
+  sl = o3g_server::Slot();
+}
+
+// Admission of one request into free slot k (device copies, grid, normals, layout, state).
+int32_t admit(o3g_server* sv, int k, o3g_server::Request& rq) {
+  cudaStream_t s = sv->s;
+  o3g_server::Slot& sl = sv->slots[k];
+  const int64_t ns = static_cast<int64_t>(rq.src.size() / 3), nt = static_cast<int64_t>(rq.tgt.size() / 3);
+  sl.used = true;
+  sl.id = rq.id;
+  sl.ns = static_cast<int>(ns);
+  sl.ntiles = iter_blocks(ns);
+  sl.ngroups = (sl.ntiles + kGroup - 1) / kGroup;
+  sl.max_iter = rq.max_iter;
+  sl.eps = rq.eps;
+  sl.r = static_cast<float>(rq.r);
+  sl.bytes = request_bytes(ns, nt);
+  sv->used += sl.bytes;
+  DevBuf d_src(s), d_tgt(s), d_nrm(s);
+  O3G_TRY(d_src.alloc(sizeof(float) * 3 * (ns > 0 ? ns : 1)));
+  O3G_TRY(d_tgt.alloc(sizeof(float) * 3 * (nt > 0 ? nt : 1)));
+  if (ns > 0) O3G_TRY(cudaMemcpyAsync(d_src.p, rq.src.data(), sizeof(float) * 3 * ns, cudaMemcpyHostToDevice, s));
+  if (nt > 0) O3G_TRY(cudaMemcpyAsync(d_tgt.p, rq.tgt.data(), sizeof(float) * 3 * nt, cudaMemcpyHostToDevice, s));
+  O3G_TRY_STATUS(o3g_build_grid(d_tgt.as<float>(), nt, 3, static_cast<float>(rq.r * 1.002), s, &sl.grid));
+  if (!rq.nrm.empty()) {
+    O3G_TRY(d_nrm.alloc(sizeof(float) * 3 * (nt > 0 ? nt : 1)));
+    if (nt > 0) O3G_TRY(cudaMemcpyAsync(d_nrm.p, rq.nrm.data(), sizeof(float) * 3 * nt, cudaMemcpyHostToDevice, s));
+    O3G_TRY_STATUS(o3g_grid_set_normals(sl.grid, d_nrm.as<float>(), nt, 3, s));
+  } else {
+    O3G_TRY_STATUS(estimate_normals_impl(sl.grid, rq.normal_radius, rq.normal_max_nn, nullptr, nullptr, 3, s));
+  }
+  SortedCloud sc(s);
+  O3G_TRY_STATUS(sort_cloud(d_src.as<float>(), ns, 3, s, &sc));
+  sl.src4 = sc.pts;
+  sl.src_aux = sc.aux.as<int>();
+  sc.buf.p = nullptr;  // now owned by the slot
+  sc.aux.p = nullptr;
+  O3G_TRY(dmalloc(reinterpret_cast<void**>(&sl.hints), sizeof(int32_t) * (ns > 0 ? ns : 1), s));
+  O3G_TRY(cudaMemsetAsync(sl.hints, 0xff, sizeof(int32_t) * (ns > 0 ? ns : 1), s));
+  O3G_TRY(dmalloc(reinterpret_cast<void**>(&sl.partials), sizeof(double) * kPartial * (sl.ntiles + sl.ngroups), s));
+  O3G_TRY(dmalloc(reinterpret_cast<void**>(&sl.counters), sizeof(unsigned) * sl.ngroups, s));
+  O3G_TRY(cudaMemsetAsync(sl.counters, 0, sizeof(unsigned) * sl.ngroups, s));
+  k_init_state<<<1, 32, 0, s>>>(static_cast<IcpState*>(sv->states) + k, to_pose(rq.T0));
+  count_launch();
+  O3G_TRY(cudaGetLastError());
+  sl.iters = 0;
+  sl.done = false;
+  return O3G_OK;
+}
+
+PairDesc slot_desc(o3g_server* sv, int k, int tile0) {
+  o3g_server::Slot& sl = sv->slots[k];
+  PairDesc P;
+  P.g = sl.grid->view();
+  P.cell = sl.grid->cell;
+  P.r = sl.r;
+  P.eps = sl.eps;
+  P.src4 = sl.src4;
+  P.ns = sl.ns;
+  P.ntiles = sl.ntiles;
+  P.tile0 = tile0;
+  P.st = static_cast<IcpState*>(sv->states) + k;
+  P.partials = sl.partials;
+  P.gsums = sl.partials + static_cast<size_t>(kPartial) * sl.ntiles;
+  P.group_cnt = sl.counters;
+  P.hints = sl.hints;
+  P.corr_out = nullptr;
+  P.d2_out = nullptr;
+  return P;
+}
+
+// One launch of `mode` over the given slots.
+int32_t launch_slots(o3g_server* sv, const std::vector<int>& ks, int mode) {
+  cudaStream_t s = sv->s;
+  std::vector<PairDesc> d;
+  std::vector<int> tiles;
+  int64_t t0 = 0;
+  for (int k : ks) {
+    d.push_back(slot_desc(sv, k, static_cast<int>(t0)));
+    for (int j = 0; j < sv->slots[k].ntiles; ++j) tiles.push_back(static_cast<int>(d.size() - 1));
+    t0 += sv->slots[k].ntiles;
+  }
+  tiles.push_back(static_cast<int>(t0));
+  if (static_cast<int64_t>(tiles.size()) > sv->tiles_cap) {
+    dfree(sv->tiles, s);
+    sv->tiles = nullptr;
+    sv->tiles_cap = static_cast<int64_t>(tiles.size()) * 2;
+    O3G_TRY(dmalloc(reinterpret_cast<void**>(&sv->tiles), sizeof(int) * sv->tiles_cap, s));
+  }
+  O3G_TRY(cudaMemcpyAsync(sv->descs, d.data(), sizeof(PairDesc) * d.size(), cudaMemcpyHostToDevice, s));
+  O3G_TRY(cudaMemcpyAsync(sv->tiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice, s));
+  PairDesc dummy{};
+  k_icp_iter<<<persistent_blocks(static_cast<int>(t0)), kThreads, 0, s>>>(
+      dummy, static_cast<const PairDesc*>(sv->descs), sv->tiles, sv->tiles + t0, mode);
+  count_launch();
+  O3G_TRY(cudaGetLastError());
+  return O3G_OK;
+}
+
+}  // namespace
+}  // namespace o3g
+
+extern "C" int32_t o3g_server_create(int32_t max_active, int64_t hbm_budget_bytes, void* stream, o3g_server** out) {
+  using namespace o3g;
+  if (!out || max_active < 1 || max_active > 65536 || hbm_budget_bytes <= 0) {
+    set_error("o3g_server_create: invalid argument");
+    return O3G_ERR_ARG;
+  }
+  *out = nullptr;
+  o3g_server* sv = new (std::nothrow) o3g_server();
+  if (!sv) {
+    set_error("o3g_server_create: host allocation failed");
+    return O3G_ERR_OOM;
+  }
+  sv->s = static_cast<cudaStream_t>(stream);
+  sv->max_active = max_active;
+  sv->budget = hbm_budget_bytes;
+  sv->slots.resize(max_active);
+  cudaError_t e = dmalloc(&sv->states, sizeof(IcpState) * max_active, sv->s);
+  if (e == cudaSuccess) e = dmalloc(&sv->descs, sizeof(PairDesc) * max_active, sv->s);
+  if (e != cudaSuccess) {
+    dfree(sv->states, sv->s);
+    delete sv;
+    return cuda_fail(e, "o3g_server_create");
+  }
+  *out = sv;
+  return O3G_OK;
+}
+
+extern "C" int32_t o3g_server_destroy(o3g_server* sv) {
+  using namespace o3g;
+  if (!sv) return O3G_OK;
+  for (auto& sl : sv->slots)
+    if (sl.used) release_slot(sv, sl);
+  dfree(sv->states, sv->s);
+  dfree(sv->descs, sv->s);
+  dfree(sv->tiles, sv->s);
+  (void)cudaStreamSynchronize(sv->s);
+  delete sv;
+  return O3G_OK;
+}
+
+extern "C" int32_t o3g_server_submit(o3g_server* sv, const float* h_src, int64_t ns, const float* h_tgt, int64_t nt,
+                                     const float* h_tgt_nrm, float normal_radius, int32_t normal_max_nn,
+                                     const double* init_T, double max_corr_dist, int32_t max_iter, double eps,
+                                     int64_t* out_id) {
+  using namespace o3g;
+  const char* fn = "o3g_server_submit";
+  if (!sv || !out_id || ns < 0 || nt < 0 || ns > 0x7fffffffLL - kThreads || nt > 0x7fffffffLL - 4096 ||
+      (ns > 0 && !h_src) || (nt > 0 && !h_tgt) || max_iter < 0 || !(max_corr_dist > 0.0) ||
+      !std::isfinite(max_corr_dist) ||
+      (!h_tgt_nrm && (normal_max_nn < 1 || normal_max_nn > O3G_MAX_NN || !(normal_radius >= 0.f)))) {
+    set_error("%s: invalid argument", fn);
+    return O3G_ERR_ARG;
+  }
+  if (!pose_ok(init_T)) {
+    set_error("%s: init_T is null or not finite", fn);
+    return O3G_ERR_NONFINITE;
+  }
+  if (request_bytes(ns, nt) > sv->budget) {
+    set_error("%s: the request needs more device memory (%lld bytes) than the whole budget", fn,
+              static_cast<long long>(request_bytes(ns, nt)));
+    return O3G_ERR_OOM;
+  }
+  o3g_server::Request rq;
+  rq.id = sv->next_id++;
+  rq.src.assign(h_src, h_src + 3 * ns);
+  rq.tgt.assign(h_tgt, h_tgt + 3 * nt);
+  if (h_tgt_nrm) rq.nrm.assign(h_tgt_nrm, h_tgt_nrm + 3 * nt);
+  rq.normal_radius = normal_radius;
+  rq.normal_max_nn = normal_max_nn;
+  for (int k = 0; k < 16; ++k) rq.T0[k] = init_T[k];
+  rq.r = max_corr_dist;
+  rq.max_iter = max_iter;
+  rq.eps = eps;
+  sv->waiting.push_back(std::move(rq));
+  *out_id = sv->waiting.back().id;
+  return O3G_OK;
+}
+
+extern "C" int32_t o3g_server_step(o3g_server* sv, int32_t* out_active, int32_t* out_waiting, int32_t* out_completed) {
+  using namespace o3g;
+  if (!sv) {
+    set_error("o3g_server_step: server is null");
+    return O3G_ERR_ARG;
+  }
+  cudaStream_t s = sv->s;
+  // admit while a slot is free and the budget allows (first come, first served)
+  while (!sv->waiting.empty()) {
+    int k = -1;
+    for (int j = 0; j < sv->max_active; ++j)
+      if (!sv->slots[j].used) {
+        k = j;
+        break;
+      }
+    o3g_server::Request& rq = sv->waiting.front();
+    const int64_t need = request_bytes(static_cast<int64_t>(rq.src.size() / 3), static_cast<int64_t>(rq.tgt.size() / 3));
+    if (k < 0 || sv->used + need > sv->budget) break;
+    const int32_t st = admit(sv, k, rq);
+    if (st < 0) {
+      release_slot(sv, sv->slots[k]);
+      o3g_server::Result res{};
+      res.status = st;
+      sv->finished[rq.id] = res;
+      sv->waiting.pop_front();
+      continue;
+    }
+    sv->waiting.pop_front();
+  }
+  std::vector<int> iterate, finishing;
+  for (int k = 0; k < sv->max_active; ++k) {
+    const auto& sl = sv->slots[k];
+    if (!sl.used) continue;
+    if (!sl.done && sl.iters < sl.max_iter) iterate.push_back(k);
+    else finishing.push_back(k);
+  }
+  if (!iterate.empty()) {
+    O3G_TRY_STATUS(launch_slots(sv, iterate, kIterate));
+    std::vector<IcpState> h(sv->max_active);
+    O3G_TRY(cudaMemcpyAsync(h.data(), sv->states, sizeof(IcpState) * sv->max_active, cudaMemcpyDeviceToHost, s));
+    O3G_TRY(cudaStreamSynchronize(s));
+    for (int k : iterate) {
+      auto& sl = sv->slots[k];
+      sl.iters = h[k].iters;
+      sl.done = h[k].done != 0;
+      if (sl.done || sl.iters >= sl.max_iter) finishing.push_back(k);
+    }
+  }
+  int completed = 0;
+  if (!finishing.empty()) {
+    O3G_TRY_STATUS(launch_slots(sv, finishing, kEvaluate));
+    std::vector<IcpState> h(sv->max_active);
+    O3G_TRY(cudaMemcpyAsync(h.data(), sv->states, sizeof(IcpState) * sv->max_active, cudaMemcpyDeviceToHost, s));
+    std::vector<int> aux(8 * sv->max_active, 0);
+    for (int k : finishing)
+      O3G_TRY(cudaMemcpyAsync(aux.data() + 8 * k, sv->slots[k].src_aux, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
+    O3G_TRY(cudaStreamSynchronize(s));
+    for (int k : finishing) {
+      auto& sl = sv->slots[k];
+      o3g_server::Result res;
+      for (int q = 0; q < 16; ++q) res.T[q] = h[k].T[q];
+      res.fitness = h[k].fitness;
+      res.rmse = h[k].rmse;
+      res.iters = h[k].iters;
+      res.status = aux[8 * k + 6] || h[k].nonfinite ? O3G_ERR_NONFINITE
+                   : h[k].few_corr                  ? O3G_WARN_FEW_CORR
+                   : h[k].degenerate                ? O3G_WARN_DEGENERATE
+                                                    : O3G_OK;
+      sv->finished[sl.id] = res;
+      release_slot(sv, sl);
+      ++completed;
+    }
+  }
+  int active = 0;
+  for (const auto& sl : sv->slots) active += sl.used;
+  if (out_active) *out_active = active;
+  if (out_waiting) *out_waiting = static_cast<int32_t>(sv->waiting.size());
+  if (out_completed) *out_completed = completed;
+  return O3G_OK;
+}
+
+extern "C" int32_t o3g_server_poll(o3g_server* sv, int64_t id, int32_t* out_done, double* out_T, double* out_fitness,
+                                   double* out_rmse, int32_t* out_iters, int32_t* out_status) {
+  using namespace o3g;
+  if (!sv || !out_done) {
+    set_error("o3g_server_poll: invalid argument");
+    return O3G_ERR_ARG;
+  }
+  auto it = sv->finished.find(id);
+  if (it == sv->finished.end()) {
+    if (id < 0 || id >= sv->next_id) {
+      set_error("o3g_server_poll: unknown request %lld", static_cast<long long>(id));
+      return O3G_ERR_ARG;
+    }
+    *out_done = 0;
+    return O3G_OK;
+  }
+  const auto& r = it->second;
+  *out_done = 1;
+  if (out_T)
+    for (int k = 0; k < 16; ++k) out_T[k] = r.T[k];
+  if (out_fitness) *out_fitness = r.fitness;
+  if (out_rmse) *out_rmse = r.rmse;
+  if (out_iters) *out_iters = r.iters;
+  if (out_status) *out_status = r.status;
+  sv->finished.erase(it);
   return O3G_OK;
 }

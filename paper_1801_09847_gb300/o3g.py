@@ -60,6 +60,12 @@ _SIGNATURES = {
                                           _f64p, _f64p, _i32p, _vp], _i32),
     "o3g_icp_point_to_plane_batch": ([_i32, _vp, _vp, _vp, _vp, _f64p, _f64p, _i32, _f64, _f64p, _f64p, _f64p, _i32p,
                                       _i32p, _vp], _i32),
+    "o3g_server_create": ([_i32, _i64, _vp, ctypes.POINTER(_vp)], _i32),
+    "o3g_server_destroy": ([_vp], _i32),
+    "o3g_server_submit": ([_vp, _vp, _i64, _vp, _i64, _vp, _f32, _i32, _f64p, _f64, _i32, _f64,
+                           ctypes.POINTER(_i64)], _i32),
+    "o3g_server_step": ([_vp, _i32p, _i32p, _i32p], _i32),
+    "o3g_server_poll": ([_vp, _i64, _i32p, _f64p, _f64p, _f64p, _i32p, _i32p], _i32),
     "o3g_icp_point_to_plane_grid_noalloc": ([_vp, _vp, _i64, _i32, _f64p, _f64, _i32, _f64, _f64p, _f64p, _f64p,
                                              _i32p, _vp], _i32),
     "o3g_launch_count": ([], _i64),
@@ -295,6 +301,68 @@ def icp_point_to_plane_batch(grids, srcs, init_Ts, max_corr_dists, max_iter: int
                                               _stream(stream)), "o3g_icp_point_to_plane_batch")
     return [dict(status=int(status[k]), T=T[k].reshape(4, 4), fitness=float(fit[k]), rmse=float(rmse[k]),
                  iters=int(iters[k])) for k in range(n)]
+
+
+class Server:
+    """Continuous-batching registration server (o3g_server_*): submit, step, poll."""
+
+    def __init__(self, max_active: int = 64, hbm_budget_bytes: int = 8 << 30, stream=None):
+        h = _vp()
+        _check(lib().o3g_server_create(int(max_active), int(hbm_budget_bytes), _stream(stream), ctypes.byref(h)),
+               "o3g_server_create")
+        self._h = h
+
+    def close(self):
+        if self._h:
+            lib().o3g_server_destroy(self._h)
+            self._h = _vp(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _host(a, name):
+        if a is None:
+            return None, 0
+        arr = np.ascontiguousarray(a, dtype=np.float32)
+        if arr.size and (arr.ndim != 2 or arr.shape[1] != 3):
+            raise ValueError(f"{name} must be N x 3")
+        return arr, (arr.shape[0] if arr.size else 0)
+
+    def submit(self, src, tgt, tgt_nrm=None, init_T=None, max_corr_dist: float = 0.05, max_iter: int = 30,
+               eps: float = 0.0, normal_radius: float = 0.1, normal_max_nn: int = 30) -> int:
+        s, ns = self._host(src, "src")
+        t, nt = self._host(tgt, "tgt")
+        n, nn = self._host(tgt_nrm, "tgt_nrm")
+        if tgt_nrm is not None and nn != nt:
+            raise O3GError(ERR_ARG, "o3g_server_submit", "normals must match the target points one to one")
+        T0 = _pose(np.eye(4) if init_T is None else init_T)
+        rid = _i64()
+        _check(lib().o3g_server_submit(self._h, _vp(s.ctypes.data if ns else 0), ns, _vp(t.ctypes.data if nt else 0),
+                                       nt, _vp(n.ctypes.data) if n is not None and nn else _vp(0),
+                                       float(normal_radius), int(normal_max_nn), _pp(T0), float(max_corr_dist),
+                                       int(max_iter), float(eps), ctypes.byref(rid)), "o3g_server_submit")
+        return rid.value
+
+    def step(self):
+        """One scheduling step; returns (active, waiting, completed_this_step)."""
+        a, w, c = _i32(), _i32(), _i32()
+        _check(lib().o3g_server_step(self._h, ctypes.byref(a), ctypes.byref(w), ctypes.byref(c)), "o3g_server_step")
+        return a.value, w.value, c.value
+
+    def poll(self, rid: int):
+        """The result dict of a finished request (then forgotten), or None while it is in flight."""
+        done, st, iters = _i32(), _i32(), _i32()
+        T = np.zeros(16)
+        fit, rmse = _f64(), _f64()
+        _check(lib().o3g_server_poll(self._h, int(rid), ctypes.byref(done), _pp(T), ctypes.byref(fit),
+                                     ctypes.byref(rmse), ctypes.byref(iters), ctypes.byref(st)), "o3g_server_poll")
+        if not done.value:
+            return None
+        return dict(status=st.value, T=T.reshape(4, 4), fitness=fit.value, rmse=rmse.value, iters=iters.value)
 
 
 def icp_point_to_plane(src, tgt, tgt_nrm, init_T, max_corr_dist: float, max_iter: int) -> dict:
