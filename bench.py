@@ -127,6 +127,22 @@ def profiled_traffic(kernel_file: str, profile: str):
     return float(m_bytes.group(1))
 
 
+def max_over_ranks(value: float, dist, dev) -> float:
+    """The largest per-rank time: the job is as slow as its slowest rank."""
+    import torch
+    t = torch.tensor([float(value)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, dist, dev) -> float:
+    """Units processed by all ranks together (whole-job throughput numerator)."""
+    import torch
+    t = torch.tensor([float(value)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t)
+    return float(t.item())
+
+
 def make_pair(rank: int):
     from paper_1801_09847_gb300 import synth
     return synth.room_frame_pair(seed=2 + rank)
@@ -195,9 +211,7 @@ def run_ours(args, ws, rank, local):
                             ("normals", o3g.KERNEL_NORMALS), ("grid", o3g.KERNEL_GRID)):
                 kern[name] = o3g.timing_read(k, reset=True)
         if dist:
-            t = torch.tensor([total], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+            total = max_over_ranks(total, dist, dev)
         return total, launches, kern, out
 
     sampler = ClockSampler(local) if rank == 0 else None
@@ -222,12 +236,7 @@ def run_ours(args, ws, rank, local):
     units_rank = ns * iters
     ms_step = total_ms / args.steps
     # weak scaling: every rank registers its own pair of the same size class
-    if dist:
-        u = torch.tensor([float(units_rank)], device=dev, dtype=torch.float64)
-        dist.all_reduce(u)
-        units = float(u.item())
-    else:
-        units = float(units_rank)
+    units = sum_over_ranks(float(units_rank), dist, dev) if dist else float(units_rank)
     value = units / (ms_step / 1e3)
     e2e_value = units / (e2e_ms / args.steps / 1e3)
 
@@ -363,6 +372,87 @@ def run_batched(args, ws, rank, local):
         print(json.dumps(line))
 
 
+# ---------------------------------------------------------- serving workload
+
+SERVE_WORKLOAD = ("registration requests, sphere-plus-plane pairs with sizes log-uniform in 5k-500k points, "
+                  "Poisson arrivals, analytic target normals, point-to-plane ICP max_corr_dist 0.05 run to "
+                  "convergence (max(|w|, |t|) < 1e-6, at most 100 iterations); continuous batching server")
+
+
+def run_serving(args, ws, rank, local):
+    """Open-loop serving: Poisson arrivals at fractions of the measured saturated rate; p50/p99 latency."""
+    import torch
+
+    from paper_1801_09847_gb300 import build, o3g, synth
+
+    build.build()
+    torch.cuda.set_device(local)
+    g = synth.rng(5 + rank)
+    sizes = synth.log_uniform_sizes(args.serve_requests, 5000, 500000, g)
+    reqs = [synth.sphere_plane_pair(int(n), seed=20000 + 100000 * rank + k) for k, n in enumerate(sizes)]
+    budget = int(args.serve_budget_gb * (1 << 30))
+
+    def serve(arrivals):
+        sv = o3g.Server(max_active=args.serve_slots, hbm_budget_bytes=budget)
+        ids, done_at, submitted_at = {}, {}, {}
+        order = np.argsort(arrivals, kind="stable")
+        nxt, n = 0, len(reqs)
+        t0 = time.perf_counter()
+        steps = 0
+        while len(done_at) < n:
+            now = time.perf_counter() - t0
+            while nxt < n and arrivals[order[nxt]] <= now:
+                k = int(order[nxt])
+                pr = reqs[k]
+                ids[sv.submit(pr.src, pr.tgt, pr.tgt_nrm, np.eye(4), 0.05, 100, eps=1e-6)] = k
+                submitted_at[k] = now
+                nxt += 1
+            active, waiting, completed = sv.step()
+            steps += 1
+            if completed:
+                t = time.perf_counter() - t0
+                for rid in sv.completed():
+                    r = sv.poll(rid)
+                    done_at[ids[rid]] = (t, r)
+            elif active == 0 and waiting == 0 and nxt < n:
+                time.sleep(max(0.0, min(1e-3, arrivals[order[nxt]] - (time.perf_counter() - t0))))
+        elapsed = time.perf_counter() - t0
+        sv.close()
+        lat = np.array([done_at[k][0] - arrivals[k] for k in range(n)])
+        iters = sum(done_at[k][1]["iters"] for k in range(n))
+        pts = sum(len(reqs[k].src) * done_at[k][1]["iters"] for k in range(n))
+        return dict(elapsed_s=elapsed, pairs_per_s=n / elapsed, point_pairs_per_s=pts / elapsed,
+                    p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
+                    mean_iters=iters / n, steps=steps), {k: done_at[k][1] for k in range(n)}
+
+    # saturated: every request waiting at t = 0
+    sat, res_sat = serve(np.zeros(len(reqs)))
+    out = {"saturated": sat}
+    for frac in (0.5, 0.9):
+        rate = frac * sat["pairs_per_s"]
+        gaps = synth.rng(77).exponential(1.0 / rate, len(reqs))
+        st, res = serve(np.cumsum(gaps) - gaps[0])
+        st["arrival_rate_per_s"] = rate
+        st["results_equal_saturated"] = all(np.array_equal(res[k]["T"], res_sat[k]["T"]) for k in res)
+        out[f"poisson_{frac}"] = st
+    # the plain single-request loop on the same requests
+    t0 = time.perf_counter()
+    single = [o3g.register_point_to_plane_host(pr.src, pr.tgt, pr.tgt_nrm, np.eye(4), 0.05, 100, eps=1e-6)
+              for pr in reqs]
+    t_single = time.perf_counter() - t0
+    out["single_request_loop"] = {"pairs_per_s": len(reqs) / t_single,
+                                  "results_equal_served": all(np.array_equal(a["T"], res_sat[k]["T"])
+                                                              for k, a in enumerate(single))}
+    line = {"metric": "served registrations/s (p50/p99 latency)", "value": out["poisson_0.9"]["pairs_per_s"],
+            "unit": "pairs/s", "n_gpus": ws, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": SERVE_WORKLOAD, "requests": len(reqs), "slots": args.serve_slots,
+                       "hbm_budget_gb": args.serve_budget_gb, "n_source_total": int(sum(sizes))},
+            "serving": out}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 # ------------------------------------------------------------ CPU oracle
 
 
@@ -433,8 +523,12 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["rgbd_frame", "batched"], default="rgbd_frame",
-                    help="rgbd_frame: the headline single-pair line; batched: 256 uneven pairs per call")
+    ap.add_argument("--workload", choices=["rgbd_frame", "batched", "serving"], default="rgbd_frame",
+                    help="rgbd_frame: the headline single-pair line; batched: 256 uneven pairs per call; "
+                         "serving: continuous-batching server under Poisson arrivals")
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-slots", type=int, default=256)
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--batch-pairs", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
@@ -448,6 +542,8 @@ def main():
         run_reference(args, ws, rank, local)
     elif args.workload == "batched":
         run_batched(args, ws, rank, local)
+    elif args.workload == "serving":
+        run_serving(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

@@ -230,6 +230,8 @@ O3G_API int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid* co
  *   o3g_server_poll sets *out_done; when done it fills the results (as
  *   o3g_icp_point_to_plane_grid; out_status holds the request's status) and
  *   forgets the request.
+ *   o3g_server_completed lists (up to cap, ascending) the ids of finished
+ *   requests that have not been polled yet.
  */
 typedef struct o3g_server o3g_server;
 O3G_API int32_t o3g_server_create(int32_t max_active, int64_t hbm_budget_bytes, void* stream, o3g_server** out);
@@ -242,6 +244,7 @@ O3G_API int32_t o3g_server_step(o3g_server* server, int32_t* out_active, int32_t
                                 int32_t* out_completed);
 O3G_API int32_t o3g_server_poll(o3g_server* server, int64_t id, int32_t* out_done, double* out_T,
                                 double* out_fitness, double* out_rmse, int32_t* out_iters, int32_t* out_status);
+O3G_API int32_t o3g_server_completed(o3g_server* server, int64_t* ids, int32_t cap, int32_t* out_n);
 
 /*
  * Allocation-free form of o3g_icp_point_to_plane_grid.  The paper has no

@@ -1619,3 +1619,18 @@ extern "C" int32_t o3g_server_poll(o3g_server* sv, int64_t id, int32_t* out_done
   sv->finished.erase(it);
   return O3G_OK;
 }
+
+extern "C" int32_t o3g_server_completed(o3g_server* sv, int64_t* ids, int32_t cap, int32_t* out_n) {
+  using namespace o3g;
+  if (!sv || !out_n || cap < 0 || (cap > 0 && !ids)) {
+    set_error("o3g_server_completed: invalid argument");
+    return O3G_ERR_ARG;
+  }
+  int32_t n = 0;
+  for (const auto& kv : sv->finished) {
+    if (n >= cap) break;
+    ids[n++] = kv.first;
+  }
+  *out_n = n;
+  return O3G_OK;
+}

@@ -66,6 +66,7 @@ _SIGNATURES = {
                            ctypes.POINTER(_i64)], _i32),
     "o3g_server_step": ([_vp, _i32p, _i32p, _i32p], _i32),
     "o3g_server_poll": ([_vp, _i64, _i32p, _f64p, _f64p, _f64p, _i32p, _i32p], _i32),
+    "o3g_server_completed": ([_vp, _vp, _i32, _i32p], _i32),
     "o3g_icp_point_to_plane_grid_noalloc": ([_vp, _vp, _i64, _i32, _f64p, _f64, _i32, _f64, _f64p, _f64p, _f64p,
                                              _i32p, _vp], _i32),
     "o3g_launch_count": ([], _i64),
@@ -352,6 +353,14 @@ class Server:
         a, w, c = _i32(), _i32(), _i32()
         _check(lib().o3g_server_step(self._h, ctypes.byref(a), ctypes.byref(w), ctypes.byref(c)), "o3g_server_step")
         return a.value, w.value, c.value
+
+    def completed(self, cap: int = 4096) -> list:
+        """Ids of finished requests not yet polled."""
+        ids = np.zeros(cap, np.int64)
+        n = _i32()
+        _check(lib().o3g_server_completed(self._h, ids.ctypes.data_as(_vp), int(cap), ctypes.byref(n)),
+               "o3g_server_completed")
+        return ids[: n.value].tolist()
 
     def poll(self, rid: int):
         """The result dict of a finished request (then forgotten), or None while it is in flight."""
