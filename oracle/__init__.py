@@ -74,6 +74,14 @@ def _load():
                                            ctypes.c_double, _i32, _f64p, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]
     lib.ora_icp_point_to_plane.restype = ctypes.c_int
+    lib.ora_icp_point_to_plane_gridnn.argtypes = lib.ora_icp_point_to_plane.argtypes
+    lib.ora_icp_point_to_plane_gridnn.restype = ctypes.c_int
+    lib.ora_grid_build.argtypes = [_f32p, _i64, ctypes.c_float]
+    lib.ora_grid_build.restype = ctypes.c_void_p
+    lib.ora_grid_free.argtypes = [ctypes.c_void_p]
+    lib.ora_grid_free.restype = None
+    lib.ora_grid_nn.argtypes = [ctypes.c_void_p, _f32p, _i64, _i32, _i32p, _f32p]
+    lib.ora_grid_nn.restype = ctypes.c_int
     lib.ora_knn_hybrid.argtypes = [_f32p, _i64, _f32p, _i64, ctypes.c_float, _i32, _i32, _i32p, _f32p, _i32p]
     lib.ora_knn_hybrid.restype = ctypes.c_int
     lib.ora_jacobi_eig3.argtypes = [_f64p, _f64p, _f64p]
@@ -115,17 +123,34 @@ def transform(src, T) -> np.ndarray:
     return out
 
 
-def nn(p, tgt, r_max: float, threads: int | None = None):
+def nn(p, tgt, r_max: float, threads: int | None = None, method: str = "brute"):
     """Step a4: brute-force fixed-radius nearest neighbour, lowest index on ties.
 
     Follows registration_icp's max_correspondence_distance (Sec. 3.3).  Returns
     (corr int32[N], d2 float32[N]); corr = -1 where no target lies within r_max.
+    method="grid" answers the same map through the exact 27-cell grid search of
+    ``ora_grid_nn`` (pinned bit-exact against the scan); it needs r_max > 0.
     """
     p, tgt = _pts(p), _pts(tgt)
     corr = np.empty(len(p), np.int32)
     d2 = np.empty(len(p), np.float32)
     if len(p) == 0:
         return corr, d2
+    if method == "grid":
+        lib = _load()
+        g = lib.ora_grid_build(tgt if len(tgt) else np.zeros((1, 3), np.float32), len(tgt),
+                               ctypes.c_float(np.float32(r_max)))
+        if not g:
+            raise ValueError("ora_grid_build failed (r_max must be positive and finite)")
+        try:
+            st = lib.ora_grid_nn(g, p, len(p), threads or default_threads(), corr, d2)
+        finally:
+            lib.ora_grid_free(g)
+        if st != OK:
+            raise ValueError(f"ora_grid_nn status {st}")
+        return corr, d2
+    if method != "brute":
+        raise ValueError(f"unknown NN method {method!r}")
     st = _load().ora_nn(p, len(p), tgt if len(tgt) else np.zeros((1, 3), np.float32), len(tgt),
                         ctypes.c_float(np.float32(r_max)), threads or default_threads(), corr, d2)
     if st != OK:
@@ -173,18 +198,24 @@ def delta_T(xi):
 
 
 def icp_point_to_plane(src, tgt, tgt_nrm, init_T, max_corr_dist: float, max_iter: int, eps: float = 0.0,
-                       threads: int | None = None) -> dict:
+                       threads: int | None = None, nn_method: str = "brute") -> dict:
     """registration_icp(..., TransformationEstimationPointToPlane()) (Sec. 3.3), steps a3..a7.
 
-    Returns dict(status, T (4x4 FP64), fitness, rmse, iters).
+    Returns dict(status, T (4x4 FP64), fitness, rmse, iters).  nn_method="grid"
+    takes the correspondences from the exact grid search (same result; for clouds
+    too large to scan).
     """
+    if nn_method not in ("brute", "grid"):
+        raise ValueError(f"unknown NN method {nn_method!r}")
     src, tgt, tgt_nrm = _pts(src), _pts(tgt), _pts(tgt_nrm)
     if len(tgt_nrm) != len(tgt):
         raise ValueError("target normals must have as many records as target points (Sec. 3.1)")
     T = np.zeros(16, np.float64)
     fit, rmse, iters = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
     one = np.zeros((1, 3), np.float32)
-    st = _load().ora_icp_point_to_plane(src if len(src) else one, len(src), tgt if len(tgt) else one, len(tgt),
+    lib = _load()
+    fn = lib.ora_icp_point_to_plane_gridnn if nn_method == "grid" else lib.ora_icp_point_to_plane
+    st = fn(src if len(src) else one, len(src), tgt if len(tgt) else one, len(tgt),
                                         tgt_nrm if len(tgt_nrm) else one, _pose(init_T).ravel(),
                                         float(max_corr_dist), int(max_iter), float(eps),
                                         threads or default_threads(), T, ctypes.byref(fit), ctypes.byref(rmse),

@@ -58,6 +58,8 @@
 #define ORA_ERR_ARG (-1)
 #define ORA_ERR_OOM (-2)
 
+typedef struct ora_grid ora_grid;
+
 /* ------------------------------------------------------------------ threads */
 
 typedef void (*range_fn)(void* ctx, int64_t lo, int64_t hi);
@@ -167,6 +169,144 @@ int ora_nn(const float* p, int64_t ns, const float* tgt, int64_t nt, float r_max
   if (ns < 0 || nt < 0 || nt > INT32_MAX || !(r_max >= 0.0f)) return ORA_ERR_ARG;
   nn_ctx c = {p, tgt, nt, r_max * r_max, corr, d2};
   parallel_for(ns, nthreads, nn_range, &c);
+  return ORA_OK;
+}
+
+/* ------------------------------------- a4 at scale: exact grid-accelerated NN */
+
+/* The same map as ora_nn, bit for bit, for clouds too large to scan in full.
+ * Targets are bucketed in a uniform grid of cell h = 1.01 r_max, cell index
+ * floor(x / h) per axis.  Why no match can be missed: a target with FP32
+ * d2 <= fl(r_max)^2 differs from p by at most (1 + 1e-6) r_max in each
+ * coordinate (the FP32 distance formula loses a few ulps at most), which is
+ * below h, so its cell index differs from p's by at most 1 on every axis and it
+ * lies in one of the 27 cells around p's cell.  The candidates of those cells
+ * are compared by (d2, j) explicitly, so the order of the scan does not matter.
+ * Targets with a non-finite coordinate never match in ora_nn (their d2 is not
+ * <= r2) and are left out.  This is an acceleration of ora_nn, not a separate
+ * definition: the pins compare the two on every input class. */
+
+typedef struct {
+  int64_t c[3];
+  int32_t j;
+} gcell;
+
+struct ora_grid {
+  const float* tgt;
+  double inv_h;
+  float r2;
+  int64_t n;   /* bucketed (finite) targets */
+  gcell* cells; /* sorted by (c[0], c[1], c[2], j) */
+};
+
+static int gcell_cmp(const void* a, const void* b) {
+  const gcell* x = (const gcell*)a;
+  const gcell* y = (const gcell*)b;
+  for (int k = 0; k < 3; ++k) {
+    if (x->c[k] < y->c[k]) return -1;
+    if (x->c[k] > y->c[k]) return 1;
+  }
+  return (x->j > y->j) - (x->j < y->j);
+}
+
+/* floor(x / h) as an integer; clamping to +-2^62 is monotone and never moves two
+ * indices further apart, so the 27-cell argument still holds. */
+static int64_t cell_index(float x, double inv_h) {
+  double v = floor((double)x * inv_h);
+  if (v > 4611686018427387904.0) v = 4611686018427387904.0;
+  if (v < -4611686018427387904.0) v = -4611686018427387904.0;
+  return (int64_t)v;
+}
+
+static int finite3(const float* x) { return isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]); }
+
+ora_grid* ora_grid_build(const float* tgt, int64_t nt, float r_max) {
+  if (nt < 0 || nt > INT32_MAX || !(r_max > 0.0f) || !isfinite(r_max)) return NULL;
+  ora_grid* g = (ora_grid*)calloc(1, sizeof(ora_grid));
+  if (!g) return NULL;
+  g->tgt = tgt;
+  g->inv_h = 1.0 / (1.01 * (double)r_max);
+  g->r2 = r_max * r_max;
+  g->cells = (gcell*)malloc(sizeof(gcell) * (size_t)(nt > 0 ? nt : 1));
+  if (!g->cells) {
+    free(g);
+    return NULL;
+  }
+  int64_t m = 0;
+  for (int64_t j = 0; j < nt; ++j) {
+    const float* q = tgt + 3 * j;
+    if (!finite3(q)) continue;
+    for (int k = 0; k < 3; ++k) g->cells[m].c[k] = cell_index(q[k], g->inv_h);
+    g->cells[m].j = (int32_t)j;
+    ++m;
+  }
+  g->n = m;
+  qsort(g->cells, (size_t)m, sizeof(gcell), gcell_cmp);
+  return g;
+}
+
+void ora_grid_free(ora_grid* g) {
+  if (!g) return;
+  free(g->cells);
+  free(g);
+}
+
+/* First bucketed target whose cell is >= c (binary search). */
+static int64_t cell_lower_bound(const ora_grid* g, const int64_t c[3]) {
+  int64_t lo = 0, hi = g->n;
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    const int64_t* m = g->cells[mid].c;
+    int less = m[0] < c[0] || (m[0] == c[0] && (m[1] < c[1] || (m[1] == c[1] && m[2] < c[2])));
+    if (less) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+typedef struct {
+  const ora_grid* g;
+  const float* p;
+  int32_t* corr;
+  float* d2;
+} gnn_ctx;
+
+static void gnn_range(void* vctx, int64_t lo, int64_t hi) {
+  gnn_ctx* c = (gnn_ctx*)vctx;
+  const ora_grid* g = c->g;
+  for (int64_t i = lo; i < hi; ++i) {
+    const float* p = c->p + 3 * i;
+    int64_t best = -1;
+    float best_d2 = 0.0f;
+    if (finite3(p)) {
+      int64_t pc[3];
+      for (int k = 0; k < 3; ++k) pc[k] = cell_index(p[k], g->inv_h);
+      for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dz = -1; dz <= 1; ++dz) {
+            int64_t nc[3] = {pc[0] + dx, pc[1] + dy, pc[2] + dz};
+            for (int64_t e = cell_lower_bound(g, nc); e < g->n; ++e) {
+              const gcell* q = &g->cells[e];
+              if (q->c[0] != nc[0] || q->c[1] != nc[1] || q->c[2] != nc[2]) break;
+              float d2 = dist2_f32(p, g->tgt + 3 * (int64_t)q->j);
+              if (!(d2 <= g->r2)) continue;
+              if (best < 0 || d2 < best_d2 || (d2 == best_d2 && q->j < best)) {
+                best = q->j;
+                best_d2 = d2;
+              }
+            }
+          }
+    }
+    c->corr[i] = (int32_t)best;
+    c->d2[i] = best < 0 ? 0.0f : best_d2;
+  }
+}
+
+/* ora_nn against a grid built over the target with the same r_max. */
+int ora_grid_nn(const ora_grid* g, const float* p, int64_t ns, int32_t nthreads, int32_t* corr, float* d2) {
+  if (!g || ns < 0) return ORA_ERR_ARG;
+  gnn_ctx c = {g, p, corr, d2};
+  parallel_for(ns, nthreads, gnn_range, &c);
   return ORA_OK;
 }
 
@@ -296,14 +436,11 @@ void ora_delta_T(const double xi[6], double dT[16]) {
 
 /* --------------------------------------------------- the ICP loop, a3..a7 */
 
-/* Point-to-plane ICP (Sec. 3.3, Eq. 1-2).  Clouds are packed xyz FP32.
- * Returns ORA_OK, ORA_WARN_DEGENERATE (some pivot was frozen),
- * ORA_WARN_FEW_CORR (stopped with < 6 correspondences), or an error. */
-int ora_icp_point_to_plane(const float* src, int64_t ns, const float* tgt, int64_t nt, const float* tgt_nrm,
-                           const double init_T[16], double max_corr_dist, int32_t max_iter, double eps,
-                           int32_t nthreads, double out_T[16], double* out_fitness, double* out_rmse,
-                           int32_t* out_iters) {
-  if (ns < 0 || nt < 0 || nt > INT32_MAX || max_iter < 0 || !(max_corr_dist >= 0.0)) return ORA_ERR_ARG;
+/* The ICP loop, steps a3..a7; grid == NULL scans every target (ora_nn). */
+static int icp_impl(const float* src, int64_t ns, const float* tgt, int64_t nt, const float* tgt_nrm,
+                    const double init_T[16], double max_corr_dist, int32_t max_iter, double eps, int32_t nthreads,
+                    const ora_grid* grid, double out_T[16], double* out_fitness, double* out_rmse,
+                    int32_t* out_iters) {
   float r_max = (float)max_corr_dist;
   int64_t nalloc = ns > 0 ? ns : 1;
   float* p = (float*)malloc(sizeof(float) * 3 * nalloc);
@@ -322,7 +459,8 @@ int ora_icp_point_to_plane(const float* src, int64_t ns, const float* tgt, int64
   int64_t count;
   for (int k = 0; k < max_iter; ++k) {
     ora_transform(src, ns, T, p);
-    ora_nn(p, ns, tgt, nt, r_max, nthreads, corr, d2);
+    if (grid) ora_grid_nn(grid, p, ns, nthreads, corr, d2);
+    else ora_nn(p, ns, tgt, nt, r_max, nthreads, corr, d2);
     ora_normal_equations(p, ns, tgt, tgt_nrm, corr, d2, A, b, &sum_r2, &sum_d2, &count);
     if (count < 6) {
       status = ORA_WARN_FEW_CORR;
@@ -339,7 +477,8 @@ int ora_icp_point_to_plane(const float* src, int64_t ns, const float* tgt, int64
   }
   /* a7: evaluation at the final pose */
   ora_transform(src, ns, T, p);
-  ora_nn(p, ns, tgt, nt, r_max, nthreads, corr, d2);
+  if (grid) ora_grid_nn(grid, p, ns, nthreads, corr, d2);
+  else ora_nn(p, ns, tgt, nt, r_max, nthreads, corr, d2);
   ora_normal_equations(p, ns, tgt, tgt_nrm, corr, d2, A, b, &sum_r2, &sum_d2, &count);
   memcpy(out_T, T, sizeof(T));
   *out_fitness = ns > 0 ? (double)count / (double)ns : 0.0;
@@ -350,6 +489,35 @@ int ora_icp_point_to_plane(const float* src, int64_t ns, const float* tgt, int64
   free(d2);
   if (status == ORA_OK && degenerate) status = ORA_WARN_DEGENERATE;
   return status;
+}
+
+/* Point-to-plane ICP (Sec. 3.3, Eq. 1-2).  Clouds are packed xyz FP32.
+ * Returns ORA_OK, ORA_WARN_DEGENERATE (some pivot was frozen),
+ * ORA_WARN_FEW_CORR (stopped with < 6 correspondences), or an error. */
+int ora_icp_point_to_plane(const float* src, int64_t ns, const float* tgt, int64_t nt, const float* tgt_nrm,
+                           const double init_T[16], double max_corr_dist, int32_t max_iter, double eps,
+                           int32_t nthreads, double out_T[16], double* out_fitness, double* out_rmse,
+                           int32_t* out_iters) {
+  if (ns < 0 || nt < 0 || nt > INT32_MAX || max_iter < 0 || !(max_corr_dist >= 0.0)) return ORA_ERR_ARG;
+  return icp_impl(src, ns, tgt, nt, tgt_nrm, init_T, max_corr_dist, max_iter, eps, nthreads, NULL, out_T,
+                  out_fitness, out_rmse, out_iters);
+}
+
+/* The same ICP with the correspondence step answered by the exact grid search
+ * (identical correspondences, hence an identical result); for large clouds. */
+int ora_icp_point_to_plane_gridnn(const float* src, int64_t ns, const float* tgt, int64_t nt, const float* tgt_nrm,
+                                  const double init_T[16], double max_corr_dist, int32_t max_iter, double eps,
+                                  int32_t nthreads, double out_T[16], double* out_fitness, double* out_rmse,
+                                  int32_t* out_iters) {
+  if (ns < 0 || nt < 0 || nt > INT32_MAX || max_iter < 0 || !((float)max_corr_dist > 0.0f) ||
+      !isfinite((float)max_corr_dist))
+    return ORA_ERR_ARG;
+  ora_grid* g = ora_grid_build(tgt, nt, (float)max_corr_dist);
+  if (!g) return ORA_ERR_OOM;
+  int st = icp_impl(src, ns, tgt, nt, tgt_nrm, init_T, max_corr_dist, max_iter, eps, nthreads, g, out_T,
+                    out_fitness, out_rmse, out_iters);
+  ora_grid_free(g);
+  return st;
 }
 
 /* ------------------------------------------------ a2: hybrid kNN and normals */

@@ -16,6 +16,8 @@ uneven size.  All randomness is numpy PCG64 with a stated seed.
 from __future__ import annotations
 
 import math
+import os
+import tempfile
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -254,6 +256,160 @@ def room_frame_pair(seed: int = 2, deg: float = 3.0, trans: float = 0.05, voxel:
     src = src[g.permutation(len(src))]
     return Pair(src.astype(np.float32), tgt.astype(np.float32), None, P, max_corr_dist, max_iter,
                 f"room_frame_s{seed}", extra=dict(viewpoint=(0.0, 0.0, 0.0)))
+
+
+# ------------------------------------------------------- fused scene fragments
+
+
+def _ray_cast_normals(room: Room, origin: np.ndarray, dirs: np.ndarray):
+    """Distance along each ray to the first surface and that surface's unit normal (facing the camera)."""
+    o = origin[None, :]
+    n = len(dirs)
+    ar = np.arange(n)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = 1.0 / dirs
+        t_wall = np.where(dirs > 0, (room.half - o) * inv, np.where(dirs < 0, (-room.half - o) * inv, np.inf))
+        ax = np.argmin(t_wall, axis=1)
+        best = t_wall[ar, ax]
+        nrm = np.zeros((n, 3))
+        nrm[ar, ax] = -np.sign(dirs[ar, ax])
+        for lo, hi in zip(room.boxes_lo, room.boxes_hi):
+            t1 = (lo[None, :] - o) * inv
+            t2 = (hi[None, :] - o) * inv
+            t_near = np.minimum(t1, t2)
+            axb = np.argmax(t_near, axis=1)  # the entry face
+            tmin = t_near[ar, axb]
+            tmax = np.min(np.maximum(t1, t2), axis=1)
+            hit = (tmax >= tmin) & (tmin > 1e-6) & (tmin < best)
+            best = np.where(hit, tmin, best)
+            idx = np.nonzero(hit)[0]
+            nrm[idx] = 0.0
+            nrm[idx, axb[idx]] = -np.sign(dirs[idx, axb[idx]])
+        a = np.sum(dirs * dirs, axis=1)
+        for c, r in zip(room.sph_c, room.sph_r):
+            oc = o[0] - c
+            b = 2.0 * (dirs @ oc)
+            cc = float(oc @ oc) - r * r
+            disc = b * b - 4 * a * cc
+            t0 = (-b - np.sqrt(np.maximum(disc, 0.0))) / (2 * a)
+            hit = (disc >= 0) & (t0 > 1e-6) & (t0 < best)
+            best = np.where(hit, t0, best)
+            idx = np.nonzero(hit)[0]
+            nrm[idx] = (o + t0[idx, None] * dirs[idx] - c[None, :]) / r
+    return best, nrm
+
+
+def pan_trajectory(count: int, radius: float, phase: float, pitch_deg: float) -> list:
+    """Camera-to-world poses panning once around the room's vertical (y) axis.
+
+    Camera k sits on a circle of `radius` about the centre, yawed by 2 pi k /
+    count + phase and pitched by pitch_deg * sin(4 pi k / count), so the segment
+    sees the walls all round plus parts of floor and ceiling.
+    """
+    poses = []
+    for k in range(count):
+        yaw = 2.0 * math.pi * k / count + phase
+        pitch = math.radians(pitch_deg) * math.sin(4.0 * math.pi * k / count)
+        R = axis_angle_matrix([0.0, 1.0, 0.0], yaw) @ axis_angle_matrix([1.0, 0.0, 0.0], pitch)
+        poses.append(make_T(R, [radius * math.cos(yaw), 0.0, radius * math.sin(yaw)]))
+    return poses
+
+
+def _render_world(args):
+    """One depth frame of a fused segment: world-frame points and analytic normals of its valid pixels."""
+    room, cam_to_world, seed_words, noise_k, intr = args
+    g = np.random.Generator(np.random.PCG64(np.random.SeedSequence(seed_words)))
+    W, H = intr["width"], intr["height"]
+    u, v = np.meshgrid(np.arange(W, dtype=np.float64), np.arange(H, dtype=np.float64))
+    d_cam = np.stack([(u - intr["cx"]) / intr["fx"], (v - intr["cy"]) / intr["fy"], np.ones_like(u)], -1)
+    d_cam = d_cam.reshape(-1, 3)
+    R, t = cam_to_world[:3, :3], cam_to_world[:3, 3]
+    depth, nrm = _ray_cast_normals(room, t, d_cam @ R.T)
+    z = depth + g.normal(0.0, 1.0, depth.shape) * noise_k * depth * depth
+    ok = np.isfinite(z) & (z > 0)
+    return (d_cam[ok] * z[ok, None]) @ R.T + t, nrm[ok]
+
+
+def voxel_centroids_normals(pts: np.ndarray, nrm: np.ndarray, voxel: float):
+    """Fusion into a voxel grid: per occupied voxel the centroid of its points and the normalised mean of
+    their analytic normals.  Output order is by packed voxel key."""
+    keys = np.floor(pts / voxel).astype(np.int64)
+    keys -= keys.min(axis=0)
+    span = keys.max(axis=0) + 1
+    lin = (keys[:, 0] * span[1] + keys[:, 1]) * span[2] + keys[:, 2]
+    uniq, inv = np.unique(lin, return_inverse=True)
+    cnt = np.bincount(inv, minlength=len(uniq)).astype(np.float64)
+    c = np.empty((len(uniq), 3))
+    m = np.empty((len(uniq), 3))
+    for a in range(3):
+        c[:, a] = np.bincount(inv, weights=pts[:, a], minlength=len(uniq)) / cnt
+        m[:, a] = np.bincount(inv, weights=nrm[:, a], minlength=len(uniq))
+    norm = np.linalg.norm(m, axis=1, keepdims=True)
+    m = np.where(norm > 0, m / np.where(norm > 0, norm, 1.0), np.array([0.0, 0.0, 1.0]))
+    return c, m
+
+
+def fuse_segment(room: Room, poses: list, seed_words: tuple, voxel: float, noise_k: float = 0.001,
+                 workers: int | None = None, intr: dict = PRIMESENSE):
+    """Ray-cast every pose of a trajectory segment, move the points to world coordinates and fuse them at
+    `voxel` m.  Frame k draws its depth noise from SeedSequence(seed_words + (k,)), so the result does not
+    depend on `workers` (frames are rendered in a spawn-context process pool when workers > 1)."""
+    jobs = [(room, T, tuple(seed_words) + (k,), noise_k, intr) for k, T in enumerate(poses)]
+    if workers is None:
+        workers = min(16, len(jobs), os.cpu_count() or 1)
+    if workers > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            frames = list(ex.map(_render_world, jobs))
+    else:
+        frames = [_render_world(j) for j in jobs]
+    pts = np.concatenate([f[0] for f in frames])
+    nrm = np.concatenate([f[1] for f in frames])
+    return voxel_centroids_normals(pts, nrm, voxel)
+
+
+def fragment_pair(n: int = 2_000_000, seed: int = 4, frames: int = 50, voxel: float = 0.005, deg: float = 1.0,
+                  trans: float = 0.01, max_corr_dist: float = 0.02, max_iter: int = 50,
+                  workers: int | None = None, cache: bool = True) -> Pair:
+    """Scene-fragment pair: two fused fragments of one furnished room, `n` points each.
+
+    Each fragment fuses `frames` 640 x 480 depth frames of a panning trajectory
+    segment (pan_trajectory; segment 1 on a 0.30 m circle, segment 2 on a 0.35 m
+    circle half a step out of phase, so the two sample the same surfaces
+    differently) at `voxel` m, then keeps a seeded subset of exactly `n` voxels.
+    Target = fragment 1 in world coordinates with its fused analytic normals;
+    source = fragment 2 mapped by the inverse of T_gt (a `deg` degree / `trans` m
+    perturbation), so T_gt maps source to target coordinates.  The result is
+    cached in the system temp directory under a key of all parameters.
+    """
+    key = f"fragment_n{n}_s{seed}_f{frames}_v{voxel}_d{deg}_t{trans}"
+    path = os.path.join(tempfile.gettempdir(), "o3g_synth_cache", key + ".npz")
+    if cache and os.path.exists(path):
+        z = np.load(path)
+        src, tgt, nrm, T = z["src"], z["tgt"], z["nrm"], z["T"]
+    else:
+        g = rng(seed)
+        seg1 = pan_trajectory(frames, 0.30, 0.0, 30.0)
+        seg2 = pan_trajectory(frames, 0.35, math.pi / frames, 30.0)
+        room = make_room(g, keep_clear=[T[:3, 3] for T in seg1 + seg2])
+        T = perturbation(g, deg, trans)
+        c1, n1 = fuse_segment(room, seg1, (seed, 1), voxel, workers=workers)
+        c2, _ = fuse_segment(room, seg2, (seed, 2), voxel, workers=workers)
+        if len(c1) < n or len(c2) < n:
+            raise ValueError(f"fragments hold {len(c1)} and {len(c2)} voxels, fewer than {n}")
+        k1 = g.choice(len(c1), n, replace=False)
+        k2 = g.choice(len(c2), n, replace=False)
+        tgt = c1[k1].astype(np.float32)
+        nrm = n1[k1].astype(np.float32)
+        src = apply_T(inv_T(T), c2[k2]).astype(np.float32)
+        if cache:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tmp = path + f".{os.getpid()}.npz"
+            np.savez(tmp, src=src, tgt=tgt, nrm=nrm, T=T)
+            os.replace(tmp, path)
+    return Pair(src, tgt, nrm, T, max_corr_dist, max_iter, f"fragment_{n}_s{seed}",
+                extra=dict(viewpoint=(0.0, 0.0, 0.0)))
 
 
 # ------------------------------------------------------------------ batches

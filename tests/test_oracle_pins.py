@@ -106,6 +106,89 @@ def test_nn_empty_target(ora):
     assert np.all(corr == -1)
 
 
+# ------------------------------- a4 at scale: the exact grid search of the oracle
+
+
+@pytest.mark.parametrize("ns,nt,r,span", [(3000, 3000, 0.05, 1.0), (2000, 5000, 0.2, 1.0), (500, 400, 1.5, 1.0),
+                                          (4000, 4000, 0.003, 0.1)])
+def test_grid_nn_equals_bruteforce_bitexact(ora, ns, nt, r, span):
+    """The grid search is an acceleration of the scan: identical indices and d2 (ties, far points included)."""
+    g = synth.rng(700 + ns + nt)
+    tgt = g.uniform(-span, span, (nt, 3)).astype(np.float32)
+    tgt = np.vstack([tgt, tgt[: nt // 5]])  # exact duplicates: the lower index must win
+    p = g.uniform(-1.2 * span, 1.2 * span, (ns, 3)).astype(np.float32)
+    p[: ns // 3] = tgt[g.integers(0, nt, ns // 3)] + g.normal(0, r / 3, (ns // 3, 3)).astype(np.float32)
+    c1, d1 = ora.nn(p, tgt, r, threads=4)
+    c2, d2 = ora.nn(p, tgt, r, threads=3, method="grid")
+    assert np.array_equal(c1, c2) and np.array_equal(d1, d2)
+    assert 0 < np.count_nonzero(c1 >= 0) < ns or r >= 1.0
+
+
+def test_grid_nn_on_a_lattice_at_the_radius(ora):
+    """Targets on a lattice of spacing exactly r: every lattice neighbour sits at d2 == r^2 (inclusive) and the
+    queries sit on the lattice, on cell faces and in between, so a missing cell or a strict bound shows."""
+    r = 0.25
+    ax = np.arange(-4, 5, dtype=np.float32) * np.float32(r)
+    tgt = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), -1).reshape(-1, 3)
+    g = synth.rng(71)
+    tgt = tgt[g.permutation(len(tgt))]
+    q = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), -1).reshape(-1, 3) + np.float32(r / 2)
+    h = np.float32(1.01 * r)
+    faces = (np.arange(-3, 4, dtype=np.float32) * h)
+    qf = np.stack(np.meshgrid(faces, faces, faces, indexing="ij"), -1).reshape(-1, 3)
+    p = np.vstack([tgt + np.array([r, 0, 0], np.float32), q, qf]).astype(np.float32)
+    c1, d1 = ora.nn(p, tgt, r)
+    c2, d2 = ora.nn(p, tgt, r, method="grid")
+    assert np.array_equal(c1, c2) and np.array_equal(d1, d2)
+    # a query exactly r from its nearest target (the target shifted by r) matches at d2 == r^2 or closer
+    assert np.all(c1[: len(tgt)] >= 0)
+
+
+def test_grid_nn_partners_at_the_radius_anywhere_in_a_cell(ora):
+    """Isolated queries at random offsets, each with one partner about r away along a random axis: the partner
+    falls in the neighbouring cell or further whenever the cell is narrower than r, so a cell below r shows."""
+    r = 0.05
+    g = synth.rng(73)
+    n = 20000
+    base = np.stack(np.meshgrid(*(np.arange(28),) * 3, indexing="ij"), -1).reshape(-1, 3)[:n] * (10 * r)
+    p = (base + g.uniform(0, 3 * r, (n, 3))).astype(np.float32)
+    e = np.zeros((n, 3), np.float32)
+    e[np.arange(n), g.integers(0, 3, n)] = g.choice([-1.0, 1.0], n) * np.float32(r)
+    tgt = (p + e).astype(np.float32)
+    c1, d1 = ora.nn(p, tgt, r)
+    c2, d2 = ora.nn(p, tgt, r, method="grid")
+    assert np.array_equal(c1, c2) and np.array_equal(d1, d2)
+    assert np.count_nonzero(c1 >= 0) > n // 4
+
+
+def test_grid_nn_nonfinite_and_far(ora):
+    tgt = np.array([[0, 0, 0], [np.nan, 0, 0], [np.inf, 0, 0], [1e30, 1e30, 1e30], [0.01, 0, 0]], np.float32)
+    p = np.array([[0.004, 0, 0], [np.nan, 0, 0], [np.inf, 0, 0], [1e30, 1e30, 1e30], [-1e30, 0, 0]], np.float32)
+    c1, d1 = ora.nn(p, tgt, 0.05)
+    c2, d2 = ora.nn(p, tgt, 0.05, method="grid")
+    assert np.array_equal(c1, c2) and np.array_equal(d1, d2)
+    assert c1.tolist() == [0, -1, -1, 3, -1]
+
+
+def test_grid_nn_large_offsets(ora):
+    """Clouds far from the origin (coarse FP32 spacing) give the same map."""
+    g = synth.rng(72)
+    tgt = (g.uniform(-1, 1, (3000, 3)) + 1000.0).astype(np.float32)
+    p = (tgt[g.integers(0, 3000, 2000)] + g.normal(0, 0.01, (2000, 3))).astype(np.float32)
+    c1, d1 = ora.nn(p, tgt, 0.02)
+    c2, d2 = ora.nn(p, tgt, 0.02, method="grid")
+    assert np.array_equal(c1, c2) and np.array_equal(d1, d2)
+
+
+def test_icp_with_grid_search_equals_scan(ora):
+    """Same correspondences every iteration, so the whole registration is bit-identical."""
+    pr = synth.sphere_plane_pair()
+    a = ora.icp_point_to_plane(pr.src, pr.tgt, pr.tgt_nrm, np.eye(4), pr.max_corr_dist, pr.max_iter)
+    b = ora.icp_point_to_plane(pr.src, pr.tgt, pr.tgt_nrm, np.eye(4), pr.max_corr_dist, pr.max_iter, nn_method="grid")
+    assert a["status"] == b["status"] and a["iters"] == b["iters"]
+    assert np.array_equal(a["T"], b["T"]) and a["fitness"] == b["fitness"] and a["rmse"] == b["rmse"]
+
+
 # --------------------------------------------------- a5: residual, Jacobian
 
 
