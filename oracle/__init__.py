@@ -82,6 +82,15 @@ def _load():
     lib.ora_grid_free.restype = None
     lib.ora_grid_nn.argtypes = [ctypes.c_void_p, _f32p, _i64, _i32, _i32p, _f32p]
     lib.ora_grid_nn.restype = ctypes.c_int
+    lib.ora_jacobi_eig4.argtypes = [_f64p, _f64p, _f64p]
+    lib.ora_jacobi_eig4.restype = None
+    lib.ora_rigid_align.argtypes = [_f32p, _i64, _f32p, _i32p, _f64p, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_int64)]
+    lib.ora_rigid_align.restype = ctypes.c_int
+    lib.ora_icp_point_to_point.argtypes = [_f32p, _i64, _f32p, _i64, _f64p, ctypes.c_double, _i32, ctypes.c_double,
+                                           _i32, _i32, _f64p, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]
+    lib.ora_icp_point_to_point.restype = ctypes.c_int
     lib.ora_knn_hybrid.argtypes = [_f32p, _i64, _f32p, _i64, ctypes.c_float, _i32, _i32, _i32p, _f32p, _i32p]
     lib.ora_knn_hybrid.restype = ctypes.c_int
     lib.ora_jacobi_eig3.argtypes = [_f64p, _f64p, _f64p]
@@ -265,3 +274,46 @@ def estimate_normals(pts, radius: float, max_nn: int, viewpoint=(0.0, 0.0, 0.0),
     if st != OK:
         raise ValueError(f"ora_estimate_normals status {st}")
     return (out, ev) if return_evals else out
+
+
+def jacobi_eig4(C):
+    """Cyclic Jacobi eigen-decomposition of a symmetric 4x4 (FP64): (evals, V) with V[:, k] <-> evals[k]."""
+    ev = np.zeros(4, np.float64)
+    V = np.zeros(16, np.float64)
+    _load().ora_jacobi_eig4(np.ascontiguousarray(C, np.float64).ravel(), ev, V)
+    return ev, V.reshape(4, 4)
+
+
+def rigid_align(p, tgt, corr):
+    """TransformationEstimationPointToPoint's step (Sec. 3.3): Horn's closed-form rigid motion taking the
+    matched p_i onto q_corr(i).  Returns (dT 4x4, degenerate flag, rotation angle, |C|)."""
+    p, tgt = _pts(p), _pts(tgt)
+    corr = np.ascontiguousarray(corr, np.int32)
+    dT = np.zeros(16, np.float64)
+    ang, cnt = ctypes.c_double(), ctypes.c_int64()
+    deg = _load().ora_rigid_align(p if len(p) else np.zeros((1, 3), np.float32), len(p),
+                                  tgt if len(tgt) else np.zeros((1, 3), np.float32),
+                                  corr if len(corr) else np.zeros(1, np.int32), dT, ctypes.byref(ang),
+                                  ctypes.byref(cnt))
+    return dT.reshape(4, 4), bool(deg), ang.value, cnt.value
+
+
+def icp_point_to_point(src, tgt, init_T, max_corr_dist: float, max_iter: int, eps: float = 0.0,
+                       threads: int | None = None, nn_method: str = "brute") -> dict:
+    """registration_icp(..., TransformationEstimationPointToPoint()) (Sec. 3.3).
+
+    Returns dict(status, T (4x4 FP64), fitness, rmse, iters).
+    """
+    if nn_method not in ("brute", "grid"):
+        raise ValueError(f"unknown NN method {nn_method!r}")
+    src, tgt = _pts(src), _pts(tgt)
+    T = np.zeros(16, np.float64)
+    fit, rmse, iters = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    one = np.zeros((1, 3), np.float32)
+    st = _load().ora_icp_point_to_point(src if len(src) else one, len(src), tgt if len(tgt) else one, len(tgt),
+                                        _pose(init_T).ravel(), float(max_corr_dist), int(max_iter), float(eps),
+                                        threads or default_threads(), int(nn_method == "grid"), T,
+                                        ctypes.byref(fit), ctypes.byref(rmse), ctypes.byref(iters))
+    if st < 0:
+        raise ValueError(f"ora_icp_point_to_point status {st}")
+    return dict(status=st, T=T.reshape(4, 4), fitness=fit.value, rmse=rmse.value, iters=iters.value)

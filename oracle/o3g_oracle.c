@@ -702,3 +702,219 @@ int ora_estimate_normals(const float* pts, int64_t n, float radius, int32_t max_
   free(cnt);
   return st;
 }
+
+/* ------------------------------------------ point-to-point ICP (Sec. 3.3) */
+
+static void mat4_mul(const double a[16], const double b[16], double out[16]) {
+  double tmp[16];
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) {
+      double s = 0.0;
+      for (int k = 0; k < 4; ++k) s += a[4 * r + k] * b[4 * k + c];
+      tmp[4 * r + c] = s;
+    }
+  memcpy(out, tmp, sizeof(tmp));
+}
+
+/* Cyclic Jacobi eigen-decomposition of a symmetric 4x4 in FP64, the scheme of
+ * ora_jacobi_eig3: each plane rotation G zeroes (G^T A G)_pq; sweeps repeat
+ * until the off-diagonal norm is below 1e-15 of the Frobenius norm.
+ * evals[k] pairs with column k of V (row-major). */
+void ora_jacobi_eig4(const double C[16], double evals[4], double V[16]) {
+  double a[16];
+  memcpy(a, C, sizeof(a));
+  for (int k = 0; k < 16; ++k) V[k] = (k % 5 == 0) ? 1.0 : 0.0;
+  double fro2 = 0.0;
+  for (int k = 0; k < 16; ++k) fro2 += a[k] * a[k];
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    double off2 = 0.0;
+    for (int r = 0; r < 4; ++r)
+      for (int c = 0; c < 4; ++c)
+        if (r != c) off2 += a[4 * r + c] * a[4 * r + c];
+    if (off2 <= 1e-30 * fro2) break;
+    for (int p = 0; p < 3; ++p)
+      for (int q = p + 1; q < 4; ++q) {
+        double apq = a[4 * p + q];
+        if (apq == 0.0) continue;
+        double theta = (a[4 * q + q] - a[4 * p + p]) / (2.0 * apq);
+        double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        double c = 1.0 / sqrt(t * t + 1.0);
+        double s = t * c;
+        double G[16], Gt[16], tmp[16];
+        for (int k = 0; k < 16; ++k) G[k] = (k % 5 == 0) ? 1.0 : 0.0;
+        G[4 * p + p] = c;
+        G[4 * q + q] = c;
+        G[4 * p + q] = s;
+        G[4 * q + p] = -s;
+        for (int r = 0; r < 4; ++r)
+          for (int cc = 0; cc < 4; ++cc) Gt[4 * r + cc] = G[4 * cc + r];
+        mat4_mul(Gt, a, tmp);
+        mat4_mul(tmp, G, a);
+        a[4 * p + q] = 0.0; /* zero by construction of G */
+        a[4 * q + p] = 0.0;
+        mat4_mul(V, G, tmp);
+        memcpy(V, tmp, sizeof(tmp));
+      }
+  }
+  for (int k = 0; k < 4; ++k) evals[k] = a[5 * k];
+}
+
+/* The rigid motion (R, t) minimising sum_i |R p_i + t - q_c(i)|^2 over the
+ * correspondences (corr[i] >= 0), by Horn's closed form with unit quaternions
+ * (J. Opt. Soc. Am. A 4(4), 1987), all in FP64 from the FP32 inputs:
+ *   mu_p, mu_q  centroids of the matched source and target points (increasing i);
+ *   S_ab        sum_i (p_i - mu_p)_a (q_i - mu_q)_b;
+ *   N           the symmetric 4x4 of Horn's paper built from S (trace 0);
+ *   (w, x, y, z) the unit eigenvector of N's largest eigenvalue, w >= 0;
+ *   R           the rotation of that quaternion;  t = mu_q - R mu_p.
+ * When the largest eigenvalue is not separated from the next one by more than
+ * 1e-10 E0, E0 = (sum |p - mu_p|^2 + sum |q - mu_q|^2) / 2 (a bound on every
+ * eigenvalue's magnitude), the rotation is not determined (for instance all
+ * points on one line); then R = I, t = mu_q - mu_p and the return value is 1.
+ * dT = [R t; 0 1].  *angle = 2 atan2(|(x, y, z)|, w), the rotation angle of R.
+ * *count = |C|.  Fewer than one correspondence: dT = I, return 0. */
+int ora_rigid_align(const float* p, int64_t ns, const float* tgt, const int32_t* corr, double dT[16],
+                    double* angle, int64_t* count) {
+  double mp[3] = {0, 0, 0}, mq[3] = {0, 0, 0};
+  int64_t n = 0;
+  for (int64_t i = 0; i < ns; ++i) {
+    if (corr[i] < 0) continue;
+    const float* q = tgt + 3 * (int64_t)corr[i];
+    for (int a = 0; a < 3; ++a) {
+      mp[a] += (double)p[3 * i + a];
+      mq[a] += (double)q[a];
+    }
+    ++n;
+  }
+  *count = n;
+  for (int k = 0; k < 16; ++k) dT[k] = (k % 5 == 0) ? 1.0 : 0.0;
+  *angle = 0.0;
+  if (n < 1) return 0;
+  for (int a = 0; a < 3; ++a) {
+    mp[a] /= (double)n;
+    mq[a] /= (double)n;
+  }
+  double S[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gp = 0.0, gq = 0.0;
+  for (int64_t i = 0; i < ns; ++i) {
+    if (corr[i] < 0) continue;
+    const float* q = tgt + 3 * (int64_t)corr[i];
+    double dp[3], dq[3];
+    for (int a = 0; a < 3; ++a) {
+      dp[a] = (double)p[3 * i + a] - mp[a];
+      dq[a] = (double)q[a] - mq[a];
+    }
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) S[3 * a + b] += dp[a] * dq[b];
+    gp += dp[0] * dp[0] + dp[1] * dp[1] + dp[2] * dp[2];
+    gq += dq[0] * dq[0] + dq[1] * dq[1] + dq[2] * dq[2];
+  }
+  const double Sxx = S[0], Sxy = S[1], Sxz = S[2], Syx = S[3], Syy = S[4], Syz = S[5], Szx = S[6], Szy = S[7],
+               Szz = S[8];
+  const double N[16] = {Sxx + Syy + Szz, Syz - Szy,        Szx - Sxz,        Sxy - Syx,
+                        Syz - Szy,       Sxx - Syy - Szz,  Sxy + Syx,        Szx + Sxz,
+                        Szx - Sxz,       Sxy + Syx,        -Sxx + Syy - Szz, Syz + Szy,
+                        Sxy - Syx,       Szx + Sxz,        Syz + Szy,        -Sxx - Syy + Szz};
+  double ev[4], V[16];
+  ora_jacobi_eig4(N, ev, V);
+  int k1 = 0;
+  for (int k = 1; k < 4; ++k)
+    if (ev[k] > ev[k1]) k1 = k;
+  double second = -INFINITY;
+  for (int k = 0; k < 4; ++k)
+    if (k != k1 && ev[k] > second) second = ev[k];
+  const double E0 = 0.5 * (gp + gq);
+  int degenerate = !(ev[k1] - second > 1e-10 * E0);
+  double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  if (!degenerate) {
+    double w = V[k1], x = V[4 + k1], y = V[8 + k1], z = V[12 + k1];
+    double len = sqrt(w * w + x * x + y * y + z * z);
+    if (w < 0.0) len = -len;
+    w /= len;
+    x /= len;
+    y /= len;
+    z /= len;
+    R[0] = w * w + x * x - y * y - z * z;
+    R[1] = 2.0 * (x * y - w * z);
+    R[2] = 2.0 * (x * z + w * y);
+    R[3] = 2.0 * (x * y + w * z);
+    R[4] = w * w - x * x + y * y - z * z;
+    R[5] = 2.0 * (y * z - w * x);
+    R[6] = 2.0 * (x * z - w * y);
+    R[7] = 2.0 * (y * z + w * x);
+    R[8] = w * w - x * x - y * y + z * z;
+    *angle = 2.0 * atan2(sqrt(x * x + y * y + z * z), w);
+  }
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) dT[4 * r + c] = R[3 * r + c];
+    dT[4 * r + 3] = mq[r] - (R[3 * r] * mp[0] + R[3 * r + 1] * mp[1] + R[3 * r + 2] * mp[2]);
+  }
+  return degenerate;
+}
+
+/* Point-to-point ICP (registration_icp with TransformationEstimationPointToPoint,
+ * Sec. 3.3): per iteration the FP32 transform and correspondence step of the
+ * point-to-plane loop, then dT = ora_rigid_align and T <- dT T.  Stops with
+ * ORA_WARN_FEW_CORR when fewer than 3 correspondences remain, after max_iter
+ * updates, or when max(angle(dT), |t(dT)|) < eps.  ORA_WARN_DEGENERATE when some
+ * update had an undetermined rotation.  use_grid selects the exact grid search. */
+int ora_icp_point_to_point(const float* src, int64_t ns, const float* tgt, int64_t nt, const double init_T[16],
+                           double max_corr_dist, int32_t max_iter, double eps, int32_t nthreads, int32_t use_grid,
+                           double out_T[16], double* out_fitness, double* out_rmse, int32_t* out_iters) {
+  if (ns < 0 || nt < 0 || nt > INT32_MAX || max_iter < 0 || !(max_corr_dist >= 0.0)) return ORA_ERR_ARG;
+  float r_max = (float)max_corr_dist;
+  if (use_grid && !(r_max > 0.0f && isfinite(r_max))) return ORA_ERR_ARG;
+  int64_t nalloc = ns > 0 ? ns : 1;
+  float* p = (float*)malloc(sizeof(float) * 3 * nalloc);
+  int32_t* corr = (int32_t*)malloc(sizeof(int32_t) * nalloc);
+  float* d2 = (float*)malloc(sizeof(float) * nalloc);
+  ora_grid* g = use_grid ? ora_grid_build(tgt, nt, r_max) : NULL;
+  if (!p || !corr || !d2 || (use_grid && !g)) {
+    free(p);
+    free(corr);
+    free(d2);
+    ora_grid_free(g);
+    return ORA_ERR_OOM;
+  }
+  double T[16];
+  memcpy(T, init_T, sizeof(T));
+  int status = ORA_OK, degenerate = 0, iters = 0;
+  int64_t count = 0;
+  for (int k = 0; k < max_iter; ++k) {
+    ora_transform(src, ns, T, p);
+    if (g) ora_grid_nn(g, p, ns, nthreads, corr, d2);
+    else ora_nn(p, ns, tgt, nt, r_max, nthreads, corr, d2);
+    count = 0;
+    for (int64_t i = 0; i < ns; ++i) count += corr[i] >= 0;
+    if (count < 3) {
+      status = ORA_WARN_FEW_CORR;
+      break;
+    }
+    double dT[16], angle;
+    if (ora_rigid_align(p, ns, tgt, corr, dT, &angle, &count)) degenerate = 1;
+    mat4_mul(dT, T, T);
+    ++iters;
+    double tn = sqrt(dT[3] * dT[3] + dT[7] * dT[7] + dT[11] * dT[11]);
+    if ((angle > tn ? angle : tn) < eps) break;
+  }
+  /* evaluation at the final pose */
+  ora_transform(src, ns, T, p);
+  if (g) ora_grid_nn(g, p, ns, nthreads, corr, d2);
+  else ora_nn(p, ns, tgt, nt, r_max, nthreads, corr, d2);
+  double sum_d2 = 0.0;
+  count = 0;
+  for (int64_t i = 0; i < ns; ++i)
+    if (corr[i] >= 0) {
+      sum_d2 += (double)d2[i];
+      ++count;
+    }
+  memcpy(out_T, T, sizeof(T));
+  *out_fitness = ns > 0 ? (double)count / (double)ns : 0.0;
+  *out_rmse = count > 0 ? sqrt(sum_d2 / (double)count) : 0.0;
+  *out_iters = iters;
+  free(p);
+  free(corr);
+  free(d2);
+  ora_grid_free(g);
+  if (status == ORA_OK && degenerate) status = ORA_WARN_DEGENERATE;
+  return status;
+}

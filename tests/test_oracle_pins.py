@@ -505,3 +505,108 @@ def test_normals_match_eigh_of_neighbour_covariance(ora):
         if w[1] - w[0] > 1e-3 * w[2]:
             cosang = abs(float(np.dot(nrm[i].astype(np.float64), V[:, 0])))
             assert cosang > 1 - 2e-7  # FP32 storage of a unit vector
+
+
+# ------------------------------------------ point-to-point ICP (Horn's closed form)
+
+
+def _kabsch_svd(p, q):
+    """Independent statement of the least-squares rigid motion: SVD of the centred cross-covariance
+    (Kabsch / Umeyama without scale, with the determinant correction that keeps R a rotation)."""
+    p = p.astype(np.float64)
+    q = q.astype(np.float64)
+    mp, mq = p.mean(0), q.mean(0)
+    H = (p - mp).T @ (q - mq)
+    U, _, Vt = np.linalg.svd(H)
+    d = np.sign(np.linalg.det(Vt.T @ U.T))
+    R = Vt.T @ np.diag([1.0, 1.0, d]) @ U.T
+    return synth.make_T(R, mq - R @ mp)
+
+
+def test_jacobi4_matches_numpy_eigh(ora):
+    g = synth.rng(80)
+    for _ in range(20):
+        M = g.normal(size=(4, 4))
+        C = M + M.T
+        ev, V = ora.jacobi_eig4(C)
+        ref = np.linalg.eigvalsh(C)
+        assert np.allclose(np.sort(ev), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+        assert np.allclose(C @ V, V * ev, atol=1e-11 * np.abs(ref).max())
+        assert np.allclose(V.T @ V, np.eye(4), atol=1e-13)
+
+
+@pytest.mark.parametrize("noise,deg,trans", [(0.0, 30.0, 0.5), (0.01, 10.0, 0.1), (0.05, 170.0, 2.0)])
+def test_rigid_align_matches_svd_kabsch(ora, noise, deg, trans):
+    g = synth.rng(81 + int(deg))
+    p = g.normal(0, 1, (500, 3)).astype(np.float32)
+    T = synth.perturbation(g, deg, trans)
+    q = (synth.apply_T(T, p) + g.normal(0, noise, p.shape)).astype(np.float32)
+    # a partial correspondence map: some points unmatched, targets in shuffled order
+    perm = g.permutation(500)
+    tgt = q[perm]
+    corr = np.argsort(perm).astype(np.int32)
+    corr[g.random(500) < 0.2] = -1
+    dT, deg_flag, ang, cnt = ora.rigid_align(p, tgt, corr)
+    m = corr >= 0
+    ref = _kabsch_svd(p[m], tgt[corr[m]])
+    assert not deg_flag and cnt == m.sum()
+    assert np.allclose(dT, ref, atol=1e-10)
+    R = dT[:3, :3]
+    assert np.allclose(R @ R.T, np.eye(3), atol=1e-13) and np.linalg.det(R) == pytest.approx(1.0, abs=1e-13)
+    assert ang == pytest.approx(np.arccos(np.clip((np.trace(R) - 1) / 2, -1, 1)), abs=1e-7)
+    if noise == 0.0:
+        a, t = synth.pose_error(dT, T)
+        assert a < 1e-6 and t < 1e-6
+
+
+def test_rigid_align_best_rotation_for_a_mirrored_cloud(ora):
+    """A reflected target: the answer is the best proper rotation, as the determinant-corrected SVD gives."""
+    g = synth.rng(84)
+    p = (g.normal(0, 1, (300, 3)) * [3.0, 2.0, 1.0]).astype(np.float32)
+    q = (p * np.float32([1, 1, -1])).astype(np.float32)
+    dT, deg_flag, _, _ = ora.rigid_align(p, q, np.arange(300, dtype=np.int32))
+    assert not deg_flag
+    assert np.allclose(dT, _kabsch_svd(p, q), atol=1e-10)
+
+
+def test_rigid_align_collinear_is_degenerate(ora):
+    t = np.linspace(-1, 1, 50)
+    p = np.stack([t, 2 * t, -t], 1).astype(np.float32)
+    q = (p + np.float32([0.1, 0.2, 0.3])).astype(np.float32)
+    dT, deg_flag, ang, _ = ora.rigid_align(p, q, np.arange(50, dtype=np.int32))
+    assert deg_flag and ang == 0.0
+    assert np.array_equal(dT[:3, :3], np.eye(3))
+    assert np.allclose(dT[:3, 3], q.astype(np.float64).mean(0) - p.astype(np.float64).mean(0), atol=1e-15)
+
+
+def test_icp_point_to_point_recovers_noise_free(ora):
+    pr = synth.sphere_plane_pair(noise=0.0, deg=3.0, trans=0.02)
+    res = ora.icp_point_to_point(pr.src, pr.tgt, np.eye(4), 0.05, 200, eps=1e-9)
+    a, t = synth.pose_error(res["T"], pr.T_gt)
+    assert a < 1e-5 and t < 1e-5, (a, t, res)
+    assert res["fitness"] == 1.0 and res["rmse"] < 1e-5
+
+
+def test_icp_point_to_point_equivariance(ora):
+    """Moving both clouds by G conjugates the result (within FP32 input rounding)."""
+    pr = synth.sphere_plane_pair(n=2000, noise=0.002, deg=3.0, trans=0.02)
+    a = ora.icp_point_to_point(pr.src, pr.tgt, np.eye(4), 0.05, 30)
+    G = synth.make_T(synth.axis_angle_matrix([0.3, -1.0, 0.5], 0.7), [0.5, -0.2, 0.1])
+    b = ora.icp_point_to_point(synth.apply_T(G, pr.src).astype(np.float32),
+                               synth.apply_T(G, pr.tgt).astype(np.float32), np.eye(4), 0.05, 30)
+    ang, dt = synth.pose_error(b["T"], G @ a["T"] @ np.linalg.inv(G))
+    assert ang < 1e-4 and dt < 1e-4
+    assert abs(a["fitness"] - b["fitness"]) < 0.01
+
+
+def test_icp_point_to_point_grid_equals_scan_and_statuses(ora):
+    pr = synth.sphere_plane_pair(n=3000)
+    a = ora.icp_point_to_point(pr.src, pr.tgt, np.eye(4), 0.05, 20)
+    b = ora.icp_point_to_point(pr.src, pr.tgt, np.eye(4), 0.05, 20, nn_method="grid")
+    assert a["status"] == b["status"] == ora.OK and a["iters"] == b["iters"] == 20
+    assert np.array_equal(a["T"], b["T"]) and a["rmse"] == b["rmse"]
+    far = ora.icp_point_to_point(pr.src + np.float32(10), pr.tgt, np.eye(4), 0.05, 5)
+    assert far["status"] == ora.WARN_FEW_CORR and far["iters"] == 0 and far["fitness"] == 0.0
+    # eps stops the loop once the update is small
+    c = ora.icp_point_to_point(pr.src, pr.tgt, np.eye(4), 0.05, 500, eps=1e-7)
+    assert c["iters"] < 500
