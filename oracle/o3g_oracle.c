@@ -768,9 +768,11 @@ void ora_jacobi_eig4(const double C[16], double evals[4], double V[16]) {
  *   (w, x, y, z) the unit eigenvector of N's largest eigenvalue, w >= 0;
  *   R           the rotation of that quaternion;  t = mu_q - R mu_p.
  * When the largest eigenvalue is not separated from the next one by more than
- * 1e-10 E0, E0 = (sum |p - mu_p|^2 + sum |q - mu_q|^2) / 2 (a bound on every
+ * 1e-6 E0, E0 = (sum |p - mu_p|^2 + sum |q - mu_q|^2) / 2 (a bound on every
  * eigenvalue's magnitude), the rotation is not determined (for instance all
- * points on one line); then R = I, t = mu_q - mu_p and the return value is 1.
+ * points on one line; float32 coordinates, good to 6e-8 relative, cannot fix a
+ * rotation whose eigenvalue gap is smaller); then R = I, t = mu_q - mu_p and
+ * the return value is 1.
  * dT = [R t; 0 1].  *angle = 2 atan2(|(x, y, z)|, w), the rotation angle of R.
  * *count = |C|.  Fewer than one correspondence: dT = I, return 0. */
 int ora_rigid_align(const float* p, int64_t ns, const float* tgt, const int32_t* corr, double dT[16],
@@ -823,7 +825,7 @@ int ora_rigid_align(const float* p, int64_t ns, const float* tgt, const int32_t*
   for (int k = 0; k < 4; ++k)
     if (k != k1 && ev[k] > second) second = ev[k];
   const double E0 = 0.5 * (gp + gq);
-  int degenerate = !(ev[k1] - second > 1e-10 * E0);
+  int degenerate = !(ev[k1] - second > 1e-6 * E0);
   double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   if (!degenerate) {
     double w = V[k1], x = V[4 + k1], y = V[8 + k1], z = V[12 + k1];
