@@ -91,6 +91,8 @@ def _load():
                                            _i32, _i32, _f64p, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]
     lib.ora_icp_point_to_point.restype = ctypes.c_int
+    lib.ora_voxel_downsample.argtypes = [_f32p, _i64, ctypes.c_float, _f32p, _i32p, ctypes.POINTER(ctypes.c_int64)]
+    lib.ora_voxel_downsample.restype = ctypes.c_int
     lib.ora_knn_hybrid.argtypes = [_f32p, _i64, _f32p, _i64, ctypes.c_float, _i32, _i32, _i32p, _f32p, _i32p]
     lib.ora_knn_hybrid.restype = ctypes.c_int
     lib.ora_jacobi_eig3.argtypes = [_f64p, _f64p, _f64p]
@@ -317,3 +319,18 @@ def icp_point_to_point(src, tgt, init_T, max_corr_dist: float, max_iter: int, ep
     if st < 0:
         raise ValueError(f"ora_icp_point_to_point status {st}")
     return dict(status=st, T=T.reshape(4, 4), fitness=fit.value, rmse=rmse.value, iters=iters.value)
+
+
+def voxel_down_sample(pts, voxel: float):
+    """voxel_down_sample (Sec. 3.1, Fig. 1): per occupied voxel floor(p / v) (FP32 quotient) the FP64
+    centroid of its points in input order, rounded to FP32; voxels in increasing (ix, iy, iz).
+    Returns (centroids float32 [M, 3], counts int32 [M])."""
+    pts = _pts(pts)
+    out = np.empty((max(len(pts), 1), 3), np.float32)
+    cnt = np.empty(max(len(pts), 1), np.int32)
+    m = ctypes.c_int64()
+    st = _load().ora_voxel_downsample(pts if len(pts) else np.zeros((1, 3), np.float32), len(pts),
+                                      ctypes.c_float(np.float32(voxel)), out, cnt, ctypes.byref(m))
+    if st != OK:
+        raise ValueError(f"ora_voxel_downsample status {st}")
+    return out[: m.value].copy(), cnt[: m.value].copy()

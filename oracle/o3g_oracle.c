@@ -920,3 +920,68 @@ int ora_icp_point_to_point(const float* src, int64_t ns, const float* tgt, int64
   if (status == ORA_OK && degenerate) status = ORA_WARN_DEGENERATE;
   return status;
 }
+
+/* ------------------------------------------------ voxel downsampling (Sec. 3.1) */
+
+typedef struct {
+  int64_t k[3];
+  int64_t i;
+} vkey;
+
+static int vkey_cmp(const void* a, const void* b) {
+  const vkey* x = (const vkey*)a;
+  const vkey* y = (const vkey*)b;
+  for (int d = 0; d < 3; ++d) {
+    if (x->k[d] < y->k[d]) return -1;
+    if (x->k[d] > y->k[d]) return 1;
+  }
+  return (x->i > y->i) - (x->i < y->i);
+}
+
+/* voxel_down_sample: one output point per occupied voxel, the centroid of the
+ * input points in it.
+ *   voxel index   (floor(x / v), floor(y / v), floor(z / v)), each quotient a
+ *                 single FP32 division; points with a non-finite coordinate are
+ *                 dropped; an index outside [-2^30, 2^30] is an error (ORA_ERR_ARG)
+ *   order         voxels in increasing (ix, iy, iz), x most significant
+ *   centroid      FP64 sum of the voxel's points in increasing input index,
+ *                 divided by their count, rounded to FP32
+ * out (capacity 3 n floats) receives the centroids, counts (capacity n, may be
+ * NULL) the number of points per voxel; *n_out the number of voxels. */
+int ora_voxel_downsample(const float* pts, int64_t n, float voxel, float* out, int32_t* counts, int64_t* n_out) {
+  *n_out = 0;
+  if (n < 0 || !(voxel > 0.0f) || !isfinite(voxel)) return ORA_ERR_ARG;
+  vkey* keys = (vkey*)malloc(sizeof(vkey) * (size_t)(n > 0 ? n : 1));
+  if (!keys) return ORA_ERR_OOM;
+  int64_t m = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const float* p = pts + 3 * i;
+    if (!finite3(p)) continue;
+    for (int d = 0; d < 3; ++d) {
+      float q = floorf(p[d] / voxel);
+      if (!(q >= -1073741824.0f && q <= 1073741824.0f)) {
+        free(keys);
+        return ORA_ERR_ARG;
+      }
+      keys[m].k[d] = (int64_t)q;
+    }
+    keys[m].i = i;
+    ++m;
+  }
+  qsort(keys, (size_t)m, sizeof(vkey), vkey_cmp);
+  int64_t nv = 0;
+  for (int64_t a = 0; a < m;) {
+    int64_t b = a + 1;
+    while (b < m && keys[b].k[0] == keys[a].k[0] && keys[b].k[1] == keys[a].k[1] && keys[b].k[2] == keys[a].k[2]) ++b;
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int64_t e = a; e < b; ++e)
+      for (int d = 0; d < 3; ++d) s[d] += (double)pts[3 * keys[e].i + d];
+    for (int d = 0; d < 3; ++d) out[3 * nv + d] = (float)(s[d] / (double)(b - a));
+    if (counts) counts[nv] = (int32_t)(b - a);
+    ++nv;
+    a = b;
+  }
+  *n_out = nv;
+  free(keys);
+  return ORA_OK;
+}

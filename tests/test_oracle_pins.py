@@ -610,3 +610,65 @@ def test_icp_point_to_point_grid_equals_scan_and_statuses(ora):
     # eps stops the loop once the update is small
     c = ora.icp_point_to_point(pr.src, pr.tgt, np.eye(4), 0.05, 500, eps=1e-7)
     assert c["iters"] < 500
+
+
+# ------------------------------------------------------------- voxel downsampling
+
+
+def _voxel_numpy(p, v):
+    """Independent statement: float32 quotients, stable lexicographic order, FP64 sums accumulated in input
+    order by bincount."""
+    ok = np.all(np.isfinite(p), axis=1)
+    p = p[ok]
+    k = np.floor(p / np.float32(v)).astype(np.int64)
+    uniq, inv = np.unique(k, axis=0, return_inverse=True)  # rows sorted lexicographically, x first
+    inv = inv.ravel()
+    cnt = np.bincount(inv, minlength=len(uniq))
+    c = np.stack([np.bincount(inv, weights=p[:, a].astype(np.float64), minlength=len(uniq)) for a in range(3)], 1)
+    return (c / cnt[:, None]).astype(np.float32), cnt.astype(np.int32)
+
+
+@pytest.mark.parametrize("n,v,span", [(20000, 0.1, 1.0), (5000, 0.013, 0.2), (3000, 5.0, 1.0), (1, 0.1, 1.0)])
+def test_voxel_downsample_matches_numpy_bitexact(ora, n, v, span):
+    g = synth.rng(90 + n)
+    p = g.uniform(-span, span, (n, 3)).astype(np.float32)
+    if n > 10:
+        p[: n // 10] = (np.round(p[: n // 10] / np.float32(v)) * np.float32(v)).astype(np.float32)  # on voxel faces
+        p[n // 10: n // 5] = p[: n // 10]  # duplicates
+    c, cnt = ora.voxel_down_sample(p, v)
+    c_ref, cnt_ref = _voxel_numpy(p, v)
+    assert np.array_equal(cnt, cnt_ref) and np.array_equal(c, c_ref)
+    assert cnt.sum() == n
+
+
+def test_voxel_downsample_properties(ora):
+    g = synth.rng(95)
+    p = g.normal(0, 1, (5000, 3)).astype(np.float32)
+    v = 0.25
+    c, cnt = ora.voxel_down_sample(p, v)
+    keys = np.floor(c / np.float32(v)).astype(np.int64)
+    # the centroid of a voxel's points lies in that voxel, and voxels come in increasing key order
+    in_keys = np.unique(np.floor(p / np.float32(v)).astype(np.int64), axis=0)
+    assert np.array_equal(keys, in_keys)
+    order = np.lexsort(keys.T[::-1])
+    assert np.array_equal(order, np.arange(len(c)))  # increasing (ix, iy, iz)
+    # one point per voxel: the output is the input point itself
+    q = (np.arange(50, dtype=np.float32)[:, None] * np.float32(v) + np.float32(v / 2)) * np.ones((1, 3), np.float32)
+    cq, nq = ora.voxel_down_sample(q, v)
+    assert np.array_equal(cq, q) and np.all(nq == 1)
+    # input order changes at most the last bits of a centroid
+    perm = g.permutation(len(p))
+    c2, cnt2 = ora.voxel_down_sample(p[perm], v)
+    assert np.array_equal(cnt, cnt2) and np.allclose(c, c2, rtol=0, atol=1e-6)
+
+
+def test_voxel_downsample_edge_cases(ora):
+    c, cnt = ora.voxel_down_sample(np.zeros((0, 3), np.float32), 0.1)
+    assert len(c) == 0 and len(cnt) == 0
+    p = np.array([[0, 0, 0], [np.nan, 0, 0], [0.01, 0.02, 0.03], [np.inf, 1, 1]], np.float32)
+    c, cnt = ora.voxel_down_sample(p, 0.1)
+    assert cnt.tolist() == [2] and np.array_equal(c[0], np.float32([0.005, 0.01, 0.015]))
+    with pytest.raises(ValueError):
+        ora.voxel_down_sample(np.array([[1e9, 0, 0]], np.float32), 0.1)
+    with pytest.raises(ValueError):
+        ora.voxel_down_sample(p, 0.0)
