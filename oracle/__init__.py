@@ -93,6 +93,9 @@ def _load():
     lib.ora_icp_point_to_point.restype = ctypes.c_int
     lib.ora_voxel_downsample.argtypes = [_f32p, _i64, ctypes.c_float, _f32p, _i32p, ctypes.POINTER(ctypes.c_int64)]
     lib.ora_voxel_downsample.restype = ctypes.c_int
+    lib.ora_evaluate_poses.argtypes = [_f32p, _i64, _f32p, _i64, _f64p, _i32, ctypes.c_double, _i32, _i32, _f64p,
+                                       _f64p, np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")]
+    lib.ora_evaluate_poses.restype = ctypes.c_int
     lib.ora_knn_hybrid.argtypes = [_f32p, _i64, _f32p, _i64, ctypes.c_float, _i32, _i32, _i32p, _f32p, _i32p]
     lib.ora_knn_hybrid.restype = ctypes.c_int
     lib.ora_jacobi_eig3.argtypes = [_f64p, _f64p, _f64p]
@@ -334,3 +337,23 @@ def voxel_down_sample(pts, voxel: float):
     if st != OK:
         raise ValueError(f"ora_voxel_downsample status {st}")
     return out[: m.value].copy(), cnt[: m.value].copy()
+
+
+def evaluate_poses(src, tgt, poses, max_corr_dist: float, threads: int | None = None, nn_method: str = "brute"):
+    """RANSAC's hypothesis validation (Sec. 3.3): for each 4x4 pose, fitness, inlier rmse and inlier count of the
+    whole source against the target at that pose.  Returns (fitness [H], rmse [H], count [H])."""
+    if nn_method not in ("brute", "grid"):
+        raise ValueError(f"unknown NN method {nn_method!r}")
+    src, tgt = _pts(src), _pts(tgt)
+    P = np.ascontiguousarray(np.asarray(poses, np.float64).reshape(-1, 16))
+    H = len(P)
+    fit = np.zeros(max(H, 1))
+    rmse = np.zeros(max(H, 1))
+    cnt = np.zeros(max(H, 1), np.int64)
+    one = np.zeros((1, 3), np.float32)
+    st = _load().ora_evaluate_poses(src if len(src) else one, len(src), tgt if len(tgt) else one, len(tgt),
+                                    P if H else np.zeros((1, 16)), H, float(max_corr_dist),
+                                    threads or default_threads(), int(nn_method == "grid"), fit, rmse, cnt)
+    if st != OK:
+        raise ValueError(f"ora_evaluate_poses status {st}")
+    return fit[:H], rmse[:H], cnt[:H]

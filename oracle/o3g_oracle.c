@@ -985,3 +985,53 @@ int ora_voxel_downsample(const float* pts, int64_t n, float voxel, float* out, i
   free(keys);
   return ORA_OK;
 }
+
+/* ------------------------------ hypothesis validation (Sec. 3.3, RANSAC) */
+
+/* The validation RANSAC spends its time in (Sec. 3.3 global registration):
+ * for each candidate pose T_h (n_poses x 16, row-major FP64), the transform and
+ * correspondence step of ICP at T_h over the whole source, then
+ *   count_h   = |C_h|
+ *   fitness_h = |C_h| / ns
+ *   rmse_h    = sqrt(sum_{C_h} d2 / |C_h|)   (0 when C_h is empty)
+ * with the FP32 d2 of the matches summed in FP64 in increasing source index.
+ * use_grid selects the exact grid search (same correspondences). */
+int ora_evaluate_poses(const float* src, int64_t ns, const float* tgt, int64_t nt, const double* poses,
+                       int32_t n_poses, double max_corr_dist, int32_t nthreads, int32_t use_grid,
+                       double* out_fitness, double* out_rmse, int64_t* out_count) {
+  if (ns < 0 || nt < 0 || nt > INT32_MAX || n_poses < 0 || !(max_corr_dist >= 0.0)) return ORA_ERR_ARG;
+  float r_max = (float)max_corr_dist;
+  if (use_grid && !(r_max > 0.0f && isfinite(r_max))) return ORA_ERR_ARG;
+  int64_t nalloc = ns > 0 ? ns : 1;
+  float* p = (float*)malloc(sizeof(float) * 3 * nalloc);
+  int32_t* corr = (int32_t*)malloc(sizeof(int32_t) * nalloc);
+  float* d2 = (float*)malloc(sizeof(float) * nalloc);
+  ora_grid* g = use_grid ? ora_grid_build(tgt, nt, r_max) : NULL;
+  if (!p || !corr || !d2 || (use_grid && !g)) {
+    free(p);
+    free(corr);
+    free(d2);
+    ora_grid_free(g);
+    return ORA_ERR_OOM;
+  }
+  for (int32_t h = 0; h < n_poses; ++h) {
+    ora_transform(src, ns, poses + 16 * (int64_t)h, p);
+    if (g) ora_grid_nn(g, p, ns, nthreads, corr, d2);
+    else ora_nn(p, ns, tgt, nt, r_max, nthreads, corr, d2);
+    int64_t count = 0;
+    double sum_d2 = 0.0;
+    for (int64_t i = 0; i < ns; ++i)
+      if (corr[i] >= 0) {
+        sum_d2 += (double)d2[i];
+        ++count;
+      }
+    out_count[h] = count;
+    out_fitness[h] = ns > 0 ? (double)count / (double)ns : 0.0;
+    out_rmse[h] = count > 0 ? sqrt(sum_d2 / (double)count) : 0.0;
+  }
+  free(p);
+  free(corr);
+  free(d2);
+  ora_grid_free(g);
+  return ORA_OK;
+}

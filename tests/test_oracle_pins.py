@@ -672,3 +672,34 @@ def test_voxel_downsample_edge_cases(ora):
         ora.voxel_down_sample(np.array([[1e9, 0, 0]], np.float32), 0.1)
     with pytest.raises(ValueError):
         ora.voxel_down_sample(p, 0.0)
+
+
+# ----------------------------------------------- hypothesis validation (RANSAC)
+
+
+def test_evaluate_poses_matches_independent_bruteforce(ora):
+    """Counts from an independent numpy float32 brute force; rmse from the same matches summed in FP64."""
+    g = synth.rng(120)
+    tgt = g.uniform(-1, 1, (1500, 3)).astype(np.float32)
+    src = (tgt[g.integers(0, 1500, 800)] + g.normal(0, 0.01, (800, 3))).astype(np.float32)
+    poses = [np.eye(4)] + [synth.perturbation(g, d, t) for d, t in ((1.0, 0.01), (5.0, 0.05), (90.0, 1.0))]
+    fit, rmse, cnt = ora.evaluate_poses(src, tgt, poses, 0.05)
+    for h, T in enumerate(poses):
+        p = ora.transform(src, T)
+        c, d2 = ind.nn_bruteforce_f32(p, tgt, 0.05)
+        m = c >= 0
+        assert cnt[h] == m.sum() and fit[h] == m.sum() / len(src)
+        ref = np.sqrt(np.sum(d2[m].astype(np.float64)) / m.sum()) if m.any() else 0.0
+        assert rmse[h] == pytest.approx(ref, rel=1e-12)
+    assert cnt[0] > cnt[3]  # the true pose explains more points than a far-off one
+    f2, r2, c2 = ora.evaluate_poses(src, tgt, poses, 0.05, nn_method="grid")
+    assert np.array_equal(c2, cnt) and np.array_equal(r2, rmse) and np.array_equal(f2, fit)
+
+
+def test_evaluate_poses_equals_zero_iteration_icp(ora):
+    """Evaluation at a pose is the final-evaluation step of ICP with no update."""
+    pr = synth.sphere_plane_pair(n=2000)
+    T = synth.perturbation(synth.rng(121), 2.0, 0.02)
+    fit, rmse, _ = ora.evaluate_poses(pr.src, pr.tgt, [T], 0.05)
+    res = ora.icp_point_to_plane(pr.src, pr.tgt, pr.tgt_nrm, T, 0.05, 0)
+    assert fit[0] == res["fitness"] and rmse[0] == res["rmse"]
