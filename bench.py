@@ -337,7 +337,7 @@ def run_batched(args, ws, rank, local):
     sampler = ClockSampler(local) if rank == 0 else None
     l0 = o3g.launch_count()
     ms_b, res_b = timed(batched, args.steps)
-    launches = (o3g.launch_count() - l0) / args.steps
+    launches = o3g.launch_count() - l0
     clocks = sampler.stop() if sampler else None
     ms_s, res_s = timed(single_loop, max(1, args.steps // 4))
     # per-iteration kernel time from the instrumented graph launches
@@ -453,6 +453,175 @@ def run_serving(args, ws, rank, local):
         print(json.dumps(line))
 
 
+# ------------------------------------------------ scene-fragment precision study
+
+FRAGMENT_WORKLOAD = ("scene-fragment pair: two fused 50-frame fragments of a seeded room (20 boxes, 10 spheres, "
+                     "4 m), 640x480 PrimeSense ray-cast depth, noise 0.001 z^2, 0.005 m voxels, seeded "
+                     "2,000,000-point subsets, fused analytic normals; source moved 1 deg / 0.01 m; point-to-plane "
+                     "ICP max_corr_dist 0.02, 50 iterations")
+
+
+def run_fragment(args, ws, rank, local):
+    """2M vs 2M points: float32+compensated against all-float64 terms, both against the FP64 oracle."""
+    import torch
+
+    from paper_1801_09847_gb300 import build, o3g, synth
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pr = synth.fragment_pair(seed=4 + rank)
+    ns, nt, r, iters = len(pr.src), len(pr.tgt), pr.max_corr_dist, pr.max_iter
+    src = torch.from_numpy(pr.src).to(dev)
+    tgt = torch.from_numpy(pr.tgt).to(dev)
+    nrm = torch.from_numpy(pr.tgt_nrm).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    init = np.eye(4)
+
+    def step(prec):
+        g = o3g.build_grid(tgt, r * args.cell_factor)
+        g.set_normals(nrm)
+        res = o3g.icp_point_to_plane_grid(g, src, init, r, iters, precision=prec)
+        g.free()
+        return res
+
+    def timed(fn, steps, instrument=False):
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if instrument:
+            o3g.timing_enable(True)
+            for k in (o3g.KERNEL_ICP_CORR, o3g.KERNEL_GRID):
+                o3g.timing_read(k, reset=True)
+        l0 = o3g.launch_count()
+        total, out = 0.0, None
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        launches = o3g.launch_count() - l0
+        kern = None
+        if instrument:
+            o3g.timing_enable(False)
+            kern = {"icp": o3g.timing_read(o3g.KERNEL_ICP_CORR, reset=True),
+                    "grid": o3g.timing_read(o3g.KERNEL_GRID, reset=True)}
+        if dist:
+            total = max_over_ranks(total, dist, dev)
+        return total / steps, launches, kern, out
+
+    for prec in ("f32", "f64"):
+        for _ in range(args.warmup):
+            step(prec)
+    sampler = ClockSampler(local) if rank == 0 else None
+    ms32, launches, _, res32 = timed(lambda: step("f32"), args.steps)
+    clocks = sampler.stop() if sampler else None
+    ms64, _, _, res64 = timed(lambda: step("f64"), max(3, args.steps // 2))
+    _, _, k32, _ = timed(lambda: step("f32"), 3, instrument=True)
+    _, _, k64, _ = timed(lambda: step("f64"), 3, instrument=True)
+
+    # e2e through the host-buffer entry point (page-locked inputs, copies inside the timed region)
+    src_h = torch.from_numpy(pr.src).pin_memory()
+    tgt_h = torch.from_numpy(pr.tgt).pin_memory()
+    nrm_h = torch.from_numpy(pr.tgt_nrm).pin_memory()
+
+    def step_host():
+        return o3g.register_point_to_plane_host(src_h, tgt_h, nrm_h, init, r, iters)
+
+    step_host()
+    e2e_ms, _, _, _ = timed(step_host, max(3, args.steps // 2))
+
+    units = float(ns * res32["iters"])
+    if dist:
+        units = sum_over_ranks(units, dist, dev)
+    value = units / (ms32 / 1e3)
+    line = None
+    if rank == 0:
+        peak, which = peaks()
+
+        def roof(kern, res):
+            ms, n = kern["icp"]
+            avg_s = ms / max(n, 1) / 1e3
+            alg = ns * (12.0 + 24.0 * res["fitness"])
+            ach = alg / avg_s / 1e9
+            return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                    "traffic": profiled_traffic("icp.cu", "k_icp_iter_fragment_2m.md"),
+                    "kernel": "k_icp_iter", "peak_source": which, "launches_timed": n,
+                    "avg_launch_us": avg_s * 1e6, "algorithmic_bytes_per_launch": alg}
+
+        study = {"f32_compensated": {"ms_per_step": ms32, "value": ns * res32["iters"] / (ms32 / 1e3),
+                                     "roofline": roof(k32, res32)},
+                 "f64": {"ms_per_step": ms64, "value": ns * res64["iters"] / (ms64 / 1e3),
+                         "roofline": roof(k64, res64)}}
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            threads = oracle.default_threads()
+            t0 = time.perf_counter()
+            ref = oracle.icp_point_to_plane(pr.src, pr.tgt, pr.tgt_nrm, init, r, iters, threads=threads,
+                                            nn_method="grid")
+            t_ora = time.perf_counter() - t0
+            cpu = {"value": ns * ref["iters"] / t_ora, "unit": UNIT, "cores": threads, "kind": "oracle",
+                   "sample": (f"the whole pair: oracle ICP (exact grid search, FP64 sums) on {ns} source points, "
+                              f"{ref['iters']} iterations, {t_ora:.1f} s")}
+            for key, res in (("f32_compensated", res32), ("f64", res64)):
+                ang, dt = synth.pose_error(res["T"], ref["T"])
+                study[key]["pose_error_vs_oracle"] = {"rad": ang, "m": dt}
+                study[key]["iters"] = res["iters"]
+            study["oracle"] = {"iters": ref["iters"], "fitness": ref["fitness"], "rmse": ref["rmse"],
+                               "pose_error_vs_ground_truth": dict(zip(("rad", "m"),
+                                                                      synth.pose_error(ref["T"], pr.T_gt)))}
+            # J^T J and J^T r at the start pose and at the oracle's final pose
+            g = o3g.build_grid(tgt, r * args.cell_factor)
+            g.set_normals(nrm)
+            for label, T in (("start_pose", init), ("final_pose", ref["T"])):
+                p = oracle.transform(pr.src, T)
+                corr, d2 = oracle.nn(p, pr.tgt, r, threads=threads, method="grid")
+                A_ref, b_ref, _, _, _ = oracle.normal_equations(p, pr.tgt, pr.tgt_nrm, corr, d2)
+                m = corr >= 0
+                pp = p[m].astype(np.float64)
+                qn = pr.tgt_nrm[corr[m]].astype(np.float64)
+                J = np.hstack([np.cross(pp, qn), qn])
+                rr = np.sum((pp - pr.tgt[corr[m]].astype(np.float64)) * qn, axis=1)
+                scale_b = np.abs(J).T @ np.abs(rr)
+                for key, prec in (("f32_compensated", "f32"), ("f64", "f64")):
+                    A, b, _ = o3g.normal_equations(g, src, T, r, precision=prec)
+                    study[key][f"JtJ_rel_error_{label}"] = float(np.linalg.norm(A - A_ref) / np.linalg.norm(A_ref))
+                    study[key][f"Jtr_scaled_error_{label}"] = float(np.max(np.abs(b - b_ref)) / np.max(scale_b))
+            g.free()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": FRAGMENT_WORKLOAD, "n_source": ns, "n_target": nt, "iterations": res32["iters"],
+                       "max_corr_dist": r, "l2": "flushed (512 MiB write) before every step",
+                       "step": "grid build + normals upload + 50 ICP iterations + evaluation",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": (ns + 2 * nt) * 12,
+                    "d2h_bytes_per_step": 16 * 8 + 8 + 8 + 4, "ms_per_step": e2e_ms},
+            "gpu_launches": launches,
+            "roofline": study["f32_compensated"]["roofline"],
+            "precision_study": study,
+            "result": {"fitness": res32["fitness"], "rmse": res32["rmse"], "status": res32["status"]},
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 # ------------------------------------------------------------ CPU oracle
 
 
@@ -523,9 +692,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["rgbd_frame", "batched", "serving"], default="rgbd_frame",
+    ap.add_argument("--workload", choices=["rgbd_frame", "batched", "serving", "fragment"], default="rgbd_frame",
                     help="rgbd_frame: the headline single-pair line; batched: 256 uneven pairs per call; "
-                         "serving: continuous-batching server under Poisson arrivals")
+                         "serving: continuous-batching server under Poisson arrivals; fragment: the 2M-point "
+                         "precision study (float32+compensated vs float64 against the oracle)")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
@@ -544,6 +714,8 @@ def main():
         run_batched(args, ws, rank, local)
     elif args.workload == "serving":
         run_serving(args, ws, rank, local)
+    elif args.workload == "fragment":
+        run_fragment(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

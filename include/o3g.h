@@ -143,6 +143,28 @@ O3G_API int32_t o3g_normal_equations(const o3g_grid* tgt, const float* d_src, in
                              float max_corr_dist, double* out_A, double* out_b, double* out_stats, void* stream);
 
 /*
+ * Arithmetic of the per-correspondence terms and of the block sums.
+ *   O3G_PREC_F32_COMPENSATED  J, r and the 27 products in float32, block sums
+ *                             compensated (TwoSum pairs), cross-block sums and
+ *                             the solve in float64 (the default everywhere).
+ *   O3G_PREC_F64              J, r and the products in float64 from the float32
+ *                             points and normals, each operation rounded once in
+ *                             the order r = ((dx nx + dy ny) + dz nz), block sums
+ *                             in plain float64 (the precision study's all-FP64
+ *                             variant).
+ * Correspondences and the float32 transform are the same under both.
+ */
+typedef enum { O3G_PREC_F32_COMPENSATED = 0, O3G_PREC_F64 = 1 } o3g_precision;
+
+/*
+ * o3g_normal_equations with a chosen o3g_precision; an unknown value is
+ * O3G_ERR_ARG.  Synchronous.
+ */
+O3G_API int32_t o3g_normal_equations_ex(const o3g_grid* tgt, const float* d_src, int64_t ns, int32_t stride,
+                                        const double* T, float max_corr_dist, int32_t precision, double* out_A,
+                                        double* out_b, double* out_stats, void* stream);
+
+/*
  * Point-to-plane ICP against a resident target grid that carries normals
  * (registration_icp(source, target, max_correspondence_distance, init,
  * TransformationEstimationPointToPlane()), Sec. 3.3).  Each iteration: the
@@ -161,6 +183,36 @@ O3G_API int32_t o3g_icp_point_to_plane_grid(const o3g_grid* tgt, const float* d_
                                     const double* init_T, double max_corr_dist, int32_t max_iter, double eps,
                                     double* out_T, double* out_fitness, double* out_rmse, int32_t* out_iters,
                                     void* stream);
+
+/*
+ * o3g_icp_point_to_plane_grid with a chosen o3g_precision for every iteration
+ * and for the final evaluation; an unknown value is O3G_ERR_ARG.
+ */
+O3G_API int32_t o3g_icp_point_to_plane_grid_ex(const o3g_grid* tgt, const float* d_src, int64_t ns, int32_t stride,
+                                               const double* init_T, double max_corr_dist, int32_t max_iter,
+                                               double eps, int32_t precision, double* out_T, double* out_fitness,
+                                               double* out_rmse, int32_t* out_iters, void* stream);
+
+/*
+ * Point-to-point ICP against a resident target grid (registration_icp with
+ * TransformationEstimationPointToPoint, Sec. 3.3; target normals not needed).
+ * Each iteration: the correspondence step of o3g_correspondences at the current
+ * pose, then the rigid motion (R, t) minimising sum_i |R p_i + t - q_i|^2 over
+ * the correspondences in closed form (Horn's unit-quaternion solution: centroids,
+ * centred cross-covariance, the eigenvector of the largest eigenvalue of Horn's
+ * symmetric 4x4), and T <- [R t; 0 1] T.  Stops after max_iter updates, with
+ * O3G_WARN_FEW_CORR when fewer than 3 correspondences remain (pose of the last
+ * update kept), or when max(angle(R), |t|) < eps (eps <= 0: never).  When the
+ * two largest eigenvalues of that 4x4 are within 1e-6 E0, E0 = (sum|p - mean p|^2
+ * + sum|q - mean q|^2) / 2, the rotation is not determined (for example
+ * collinear matches): R = I, t = mean q - mean p and the status is
+ * O3G_WARN_DEGENERATE.  Results as in o3g_icp_point_to_plane_grid.
+ * Synchronous.
+ */
+O3G_API int32_t o3g_icp_point_to_point_grid(const o3g_grid* tgt, const float* d_src, int64_t ns, int32_t stride,
+                                            const double* init_T, double max_corr_dist, int32_t max_iter, double eps,
+                                            double* out_T, double* out_fitness, double* out_rmse, int32_t* out_iters,
+                                            void* stream);
 
 /*
  * One-shot form of the above on raw device clouds: builds a grid over the
@@ -208,6 +260,38 @@ O3G_API int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid* co
                                              const double* max_corr_dist, int32_t max_iter, double eps,
                                              double* out_T, double* out_fitness, double* out_rmse,
                                              int32_t* out_iters, int32_t* out_status, void* stream);
+
+/*
+ * Hypothesis validation (the step RANSAC-based global registration spends its
+ * time in, Sec. 3.3): for each candidate pose T_h, the correspondence step of
+ * o3g_correspondences at T_h over the whole source, then
+ *   out_fitness[h] = |C_h| / ns,  out_rmse[h] = sqrt(sum_{C_h} d2 / |C_h|)
+ *   (0 when C_h is empty),  out_inliers[h] = |C_h| (may be NULL).
+ * poses: n_poses x 16 row-major float64, host.  Outputs: host arrays of
+ * n_poses.  The target grid needs no normals.  A non-finite pose or source
+ * coordinate: O3G_ERR_NONFINITE.  Synchronous.
+ */
+O3G_API int32_t o3g_evaluate_poses(const o3g_grid* tgt, const float* d_src, int64_t ns, int32_t stride, int32_t n_poses,
+                                   const double* poses, double max_corr_dist, double* out_fitness, double* out_rmse,
+                                   int64_t* out_inliers, void* stream);
+
+/*
+ * Voxel downsampling (voxel_down_sample, Sec. 3.1 and Fig. 1): one output point
+ * per occupied voxel, the centroid of the input points in it.
+ *   voxel index  (floor(x / voxel), floor(y / voxel), floor(z / voxel)), each
+ *                quotient one correctly rounded float32 division
+ *   order        voxels in increasing (ix, iy, iz), x most significant
+ *   centroid     float64 sum of the voxel's points in increasing input index,
+ *                divided by their count, rounded to float32
+ * Points with a non-finite coordinate are dropped.  d_xyz: n rows of `stride`
+ * floats (x, y, z first), device, caller-owned.  d_out: device, caller-owned,
+ * room for 3 n floats (packed xyz; *out_n rows are written).  d_counts: device,
+ * room for n int32 (points per voxel), or NULL.  A voxel index outside
+ * [-2^30, 2^30], voxel <= 0 or not finite: O3G_ERR_ARG (outputs untouched).
+ * Synchronous.
+ */
+O3G_API int32_t o3g_voxel_down_sample(const float* d_xyz, int64_t n, int32_t stride, float voxel, float* d_out,
+                                      int32_t* d_counts, int64_t* out_n, void* stream);
 
 /*
  * Serving: registration requests of any size handled as a continuously batched
@@ -285,13 +369,17 @@ O3G_API int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* tgt, const f
  * forgets them.  kind: O3G_KERNEL_ICP_CORR (per-iteration correspondence +
  * reduction), O3G_KERNEL_ICP_SOLVE (per-iteration reduce + solve + update),
  * O3G_KERNEL_NORMALS (normal estimation), O3G_KERNEL_GRID (one whole grid build),
- * O3G_KERNEL_ICP_BATCH (all iteration launches of one batched call, one record).
+ * O3G_KERNEL_ICP_BATCH (all iteration launches of one batched call, one record),
+ * O3G_KERNEL_VOXEL (one whole voxel downsampling call), O3G_KERNEL_EVAL (the
+ * launches of one o3g_evaluate_poses call, one record).
  */
 #define O3G_KERNEL_ICP_CORR 0
 #define O3G_KERNEL_ICP_SOLVE 1
 #define O3G_KERNEL_NORMALS 2
 #define O3G_KERNEL_GRID 3
 #define O3G_KERNEL_ICP_BATCH 4
+#define O3G_KERNEL_VOXEL 5
+#define O3G_KERNEL_EVAL 6
 O3G_API int64_t o3g_launch_count(void);
 O3G_API int32_t o3g_timing_enable(int32_t on);
 O3G_API int32_t o3g_timing_read(int32_t kind, double* total_ms, int64_t* launches, int32_t reset);

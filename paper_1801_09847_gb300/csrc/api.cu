@@ -71,7 +71,7 @@ void dfree(void* p, cudaStream_t s) {
 namespace {
 std::atomic<int64_t> g_launches{0};
 std::atomic<int> g_timing{0};
-constexpr int kKinds = 5;
+constexpr int kKinds = 7;
 struct EventPair {
   cudaEvent_t a, b;
 };

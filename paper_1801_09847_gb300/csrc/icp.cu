@@ -58,6 +58,9 @@ struct IcpState {
 
 enum Mode : int { kIterate = 0, kEquations = 1, kEvaluate = 2, kCorrOnly = 3 };
 
+// Which transformation estimate an iteration makes (Sec. 3.3).
+enum Kind : int { kPointToPlane = 0, kPointToPoint = 1 };
+
 __global__ void k_init_state(IcpState* st, Pose T) {
   if (threadIdx.x != 0) return;
   for (int k = 0; k < 16; ++k) st->T[k] = T.m[k];
@@ -216,24 +219,47 @@ __device__ void box_search_global(const GridView& g, float cell, float px, float
 
 // Block-wide search with the candidate cells staged in shared memory.  The
 // block's queries are consecutive in Morton order, so the boxes their bounds
-// allow overlap.  The block takes the union of those boxes; if it is small
-// enough, it loads the union's column offsets (one round trip), copies every
-// point of the union into shared memory (one coalesced pass), and then each
-// thread scans exactly its own box there.  This replaces each thread's chain of
-// dependent global loads with two block-wide round trips.  Returns false, with
-// nothing changed, when the union does not fit: the caller then searches from
-// global memory.  All threads of the block must call this.
-constexpr int kStageCols = 64;   // columns of the union box
+// allow overlap.  The block takes the bounding box of those boxes, and for each
+// of its (x, y) columns the union of the z-ranges its threads will scan there;
+// if that fits, it loads those columns' cell offsets (one round trip), copies
+// every point of those z-ranges into shared memory (one warp per column,
+// coalesced), and then each thread scans exactly its own cells there.  This
+// replaces each thread's chain of dependent global loads with two block-wide
+// round trips, and stages only cells some thread needs.  Returns false, with
+// nothing changed, when the staged set does not fit: the caller then searches
+// from global memory.  All threads of the block must call this.
+constexpr int kStageCols = 128;  // columns of the bounding box
 constexpr int kStageZ = 15;      // z-cells per column
-constexpr int kStagePts = 2048;  // staged points (32 KB)
+constexpr int kStagePts = 1792;  // staged points (28 KB)
 
 struct Stage {
   float4 pts[kStagePts];
   uint32_t off[kStageCols][kStageZ + 1];  // global cell_start of each z-cell of each column
-  uint32_t base[kStageCols + 1];          // staged position of each column's first point
+  uint32_t base[kStageCols + 1];          // staged position of each column's first staged point
+  int zlo[kStageCols], zhi[kStageCols];   // union of the threads' z-ranges per column (box-relative)
   int box[6];
   int total;
 };
+
+// The z-range [zl, zh] (grid-relative) a query at p must scan in column
+// (x, y) for its current bound, or zl > zh when the column cannot hold a
+// candidate.  The same expression serves the planning and the scan, and the
+// bound only shrinks in between, so the scanned range stays inside the planned one.
+__device__ __forceinline__ void column_range(const GridView& g, float cell, float px, float py, float pz,
+                                             float margin, float bound, int x, int y, int az, int bz, int& zl,
+                                             int& zh) {
+  const float gx = slab_gap(px, x + g.lo_x, cell, margin);
+  const float gy = slab_gap(py, y + g.lo_y, cell, margin);
+  const float lim = __fmul_rn(bound, 1.0001f) - (gx * gx + gy * gy);
+  if (lim < 0.f) {
+    zl = 1;
+    zh = 0;
+    return;
+  }
+  const float rz = __fadd_rn(fast_sqrt(lim), margin);
+  zl = max(az, cell_coord(__fsub_rn(pz, rz), g.inv_cell) - g.lo_z);
+  zh = min(bz, cell_coord(__fadd_rn(pz, rz), g.inv_cell) - g.lo_z);
+}
 
 __device__ bool staged_search(const GridView& g, float cell, float px, float py, float pz, float r, bool live,
                               Nearest& nb, Stage& S) {
@@ -270,54 +296,79 @@ __device__ bool staged_search(const GridView& g, float cell, float px, float py,
   const int NCY = BY - AY + 1, NCZ = BZ - AZ + 1;
   const int ncol = (BX - AX + 1) * NCY;
   if (ncol > kStageCols || NCZ > kStageZ) return false;
-  // column offsets (all loads independent)
+  // the union of the z-ranges each thread will scan, per column
   for (int t = threadIdx.x; t < ncol; t += blockDim.x) {
-    const int col = ((AX + t / NCY) * g.sy + (AY + t % NCY)) * g.sz + AZ;
-    for (int z = 0; z <= NCZ; ++z) S.off[t][z] = g.cell_start[col + z];
+    S.zlo[t] = 0x7fffffff;
+    S.zhi[t] = -1;
   }
   __syncthreads();
-  if (threadIdx.x < 32) {  // exclusive scan of the column lengths (ncol <= 64: two per lane)
-    const int t0 = 2 * threadIdx.x, t1 = t0 + 1;
-    const uint32_t l0 = t0 < ncol ? S.off[t0][NCZ] - S.off[t0][0] : 0u;
-    const uint32_t l1 = t1 < ncol ? S.off[t1][NCZ] - S.off[t1][0] : 0u;
-    uint32_t inc = l0 + l1;
+  if (any) {
+    for (int x = ax; x <= bx; ++x)
+      for (int y = ay; y <= by; ++y) {
+        int zl, zh;
+        column_range(g, cell, px, py, pz, margin, nb.d2, x, y, az, bz, zl, zh);
+        if (zl > zh) continue;
+        const int t = (x - AX) * NCY + (y - AY);
+        atomicMin(&S.zlo[t], zl - AZ);
+        atomicMax(&S.zhi[t], zh - AZ);
+      }
+  }
+  __syncthreads();
+  // cell offsets of each column's planned range (all loads independent)
+  for (int t = threadIdx.x; t < ncol; t += blockDim.x) {
+    const int zl = S.zlo[t], zh = S.zhi[t];
+    if (zl > zh) continue;
+    const int col = ((AX + t / NCY) * g.sy + (AY + t % NCY)) * g.sz + AZ;
+    for (int z = zl; z <= zh + 1; ++z) S.off[t][z] = g.cell_start[col + z];
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {  // exclusive scan of the planned column lengths (kStageCols / 32 per lane)
+    constexpr int kPer = kStageCols / 32;
+    uint32_t len[kPer];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int t = kPer * threadIdx.x + k;
+      len[k] = (t < ncol && S.zlo[t] <= S.zhi[t]) ? S.off[t][S.zhi[t] + 1] - S.off[t][S.zlo[t]] : 0u;
+      sum += len[k];
+    }
+    uint32_t inc = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(full, inc, o);
       if (threadIdx.x >= o) inc += y;
     }
-    const uint32_t ex = inc - (l0 + l1);
-    if (t0 <= ncol) S.base[t0] = ex;
-    if (t1 <= ncol) S.base[t1] = ex + l0;
+    uint32_t run = inc - sum;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int t = kPer * threadIdx.x + k;
+      if (t <= ncol) S.base[t] = run;
+      run += len[k];
+    }
     if (threadIdx.x == 31) S.total = static_cast<int>(inc);
   }
   __syncthreads();
   const int M = S.total;
   if (M > kStagePts) return false;
-  for (int m = threadIdx.x; m < M; m += blockDim.x) {
-    int lo = 0, hi = ncol - 1;  // column holding staged position m: last t with base[t] <= m
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (static_cast<int>(S.base[mid]) <= m) lo = mid;
-      else hi = mid - 1;
+  {  // copy: one warp per column, lanes over its points
+    const int lane = threadIdx.x & 31;
+    for (int t = threadIdx.x >> 5; t < ncol; t += blockDim.x >> 5) {
+      if (S.zlo[t] > S.zhi[t]) continue;
+      const uint32_t g0 = S.off[t][S.zlo[t]];
+      const int len = static_cast<int>(S.off[t][S.zhi[t] + 1] - g0);
+      const int b = static_cast<int>(S.base[t]);
+      for (int k = lane; k < len; k += 32) S.pts[b + k] = g.pts[g0 + k];
     }
-    S.pts[m] = g.pts[S.off[lo][0] + (m - static_cast<int>(S.base[lo]))];
   }
   __syncthreads();
   if (!any) return true;
   for (int x = ax; x <= bx; ++x) {
-    const float gx = slab_gap(px, x + g.lo_x, cell, margin);
     for (int y = ay; y <= by; ++y) {
-      const float gy = slab_gap(py, y + g.lo_y, cell, margin);
-      const float lim = __fmul_rn(nb.d2, 1.0001f) - (gx * gx + gy * gy);
-      if (lim < 0.f) continue;
-      const float rz = __fadd_rn(fast_sqrt(lim), margin);
-      const int zl = max(az, cell_coord(__fsub_rn(pz, rz), g.inv_cell) - g.lo_z);
-      const int zh = min(bz, cell_coord(__fadd_rn(pz, rz), g.inv_cell) - g.lo_z);
+      int zl, zh;
+      column_range(g, cell, px, py, pz, margin, nb.d2, x, y, az, bz, zl, zh);
       if (zl > zh) continue;
       const int t = (x - AX) * NCY + (y - AY);
-      const uint32_t o0 = S.off[t][0];
-      const int shift = static_cast<int>(S.base[t]) - static_cast<int>(o0);
+      const int shift = static_cast<int>(S.base[t]) - static_cast<int>(S.off[t][S.zlo[t]]);
       const uint32_t gb = S.off[t][zl - AZ], ge = S.off[t][zh + 1 - AZ];
       for (uint32_t k = gb; k < ge; ++k) consider(nb, S.pts[static_cast<int>(k) + shift], static_cast<int>(k), px, py, pz);
     }
@@ -377,6 +428,31 @@ __device__ void block_reduce_store(float (&v)[32], float (&c)[32], double* __res
     float s = ws[0][t], cc = wc[0][t];
     for (int w = 1; w < kThreads / 32; ++w) add_pair(s, cc, ws[w][t], wc[w][t]);
     out[t] = static_cast<double>(s) + static_cast<double>(cc);
+  }
+}
+
+// The all-float64 form of block_reduce_store: the same butterfly reduce-scatter
+// and in-order warp combination on doubles, plain float64 adds.
+__device__ void block_reduce_store_f64(double (&v)[32], double* __restrict__ out) {
+  __shared__ double ws[kThreads / 32][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int half = 16; half >= 1; half >>= 1) {
+    const bool upper = (lane & half) != 0;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const double send = upper ? v[j] : v[j + half];
+      const double keep = upper ? v[j + half] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+    }
+  }
+  ws[warp][lane] = v[0];
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < kPartial) {
+    double s = ws[0][t];
+    for (int w = 1; w < kThreads / 32; ++w) s += ws[w][t];
+    out[t] = s;
   }
 }
 
@@ -527,11 +603,240 @@ __device__ void solve_update(const double* sums, IcpState* __restrict__ st, doub
   }
 }
 
+// Largest root of x^4 + c2 x^2 + c1 x + c0 (the characteristic polynomial of a
+// trace-free symmetric 4x4 scaled so that every eigenvalue lies in [-1, 1]),
+// by Newton's method from x = 1.  To the right of its largest root the quartic
+// is increasing and convex (the roots of its derivatives interlace its own), so
+// the iterates fall monotonically onto the root: float32 steps first, then
+// float64 steps until the step is below 1e-15 (at most 64 of each).
+__device__ double quartic_top_root(double c2, double c1, double c0) {
+  const float f2 = static_cast<float>(c2), f1 = static_cast<float>(c1), f0 = static_cast<float>(c0);
+  float xf = 1.0f;
+  for (int k = 0; k < 64; ++k) {
+    const float x2 = xf * xf;
+    const float f = (x2 + f2) * x2 + (f1 * xf + f0);
+    const float d = (4.0f * x2 + 2.0f * f2) * xf + f1;
+    if (!(f > 0.0f) || !(d > 0.0f)) break;
+    const float nx = xf - f / d;
+    if (!(nx < xf)) break;
+    xf = nx;
+  }
+  double x = xf;
+  for (int k = 0; k < 64; ++k) {
+    const double x2 = x * x;
+    const double f = fma(x2 + c2, x2, fma(c1, x, c0));
+    const double d = fma(fma(4.0, x2, 2.0 * c2), x, c1);
+    if (!(d > 1e-300)) break;
+    const double step = f * recip(d);
+    x -= step;
+    if (!(fabs(step) > 1e-15)) break;
+  }
+  return x;
+}
+
+// Largest root of x^3 + a2 x^2 + a1 x + a0 below x0 (the quartic above with
+// its top root x0 divided out), by the same Newton iteration from x0.
+__device__ double cubic_top_root(double a2, double a1, double a0, double x0) {
+  double x = x0;
+  for (int k = 0; k < 64; ++k) {
+    const double f = fma(fma(x + a2, x, a1), x, a0);
+    const double d = fma(fma(3.0, x, 2.0 * a2), x, a1);
+    if (!(d > 1e-300)) break;
+    const double step = f * recip(d);
+    x -= step;
+    if (!(fabs(step) > 1e-15)) break;
+  }
+  return x;
+}
+
+// Point-to-point update on one warp in float64 (TransformationEstimationPointToPoint,
+// Sec. 3.3): the rigid motion minimising sum |R p + t - q|^2 over the matched
+// pairs, by Horn's unit-quaternion closed form.  The block sums hold the
+// moments of a = p - c and b = q - c for a fixed reference point c near the
+// clouds (sums 0-2: a, 3-5: b, 6-14: a b^T row-major, 15: |a|^2, 16: |b|^2),
+// from which the centred cross-covariance S and E0 = (sum|a - mean a|^2 +
+// sum|b - mean b|^2) / 2 follow.  Horn's trace-free symmetric N (built from S)
+// is scaled by 1 / |N|_F, which puts every eigenvalue in [-1, 1]; its largest
+// eigenvalue comes from the characteristic quartic (Newton, as in the QCP method
+// of Theobald, Acta Cryst. A 61, 2005), the second largest from the deflated
+// cubic.  A gap below 1e-6 E0 (E0 bounds every eigenvalue's magnitude) leaves
+// the rotation undetermined: R = I, the degenerate flag is set.  (Newton on a
+// double root stops about 1e-8 from it, so a threshold near the float64
+// rounding level would miss exact degeneracy; float32 inputs cannot fix a
+// rotation with a smaller gap anyway.)  Otherwise the
+// quaternion is the column of adj(N - lambda I) whose diagonal entry has the
+// largest magnitude (for a simple eigenvalue adj is a multiple of v v^T),
+// normalised with w >= 0.
+// t = mean q - R mean p;  T <- [R t; 0 1] T;  done when max(angle, |t|) < eps.
+__device__ void solve_update_p2p(const double* sums, IcpState* __restrict__ st, double eps, float cx, float cy,
+                                 float cz) {
+  // the 3x3 and 4x4 matrices live in shared memory and each lane handles one
+  // entry, which keeps the register footprint of the kernel that runs this low
+  __shared__ double sS[9], sN[16], sM[16];
+  const int lane = threadIdx.x & 31;
+  const double n = sums[29];
+  const double inv_n = recip(n);
+  if (lane < 9) {
+    const int i = lane / 3, j = lane % 3;
+    sS[lane] = fma(-n * (sums[i] * inv_n), sums[3 + j] * inv_n, sums[6 + lane]);
+  }
+  __syncwarp();
+  double gp = sums[15], gq = sums[16];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    gp = fma(-n * (sums[k] * inv_n), sums[k] * inv_n, gp);
+    gq = fma(-n * (sums[3 + k] * inv_n), sums[3 + k] * inv_n, gq);
+  }
+  const double E0 = 0.5 * (gp + gq);
+  if (lane < 16) {
+    // Horn's N from S (rows x, y, z of S index the source, columns the target)
+    const double Sxx = sS[0], Sxy = sS[1], Sxz = sS[2], Syx = sS[3], Syy = sS[4], Syz = sS[5], Szx = sS[6],
+                 Szy = sS[7], Szz = sS[8];
+    double v;
+    switch (lane) {
+      case 0: v = Sxx + Syy + Szz; break;
+      case 1: case 4: v = Syz - Szy; break;
+      case 2: case 8: v = Szx - Sxz; break;
+      case 3: case 12: v = Sxy - Syx; break;
+      case 5: v = Sxx - Syy - Szz; break;
+      case 6: case 9: v = Sxy + Syx; break;
+      case 7: case 13: v = Szx + Sxz; break;
+      case 10: v = -Sxx + Syy - Szz; break;
+      case 11: case 14: v = Syz + Szy; break;
+      default: v = -Sxx - Syy + Szz; break;
+    }
+    sN[lane] = v;
+  }
+  __syncwarp();
+  double w = 1.0, x = 0.0, y = 0.0, z = 0.0;
+  bool degenerate = true;
+  {
+    // characteristic polynomial x^4 + c2 x^2 + c1 x + c0 of the trace-free N
+    // scaled by 1 / |N|_F (so every eigenvalue lies in [-1, 1]):
+    // c2 = -tr(N^2) / 2, c1 = -tr(N^3) / 3, c0 = det N (Laplace expansion along
+    // rows 0, 1: lane k < 6 takes column pair k), each times the scale's power
+    double t2 = 0.0, t3 = 0.0, dt = 0.0;
+    if (lane < 16) {
+      const int i = lane >> 2, j = lane & 3;
+      double n2 = 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) n2 = fma(sN[4 * i + k], sN[4 * k + j], n2);
+      t2 = sN[lane] * sN[lane];
+      t3 = n2 * sN[4 * j + i];
+    }
+    if (lane < 6) {
+      const int a = lane < 3 ? 0 : (lane < 5 ? 1 : 2);
+      const int b = lane < 3 ? lane + 1 : (lane < 5 ? lane - 1 : 3);
+      const int c = (a != 0 && b != 0) ? 0 : ((a != 1 && b != 1) ? 1 : 2);
+      const int d = 6 - a - b - c;
+      const double top = sN[a] * sN[4 + b] - sN[b] * sN[4 + a];
+      const double bot = sN[8 + c] * sN[12 + d] - sN[8 + d] * sN[12 + c];
+      dt = ((1 + a + b) & 1) ? -top * bot : top * bot;
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      t2 += __shfl_xor_sync(0xffffffffu, t2, off);
+      t3 += __shfl_xor_sync(0xffffffffu, t3, off);
+      dt += __shfl_xor_sync(0xffffffffu, dt, off);
+    }
+    // every lane now holds the same bits (each butterfly step adds the same two
+    // partial sums in swapped order, and addition commutes), so the root
+    // iterations and the branches below are warp-uniform
+    const double nf = sqrt(t2);
+    if (nf > 0.0 && E0 > 0.0) {
+      const double sc = 1.0 / nf, sc2 = sc * sc;
+      const double c2 = -0.5, c1 = -t3 / 3.0 * (sc2 * sc), c0 = dt * (sc2 * sc2);
+      const double l1 = quartic_top_root(c2, c1, c0);
+      const double a1 = fma(l1, l1, c2);
+      const double l2 = cubic_top_root(l1, a1, fma(l1, a1, c1), l1);
+      degenerate = !(l1 - l2 > 1e-6 * E0 * sc);
+      if (!degenerate && lane < 16) sM[lane] = sN[lane] * sc - ((lane % 5 == 0) ? l1 : 0.0);
+    }
+    if (!degenerate) {
+      __syncwarp();
+      // cofactor (i, j) of M = N - l1 I on lane 4 i + j
+      double cof = 0.0;
+      if (lane < 16) {
+        const int i = lane >> 2, j = lane & 3;
+        const int r0 = i == 0 ? 1 : 0, r1 = i <= 1 ? 2 : 1, r2 = i <= 2 ? 3 : 2;
+        const int q0 = j == 0 ? 1 : 0, q1 = j <= 1 ? 2 : 1, q2 = j <= 2 ? 3 : 2;
+        const double d3 = sM[4 * r0 + q0] * (sM[4 * r1 + q1] * sM[4 * r2 + q2] - sM[4 * r1 + q2] * sM[4 * r2 + q1]) -
+                          sM[4 * r0 + q1] * (sM[4 * r1 + q0] * sM[4 * r2 + q2] - sM[4 * r1 + q2] * sM[4 * r2 + q0]) +
+                          sM[4 * r0 + q2] * (sM[4 * r1 + q0] * sM[4 * r2 + q1] - sM[4 * r1 + q1] * sM[4 * r2 + q0]);
+        cof = ((i + j) & 1) ? -d3 : d3;
+      }
+      // adj(M) = (l2 - l1)(l3 - l1)(l4 - l1) v v^T: its diagonal is <= 0, and the
+      // entry of largest magnitude marks the best-conditioned column
+      const double e0 = fabs(shfl_d(cof, 0)), e1 = fabs(shfl_d(cof, 5)), e2 = fabs(shfl_d(cof, 10)),
+                   e3 = fabs(shfl_d(cof, 15));
+      int jb = 0;
+      double best = e0;
+      if (e1 > best) { best = e1; jb = 1; }
+      if (e2 > best) { best = e2; jb = 2; }
+      if (e3 > best) { best = e3; jb = 3; }
+      w = shfl_d(cof, jb);
+      x = shfl_d(cof, 4 + jb);
+      y = shfl_d(cof, 8 + jb);
+      z = shfl_d(cof, 12 + jb);
+      double len = sqrt(w * w + x * x + y * y + z * z);
+      if (!(len > 0.0)) {  // no usable column: treat as undetermined
+        degenerate = true;
+        len = 1.0;
+      }
+      if (w < 0.0) len = -len;
+      const double il = 1.0 / len;
+      w *= il;
+      x *= il;
+      y *= il;
+      z *= il;
+    }
+  }
+  if (degenerate) w = 1.0, x = y = z = 0.0;
+  // lane 4 r + c: entry (r, c) of [dR t] T, r < 3
+  const int r = (lane >> 2) < 3 ? (lane >> 2) : 0, c = lane & 3;
+  double d0, d1, d2;
+  if (r == 0) {
+    d0 = w * w + x * x - y * y - z * z;
+    d1 = 2.0 * (x * y - w * z);
+    d2 = 2.0 * (x * z + w * y);
+  } else if (r == 1) {
+    d0 = 2.0 * (x * y + w * z);
+    d1 = w * w - x * x + y * y - z * z;
+    d2 = 2.0 * (y * z - w * x);
+  } else {
+    d0 = 2.0 * (x * z - w * y);
+    d1 = 2.0 * (y * z + w * x);
+    d2 = w * w - x * x - y * y + z * z;
+  }
+  // translation row r: mean q - dR mean p (means of a and b shifted back by c)
+  const double mpx = fma(sums[0], inv_n, static_cast<double>(cx)), mpy = fma(sums[1], inv_n, static_cast<double>(cy)),
+               mpz = fma(sums[2], inv_n, static_cast<double>(cz));
+  const double mq_r = fma(sums[3 + r], inv_n, static_cast<double>(r == 0 ? cx : (r == 1 ? cy : cz)));
+  const double tr = mq_r - (d0 * mpx + d1 * mpy + d2 * mpz);
+  const double Tpre = lane < 12 ? st->T[lane] : 0.0;
+  const double t0 = shfl_d(Tpre, c), t1 = shfl_d(Tpre, 4 + c), t2 = shfl_d(Tpre, 8 + c);
+  double tn = d0 * t0 + d1 * t1 + d2 * t2;
+  if (c == 3) tn += tr;
+  const double tx = shfl_d(tr, 0), ty = shfl_d(tr, 4), tz = shfl_d(tr, 8);
+  if (lane < 12) {
+    st->T[lane] = tn;
+    if (c < 3) st->R[3 * r + c] = __double2float_rn(tn);
+    else st->t[r] = __double2float_rn(tn);
+  }
+  if (lane == 0) {
+    if (degenerate) st->degenerate = 1;
+    st->iters += 1;
+    const double angle = degenerate ? 0.0 : 2.0 * atan2(sqrt(x * x + y * y + z * z), w);
+    const double tl = sqrt(tx * tx + ty * ty + tz * tz);
+    if (eps > 0.0 && fmax(angle, tl) < eps) st->done = 1;
+  }
+}
+
 // Run by the last block of a launch once every group sum is stored: the float64
 // total in group order, then per mode the update, the stored normal equations,
 // or fitness / rmse.
 __device__ void finish(const double* __restrict__ gsums, int ngroups, IcpState* __restrict__ st, double eps,
-                       int mode, int ns) {
+                       int mode, int ns, int kind, float cx, float cy, float cz) {
   __shared__ double sums[kPartial];
   sum_partials(gsums, 0, ngroups, sums);
   if (threadIdx.x == 0) st->arrived = 0u;  // ready for the next launch
@@ -552,7 +857,7 @@ __device__ void finish(const double* __restrict__ gsums, int ngroups, IcpState* 
   }
   if (threadIdx.x >= 32) return;
   const bool bad = __any_sync(0xffffffffu, threadIdx.x < 27 && !isfinite(sums[threadIdx.x]));
-  if (bad || count < 6.0) {
+  if (bad || count < (kind == kPointToPoint ? 3.0 : 6.0)) {
     if (threadIdx.x == 0) {
       if (bad) st->nonfinite = 1;
       else st->few_corr = 1;
@@ -560,7 +865,8 @@ __device__ void finish(const double* __restrict__ gsums, int ngroups, IcpState* 
     }
     return;
   }
-  solve_update(sums, st, eps);
+  if (kind == kPointToPoint) solve_update_p2p(sums, st, eps, cx, cy, cz);
+  else solve_update(sums, st, eps);
 }
 
 // Everything one registration problem brings to an iteration launch.
@@ -568,6 +874,8 @@ struct PairDesc {
   GridView g;
   float cell, r;
   double eps;          // convergence threshold of this pair (<= 0: never)
+  int kind;            // kPointToPlane or kPointToPoint
+  float ctr[3];        // point-to-point: reference point subtracted before the moments
   const float4* src4;  // cell-sorted source, .w = original index bits
   int ns;
   int ntiles;          // ceil(ns / kThreads), at least 1
@@ -581,10 +889,67 @@ struct PairDesc {
   float* d2_out;
 };
 
+// Point-to-point terms of one correspondence, about the reference point c =
+// P.ctr (near the clouds, so the moments do not cancel): a = p - c, b = q - c,
+// a b^T (row-major), |a|^2, |b|^2, d2 and 1, in the slots solve_update_p2p reads.
+// The float32 form carries every term as an exact pair v + e: a and b by TwoSum,
+// each product by TwoProduct (the FMA gives the rounding error of a*b) plus the
+// cross terms of the low parts, so the compensated block sums see the exact
+// moments up to 2^-48 relative.  |a|^2 and |b|^2 only scale the degeneracy test
+// and stay plain float32.
+__device__ __forceinline__ void p2p_terms(const PairDesc& P, float3 p, float4 q, float d2, float (&v)[32],
+                                          float (&e)[32]) {
+  float ah[3], al[3], bh[3], bl[3];
+  const float pv[3] = {p.x, p.y, p.z}, qv[3] = {q.x, q.y, q.z};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    two_sum(pv[k], -P.ctr[k], ah[k], al[k]);
+    two_sum(qv[k], -P.ctr[k], bh[k], bl[k]);
+    v[k] = ah[k];
+    e[k] = al[k];
+    v[3 + k] = bh[k];
+    e[3 + k] = bl[k];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float hh = __fmul_rn(ah[i], bh[j]);
+      v[6 + 3 * i + j] = hh;
+      e[6 + 3 * i + j] = fmaf(ah[i], bl[j], fmaf(al[i], bh[j], fmaf(ah[i], bh[j], -hh)));
+    }
+  v[15] = ah[0] * ah[0] + ah[1] * ah[1] + ah[2] * ah[2];
+  v[16] = bh[0] * bh[0] + bh[1] * bh[1] + bh[2] * bh[2];
+  v[28] = d2;
+  v[29] = 1.f;
+}
+
+// The all-float64 form: a and b are exact in float64, the products round once.
+__device__ __forceinline__ void p2p_terms(const PairDesc& P, float3 p, float4 q, float d2, double (&v)[32]) {
+  const double a[3] = {static_cast<double>(p.x) - P.ctr[0], static_cast<double>(p.y) - P.ctr[1],
+                       static_cast<double>(p.z) - P.ctr[2]};
+  const double b[3] = {static_cast<double>(q.x) - P.ctr[0], static_cast<double>(q.y) - P.ctr[1],
+                       static_cast<double>(q.z) - P.ctr[2]};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    v[k] = a[k];
+    v[3 + k] = b[k];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) v[6 + 3 * i + j] = a[i] * b[j];
+  v[15] = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+  v[16] = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  v[28] = d2;
+  v[29] = 1.0;
+}
+
 // One tile (kThreads cell-sorted source points, tile j of pair P) of one ICP step.
 // mode kIterate: skipped once the pair is done; the other modes always run.
 // kCorrOnly writes corr/d2 and no sums.  The last tile of the pair to finish
 // performs the pair's solve and update (see finish).  Block-uniform control flow.
+template <bool F64>
 __device__ void icp_tile(const PairDesc& P, int j, int mode, Stage& stage) {
   if (mode == kIterate && P.st->done) return;
   float R[9], t[3];
@@ -593,9 +958,6 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, Stage& stage) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) t[k] = P.st->t[k];
   const float r2 = __fmul_rn(P.r, P.r);
-  float v[32], c[32];
-#pragma unroll
-  for (int k = 0; k < 32; ++k) v[k] = c[k] = 0.f;
   const int i = j * kThreads + threadIdx.x;
   // every lane runs the search (lanes past the end on a far-away dummy point) so
   // that the warp-wide exchange of first candidates is convergent
@@ -608,13 +970,58 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, Stage& stage) {
   if (!staged_search(P.g, P.cell, p.x, p.y, p.z, P.r, live, nb, stage) && live)
     box_search_global(P.g, P.cell, p.x, p.y, p.z, P.r, nb);
   const float bd2 = nb.d2;
+  const int bp = live ? nb.pos : -1;
   if (live) {
-    const int bp = nb.pos;
     if (P.hints) P.hints[i] = bp;
     if (mode == kCorrOnly) {
       const int o = __float_as_int(s.w);
       P.corr_out[o] = bp >= 0 ? __float_as_int(P.g.pts[bp].w) : -1;
       P.d2_out[o] = bp >= 0 ? bd2 : 0.f;
+    }
+  }
+  if (mode == kCorrOnly) return;
+  double* const partial = P.partials + static_cast<size_t>(j) * kPartial;
+  if constexpr (F64) {
+    // every term in float64 from the float32 p, q, n, each product and sum
+    // rounded once in the oracle's order (no fused multiply-add)
+    double v[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = 0.0;
+    if (bp >= 0 && P.kind == kPointToPoint) {
+      p2p_terms(P, p, P.g.pts[bp], bd2, v);
+    } else if (bp >= 0) {
+      const float4 q = P.g.pts[bp];
+      const float4 n = P.g.nrm[bp];
+      const double px = p.x, py = p.y, pz = p.z, nx = n.x, ny = n.y, nz = n.z;
+      const double dx = __dsub_rn(px, static_cast<double>(q.x));
+      const double dy = __dsub_rn(py, static_cast<double>(q.y));
+      const double dz = __dsub_rn(pz, static_cast<double>(q.z));
+      const double res = __dadd_rn(__dadd_rn(__dmul_rn(dx, nx), __dmul_rn(dy, ny)), __dmul_rn(dz, nz));
+      double J[6];
+      J[0] = __dsub_rn(__dmul_rn(py, nz), __dmul_rn(pz, ny));
+      J[1] = __dsub_rn(__dmul_rn(pz, nx), __dmul_rn(px, nz));
+      J[2] = __dsub_rn(__dmul_rn(px, ny), __dmul_rn(py, nx));
+      J[3] = nx;
+      J[4] = ny;
+      J[5] = nz;
+      int k = 0;
+#pragma unroll
+      for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int b = a; b < 6; ++b) v[k++] = __dmul_rn(J[a], J[b]);
+#pragma unroll
+      for (int a = 0; a < 6; ++a) v[21 + a] = __dmul_rn(J[a], res);
+      v[27] = __dmul_rn(res, res);
+      v[28] = static_cast<double>(bd2);
+      v[29] = 1.0;
+    }
+    block_reduce_store_f64(v, partial);
+  } else {
+    float v[32], c[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = c[k] = 0.f;
+    if (bp >= 0 && P.kind == kPointToPoint) {
+      p2p_terms(P, p, P.g.pts[bp], bd2, v, c);
     } else if (bp >= 0) {
       const float4 q = P.g.pts[bp];
       const float4 n = P.g.nrm[bp];
@@ -638,9 +1045,8 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, Stage& stage) {
       v[28] = bd2;
       v[29] = 1.f;
     }
+    block_reduce_store(v, c, partial);
   }
-  if (mode == kCorrOnly) return;
-  block_reduce_store(v, c, P.partials + static_cast<size_t>(j) * kPartial);
   // The last block of each group of kGroup blocks sums the group (float64, block
   // order); the last group to finish sums the groups and finishes the launch.
   __shared__ bool last;
@@ -665,7 +1071,7 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, Stage& stage) {
   __syncthreads();
   if (!last) return;
   __threadfence();
-  finish(P.gsums, ngroups, P.st, P.eps, mode, P.ns);
+  finish(P.gsums, ngroups, P.st, P.eps, mode, P.ns, P.kind, P.ctr[0], P.ctr[1], P.ctr[2]);
 }
 
 // One ICP step of every pair: a persistent kernel whose blocks walk the global
@@ -673,7 +1079,9 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, Stage& stage) {
 // `one` owns every tile.  The pair of a tile comes from tile_pair.  Tiles of
 // different pairs are independent; each pair's partial sums sit in fixed per-tile
 // slots, so every pair's result is the same alone and in any batch.
-__global__ void __launch_bounds__(kThreads) k_icp_iter(PairDesc one, const PairDesc* __restrict__ pairs,
+// F64 selects the all-float64 per-correspondence arithmetic (precision study).
+template <bool F64>
+__global__ void __launch_bounds__(kThreads, 5) k_icp_iter(PairDesc one, const PairDesc* __restrict__ pairs,
                                                        const int* __restrict__ tile_pair,
                                                        const int* __restrict__ ntiles_total, int mode) {
   __shared__ Stage stage;
@@ -682,19 +1090,21 @@ __global__ void __launch_bounds__(kThreads) k_icp_iter(PairDesc one, const PairD
   for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
     if (threadIdx.x == 0) P = pairs ? pairs[tile_pair[tile]] : one;
     __syncthreads();
-    icp_tile(P, tile - P.tile0, mode, stage);
+    icp_tile<F64>(P, tile - P.tile0, mode, stage);
     __syncthreads();
   }
 }
 
 // Blocks of the persistent iteration kernel: every tile at once when they fit
 // on the GPU together, else as many as are resident (they loop over tiles).
+template <bool F64 = false>
 int persistent_blocks(int ntiles) {
   static int resident = 0;
   if (resident == 0) {
     int dev = 0, sms = kNumSMs, per_sm = 1;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_icp_iter, kThreads, 0) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_icp_iter<F64>, kThreads, 0) != cudaSuccess ||
+        per_sm < 1)
       per_sm = 1;
     (void)cudaGetLastError();
     resident = sms * per_sm;
@@ -753,13 +1163,18 @@ struct Work {
     return O3G_OK;
   }
   int32_t launch(const o3g_grid* g, int ns, float r, double eps, int mode, int32_t* corr, float* d2,
-                 cudaStream_t s) {
+                 cudaStream_t s, bool f64 = false, int kind = kPointToPlane) {
     double* pp = partials.as<double>();
     PairDesc P;
     P.g = g->view();
     P.cell = g->cell;
     P.r = r;
     P.eps = eps;
+    P.kind = kind;
+    // the centre of the grid's box: near every point that can find a partner
+    for (int k = 0; k < 3; ++k)
+      P.ctr[k] = kind == kPointToPoint ? (static_cast<float>(g->lo[k]) + 0.5f * static_cast<float>(g->span[k])) * g->cell
+                                       : 0.f;
     P.src4 = src.pts;
     P.ns = ns;
     P.ntiles = nblk;
@@ -771,7 +1186,8 @@ struct Work {
     P.hints = (mode == kIterate || mode == kEvaluate) ? hints.as<int32_t>() : nullptr;
     P.corr_out = corr;
     P.d2_out = d2;
-    k_icp_iter<<<persistent_blocks(nblk), kThreads, 0, s>>>(P, nullptr, nullptr, nullptr, mode);
+    if (f64) k_icp_iter<true><<<persistent_blocks<true>(nblk), kThreads, 0, s>>>(P, nullptr, nullptr, nullptr, mode);
+    else k_icp_iter<false><<<persistent_blocks<false>(nblk), kThreads, 0, s>>>(P, nullptr, nullptr, nullptr, mode);
     count_launch();
     return O3G_OK;
   }
@@ -781,15 +1197,21 @@ struct Work {
 
 int32_t icp_run(const o3g_grid* g, const float* d_src, int64_t ns, int32_t stride, const double* init_T,
                 double max_corr_dist, int32_t max_iter, double eps, double* out_T, double* out_fitness,
-                double* out_rmse, int32_t* out_iters, cudaStream_t s) {
-  const char* fn = "o3g_icp_point_to_plane_grid";
+                double* out_rmse, int32_t* out_iters, cudaStream_t s, int32_t precision, bool point_to_point) {
+  const char* fn = point_to_point ? "o3g_icp_point_to_point_grid" : "o3g_icp_point_to_plane_grid";
+  const int kind = point_to_point ? kPointToPoint : kPointToPlane;
+  if (precision != O3G_PREC_F32_COMPENSATED && precision != O3G_PREC_F64) {
+    set_error("%s: unknown precision %d", fn, precision);
+    return O3G_ERR_ARG;
+  }
+  const bool f64 = precision == O3G_PREC_F64;
   if (!g || !out_T || !out_fitness || !out_rmse || max_iter < 0 || !(max_corr_dist >= 0.0) ||
       !std::isfinite(max_corr_dist)) {
     set_error("%s: invalid argument", fn);
     return O3G_ERR_ARG;
   }
   O3G_TRY_STATUS(check_src(fn, d_src, ns, stride));
-  if (!g->has_normals) {
+  if (!point_to_point && !g->has_normals) {
     set_error("%s: the target grid carries no normals (attach or estimate them first)", fn);
     return O3G_ERR_ARG;
   }
@@ -803,9 +1225,9 @@ int32_t icp_run(const o3g_grid* g, const float* d_src, int64_t ns, int32_t strid
   const int n = static_cast<int>(ns);
   for (int it = 0; it < max_iter; ++it) {
     TimedRegion tr(O3G_KERNEL_ICP_CORR, s);
-    w.launch(g, n, r, eps, kIterate, nullptr, nullptr, s);
+    w.launch(g, n, r, eps, kIterate, nullptr, nullptr, s, f64, kind);
   }
-  w.launch(g, n, r, eps, kEvaluate, nullptr, nullptr, s);
+  w.launch(g, n, r, eps, kEvaluate, nullptr, nullptr, s, f64, kind);
   O3G_TRY(cudaGetLastError());
   IcpState h;
   int aux[8];
@@ -817,7 +1239,7 @@ int32_t icp_run(const o3g_grid* g, const float* d_src, int64_t ns, int32_t strid
     return O3G_ERR_NONFINITE;
   }
   if (h.nonfinite) {
-    set_error("%s: the normal equations became non-finite (check the target normals)", fn);
+    set_error("%s: the update sums became non-finite", fn);
     return O3G_ERR_NONFINITE;
   }
   for (int k = 0; k < 16; ++k) out_T[k] = h.T[k];
@@ -855,11 +1277,12 @@ extern "C" int32_t o3g_correspondences(const o3g_grid* g, const float* d_src, in
   return O3G_OK;
 }
 
-extern "C" int32_t o3g_normal_equations(const o3g_grid* g, const float* d_src, int64_t ns, int32_t stride,
-                                        const double* T, float max_corr_dist, double* out_A, double* out_b,
-                                        double* out_stats, void* stream) {
+extern "C" int32_t o3g_normal_equations_ex(const o3g_grid* g, const float* d_src, int64_t ns, int32_t stride,
+                                           const double* T, float max_corr_dist, int32_t precision, double* out_A,
+                                           double* out_b, double* out_stats, void* stream) {
   const char* fn = "o3g_normal_equations";
-  if (!g || !out_A || !out_b || !out_stats || !(max_corr_dist >= 0.f) || !std::isfinite(max_corr_dist)) {
+  if (!g || !out_A || !out_b || !out_stats || !(max_corr_dist >= 0.f) || !std::isfinite(max_corr_dist) ||
+      (precision != O3G_PREC_F32_COMPENSATED && precision != O3G_PREC_F64)) {
     set_error("%s: invalid argument", fn);
     return O3G_ERR_ARG;
   }
@@ -875,7 +1298,8 @@ extern "C" int32_t o3g_normal_equations(const o3g_grid* g, const float* d_src, i
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Work w(s);
   O3G_TRY_STATUS(w.prepare(d_src, ns, stride, g->cell, T, s));
-  w.launch(g, static_cast<int>(ns), max_corr_dist, 0.0, kEquations, nullptr, nullptr, s);
+  w.launch(g, static_cast<int>(ns), max_corr_dist, 0.0, kEquations, nullptr, nullptr, s,
+           precision == O3G_PREC_F64);
   O3G_TRY(cudaGetLastError());
   IcpState h;
   O3G_TRY(cudaMemcpyAsync(&h, w.state.p, sizeof(IcpState), cudaMemcpyDeviceToHost, s));
@@ -886,12 +1310,35 @@ extern "C" int32_t o3g_normal_equations(const o3g_grid* g, const float* d_src, i
   return O3G_OK;
 }
 
+extern "C" int32_t o3g_normal_equations(const o3g_grid* g, const float* d_src, int64_t ns, int32_t stride,
+                                        const double* T, float max_corr_dist, double* out_A, double* out_b,
+                                        double* out_stats, void* stream) {
+  return o3g_normal_equations_ex(g, d_src, ns, stride, T, max_corr_dist, O3G_PREC_F32_COMPENSATED, out_A, out_b,
+                                 out_stats, stream);
+}
+
 extern "C" int32_t o3g_icp_point_to_plane_grid(const o3g_grid* g, const float* d_src, int64_t ns, int32_t stride,
                                                const double* init_T, double max_corr_dist, int32_t max_iter,
                                                double eps, double* out_T, double* out_fitness, double* out_rmse,
                                                int32_t* out_iters, void* stream) {
   return icp_run(g, d_src, ns, stride, init_T, max_corr_dist, max_iter, eps, out_T, out_fitness, out_rmse, out_iters,
-                 static_cast<cudaStream_t>(stream));
+                 static_cast<cudaStream_t>(stream), O3G_PREC_F32_COMPENSATED);
+}
+
+extern "C" int32_t o3g_icp_point_to_point_grid(const o3g_grid* g, const float* d_src, int64_t ns, int32_t stride,
+                                               const double* init_T, double max_corr_dist, int32_t max_iter,
+                                               double eps, double* out_T, double* out_fitness, double* out_rmse,
+                                               int32_t* out_iters, void* stream) {
+  return icp_run(g, d_src, ns, stride, init_T, max_corr_dist, max_iter, eps, out_T, out_fitness, out_rmse, out_iters,
+                 static_cast<cudaStream_t>(stream), O3G_PREC_F32_COMPENSATED, true);
+}
+
+extern "C" int32_t o3g_icp_point_to_plane_grid_ex(const o3g_grid* g, const float* d_src, int64_t ns, int32_t stride,
+                                                  const double* init_T, double max_corr_dist, int32_t max_iter,
+                                                  double eps, int32_t precision, double* out_T, double* out_fitness,
+                                                  double* out_rmse, int32_t* out_iters, void* stream) {
+  return icp_run(g, d_src, ns, stride, init_T, max_corr_dist, max_iter, eps, out_T, out_fitness, out_rmse, out_iters,
+                 static_cast<cudaStream_t>(stream), precision);
 }
 
 extern "C" int32_t o3g_icp_point_to_plane(const float* d_src, int64_t ns, int32_t src_stride, const float* d_tgt,
@@ -912,7 +1359,7 @@ extern "C" int32_t o3g_icp_point_to_plane(const float* d_src, int64_t ns, int32_
   int32_t st = o3g_grid_set_normals(g, d_tgt_nrm, n_nrm, nrm_stride, nullptr);
   if (st >= 0)
     st = icp_run(g, d_src, ns, src_stride, init_T, max_corr_dist, max_iter, 0.0, out_T, out_fitness, out_rmse, nullptr,
-                 nullptr);
+                 nullptr, O3G_PREC_F32_COMPENSATED);
   o3g_free_grid(g);
   return st;
 }
@@ -1032,6 +1479,8 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const 
     P.cell = g->cell;
     P.r = r;
     P.eps = eps;
+    P.kind = kPointToPlane;
+    P.ctr[0] = P.ctr[1] = P.ctr[2] = 0.f;
     P.src4 = src4;
     P.ns = n;
     P.ntiles = nblk;
@@ -1043,7 +1492,7 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const 
     P.hints = nullptr;
     P.corr_out = nullptr;
     P.d2_out = nullptr;
-    k_icp_iter<<<persistent_blocks(nblk), kThreads, 0, s>>>(P, nullptr, nullptr, nullptr, mode);
+    k_icp_iter<false><<<persistent_blocks(nblk), kThreads, 0, s>>>(P, nullptr, nullptr, nullptr, mode);
     count_launch();
   }
   O3G_TRY(cudaGetLastError());
@@ -1104,7 +1553,8 @@ int32_t run_iterations(const PairDesc* descs, const int* tile_pair, const int* d
   PairDesc dummy{};
   auto enqueue = [&](cudaStream_t q) {
     for (int it = 0; it <= max_iter; ++it)
-      k_icp_iter<<<blocks, kThreads, 0, q>>>(dummy, descs, tile_pair, d_ntiles, it < max_iter ? kIterate : kEvaluate);
+      k_icp_iter<false><<<blocks, kThreads, 0, q>>>(dummy, descs, tile_pair, d_ntiles,
+                                                    it < max_iter ? kIterate : kEvaluate);
   };
   cudaStream_t cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -1205,6 +1655,8 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
     P.cell = tgts[p]->cell;
     P.r = static_cast<float>(max_corr_dist[p]);
     P.eps = eps;
+    P.kind = kPointToPlane;
+    P.ctr[0] = P.ctr[1] = P.ctr[2] = 0.f;
     P.src4 = d_src4.as<float4>() + off[p];
     P.ns = static_cast<int>(ns[p]);
     P.ntiles = ntiles[p];
@@ -1388,6 +1840,8 @@ PairDesc slot_desc(o3g_server* sv, int k, int tile0) {
   P.cell = sl.grid->cell;
   P.r = sl.r;
   P.eps = sl.eps;
+  P.kind = kPointToPlane;
+  P.ctr[0] = P.ctr[1] = P.ctr[2] = 0.f;
   P.src4 = sl.src4;
   P.ns = sl.ns;
   P.ntiles = sl.ntiles;
@@ -1423,7 +1877,7 @@ int32_t launch_slots(o3g_server* sv, const std::vector<int>& ks, int mode) {
   O3G_TRY(cudaMemcpyAsync(sv->descs, d.data(), sizeof(PairDesc) * d.size(), cudaMemcpyHostToDevice, s));
   O3G_TRY(cudaMemcpyAsync(sv->tiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice, s));
   PairDesc dummy{};
-  k_icp_iter<<<persistent_blocks(static_cast<int>(t0)), kThreads, 0, s>>>(
+  k_icp_iter<false><<<persistent_blocks(static_cast<int>(t0)), kThreads, 0, s>>>(
       dummy, static_cast<const PairDesc*>(sv->descs), sv->tiles, sv->tiles + t0, mode);
   count_launch();
   O3G_TRY(cudaGetLastError());
@@ -1632,5 +2086,172 @@ extern "C" int32_t o3g_server_completed(o3g_server* sv, int64_t* ids, int32_t ca
     ids[n++] = kv.first;
   }
   *out_n = n;
+  return O3G_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Hypothesis validation: fitness and inlier rmse of the whole source at many
+// candidate poses against one target grid (the check RANSAC spends its time
+// in, Sec. 3.3).  One persistent launch walks the (pose, tile) work items; each
+// block runs the exact correspondence search of the ICP kernel for its tile at
+// its pose and stores (|C|, sum d2) for the tile; a second launch sums each
+// pose's tiles in fixed order on one warp.
+
+namespace o3g {
+namespace {
+
+struct PoseF {
+  float R[9], t[3];
+};
+
+__global__ void k_pose_round(const double* __restrict__ poses, int n, PoseF* __restrict__ out) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= n) return;
+  const double* T = poses + 16 * static_cast<size_t>(h);
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) out[h].R[3 * r + c] = __double2float_rn(T[4 * r + c]);
+    out[h].t[r] = __double2float_rn(T[4 * r + 3]);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 5) k_eval_poses(GridView g, float cell, float r,
+                                                             const float4* __restrict__ src4, int ns, int ntiles,
+                                                             const PoseF* __restrict__ poses, int n_poses,
+                                                             double* __restrict__ partials) {
+  __shared__ Stage stage;
+  __shared__ double ws[kThreads / 32][2];
+  const int64_t items = static_cast<int64_t>(ntiles) * n_poses;
+  const float r2 = __fmul_rn(r, r);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+    const int h = static_cast<int>(item / ntiles), j = static_cast<int>(item % ntiles);
+    float R[9], t[3];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[k] = poses[h].R[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t[k] = poses[h].t[k];
+    const int i = j * kThreads + threadIdx.x;
+    const bool live = i < ns;
+    const float4 s = live ? src4[i] : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
+    const float3 p = live ? xform_rn(R, t, s.x, s.y, s.z) : make_float3(3.0e38f, 3.0e38f, 3.0e38f);
+    Nearest nb{r2, 0x7fffffff, -1};
+    if (!staged_search(g, cell, p.x, p.y, p.z, r, live, nb, stage) && live)
+      box_search_global(g, cell, p.x, p.y, p.z, r, nb);
+    double cnt = (live && nb.pos >= 0) ? 1.0 : 0.0;
+    double d2 = (live && nb.pos >= 0) ? static_cast<double>(nb.d2) : 0.0;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+      d2 += __shfl_xor_sync(0xffffffffu, d2, off);
+    }
+    if (lane == 0) {
+      ws[warp][0] = cnt;
+      ws[warp][1] = d2;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      double v = ws[0][threadIdx.x];
+      for (int w = 1; w < kThreads / 32; ++w) v += ws[w][threadIdx.x];
+      partials[2 * static_cast<size_t>(item) + threadIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// One warp per pose: the pose's tiles summed in fixed order (lane l takes tiles
+// l, l + 32, ... in order, then a butterfly over lanes).
+__global__ void k_eval_sum(const double* __restrict__ partials, int ntiles, int n_poses, int ns,
+                           double* __restrict__ out) {
+  const int h = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (h >= n_poses) return;
+  double cnt = 0.0, d2 = 0.0;
+  for (int j = lane; j < ntiles; j += 32) {
+    const size_t k = 2 * (static_cast<size_t>(h) * ntiles + j);
+    cnt += partials[k];
+    d2 += partials[k + 1];
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+    d2 += __shfl_xor_sync(0xffffffffu, d2, off);
+  }
+  if (lane == 0) {
+    out[3 * static_cast<size_t>(h) + 0] = ns > 0 ? cnt / static_cast<double>(ns) : 0.0;
+    out[3 * static_cast<size_t>(h) + 1] = cnt > 0.0 ? sqrt(d2 / cnt) : 0.0;
+    out[3 * static_cast<size_t>(h) + 2] = cnt;
+  }
+}
+
+int eval_blocks(int64_t items) {
+  static int resident = 0;
+  if (resident == 0) {
+    int dev = 0, sms = kNumSMs, per_sm = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_poses, kThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    (void)cudaGetLastError();
+    resident = sms * per_sm;
+  }
+  return items < resident ? static_cast<int>(items < 1 ? 1 : items) : resident;
+}
+
+}  // namespace
+}  // namespace o3g
+
+extern "C" int32_t o3g_evaluate_poses(const o3g_grid* g, const float* d_src, int64_t ns, int32_t stride,
+                                      int32_t n_poses, const double* poses, double max_corr_dist,
+                                      double* out_fitness, double* out_rmse, int64_t* out_inliers, void* stream) {
+  const char* fn = "o3g_evaluate_poses";
+  if (!g || n_poses < 0 || (n_poses > 0 && (!poses || !out_fitness || !out_rmse)) || !(max_corr_dist >= 0.0) ||
+      !std::isfinite(max_corr_dist)) {
+    set_error("%s: invalid argument", fn);
+    return O3G_ERR_ARG;
+  }
+  O3G_TRY_STATUS(check_src(fn, d_src, ns, stride));
+  for (int64_t k = 0; k < 16 * static_cast<int64_t>(n_poses); ++k)
+    if (!std::isfinite(poses[k])) {
+      set_error("%s: pose %lld is not finite", fn, static_cast<long long>(k / 16));
+      return O3G_ERR_NONFINITE;
+    }
+  if (n_poses == 0) return O3G_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int ntiles = iter_blocks(ns);
+  const int64_t items = static_cast<int64_t>(ntiles) * n_poses;
+  SortedCloud src(s);
+  DevBuf d_poses(s), d_posef(s), part(s), out(s);
+  O3G_TRY_STATUS(sort_cloud(d_src, ns, stride, s, &src));
+  O3G_TRY(d_poses.alloc(sizeof(double) * 16 * static_cast<size_t>(n_poses)));
+  O3G_TRY(d_posef.alloc(sizeof(PoseF) * static_cast<size_t>(n_poses)));
+  O3G_TRY(part.alloc(sizeof(double) * 2 * static_cast<size_t>(items)));
+  O3G_TRY(out.alloc(sizeof(double) * 3 * static_cast<size_t>(n_poses)));
+  O3G_TRY(cudaMemcpyAsync(d_poses.p, poses, sizeof(double) * 16 * static_cast<size_t>(n_poses),
+                          cudaMemcpyHostToDevice, s));
+  {
+    TimedRegion tr(O3G_KERNEL_EVAL, s);
+    k_pose_round<<<(n_poses + 127) / 128, 128, 0, s>>>(d_poses.as<double>(), n_poses, d_posef.as<PoseF>());
+    k_eval_poses<<<eval_blocks(items), kThreads, 0, s>>>(g->view(), g->cell, static_cast<float>(max_corr_dist),
+                                                         src.pts, static_cast<int>(ns), ntiles, d_posef.as<PoseF>(),
+                                                         n_poses, part.as<double>());
+    k_eval_sum<<<(n_poses + 3) / 4, 128, 0, s>>>(part.as<double>(), ntiles, n_poses, static_cast<int>(ns),
+                                                 out.as<double>());
+    count_launch(3);
+  }
+  O3G_TRY(cudaGetLastError());
+  std::vector<double> h(3 * static_cast<size_t>(n_poses));
+  int aux[8];
+  O3G_TRY(cudaMemcpyAsync(h.data(), out.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+  O3G_TRY(cudaMemcpyAsync(aux, src.aux.p, sizeof(aux), cudaMemcpyDeviceToHost, s));
+  O3G_TRY(cudaStreamSynchronize(s));
+  if (aux[6]) {
+    set_error("%s: non-finite source coordinate", fn);
+    return O3G_ERR_NONFINITE;
+  }
+  for (int k = 0; k < n_poses; ++k) {
+    out_fitness[k] = h[3 * k];
+    out_rmse[k] = h[3 * k + 1];
+    if (out_inliers) out_inliers[k] = static_cast<int64_t>(h[3 * k + 2]);
+  }
   return O3G_OK;
 }

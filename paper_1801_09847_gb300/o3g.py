@@ -52,6 +52,14 @@ _SIGNATURES = {
     "o3g_estimate_normals": ([_vp, _f32, _i32, _vp, _vp, _i32, _vp], _i32),
     "o3g_correspondences": ([_vp, _vp, _i64, _i32, _f64p, _f32, _vp, _vp, _vp], _i32),
     "o3g_normal_equations": ([_vp, _vp, _i64, _i32, _f64p, _f32, _f64p, _f64p, _f64p, _vp], _i32),
+    "o3g_normal_equations_ex": ([_vp, _vp, _i64, _i32, _f64p, _f32, _i32, _f64p, _f64p, _f64p, _vp], _i32),
+    "o3g_evaluate_poses": ([_vp, _vp, _i64, _i32, _i32, _f64p, _f64, _f64p, _f64p,
+                            ctypes.POINTER(ctypes.c_int64), _vp], _i32),
+    "o3g_voxel_down_sample": ([_vp, _i64, _i32, _f32, _vp, _vp, ctypes.POINTER(ctypes.c_int64), _vp], _i32),
+    "o3g_icp_point_to_point_grid": ([_vp, _vp, _i64, _i32, _f64p, _f64, _i32, _f64, _f64p, _f64p, _f64p, _i32p, _vp],
+                                    _i32),
+    "o3g_icp_point_to_plane_grid_ex": ([_vp, _vp, _i64, _i32, _f64p, _f64, _i32, _f64, _i32, _f64p, _f64p, _f64p,
+                                        _i32p, _vp], _i32),
     "o3g_icp_point_to_plane_grid": ([_vp, _vp, _i64, _i32, _f64p, _f64, _i32, _f64, _f64p, _f64p, _f64p, _i32p, _vp],
                                     _i32),
     "o3g_icp_point_to_plane": ([_vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64, _i32, _f64p, _f64, _i32, _f64p, _f64p,
@@ -74,7 +82,18 @@ _SIGNATURES = {
     "o3g_timing_read": ([_i32, _f64p, ctypes.POINTER(_i64), _i32], _i32),
 }
 
-KERNEL_ICP_CORR, KERNEL_ICP_SOLVE, KERNEL_NORMALS, KERNEL_GRID, KERNEL_ICP_BATCH = 0, 1, 2, 3, 4
+KERNEL_ICP_CORR, KERNEL_ICP_SOLVE, KERNEL_NORMALS, KERNEL_GRID, KERNEL_ICP_BATCH, KERNEL_VOXEL, KERNEL_EVAL = range(7)
+# o3g_precision
+PREC_F32_COMPENSATED, PREC_F64 = 0, 1
+_PRECISIONS = {"f32": PREC_F32_COMPENSATED, "f64": PREC_F64}
+
+
+def _precision(precision) -> int:
+    if precision in _PRECISIONS:
+        return _PRECISIONS[precision]
+    if precision in (PREC_F32_COMPENSATED, PREC_F64):
+        return int(precision)
+    raise ValueError(f"unknown precision {precision!r} (use 'f32' or 'f64')")
 
 
 def launch_count() -> int:
@@ -237,15 +256,19 @@ def correspondences(grid: Grid, src, T, max_corr_dist: float, stream=None):
     return corr, d2
 
 
-def normal_equations(grid: Grid, src, T, max_corr_dist: float, stream=None):
-    """J^T J (6x6), J^T r (6), (sum r^2, sum d2, |C|) at pose T (Eq. 2)."""
+def normal_equations(grid: Grid, src, T, max_corr_dist: float, stream=None, precision="f32"):
+    """J^T J (6x6), J^T r (6), (sum r^2, sum d2, |C|) at pose T (Eq. 2).
+
+    precision "f32" (float32 terms, compensated block sums) or "f64" (all float64).
+    """
     p, ns, stride = _cloud(src, "src")
     A = np.zeros(36)
     b = np.zeros(6)
     stats = np.zeros(3)
     Tp = _pose(T)
-    _check(lib().o3g_normal_equations(grid.handle, p, ns, stride, _pp(Tp), float(max_corr_dist), _pp(A), _pp(b),
-                                      _pp(stats), _stream(stream)), "o3g_normal_equations")
+    _check(lib().o3g_normal_equations_ex(grid.handle, p, ns, stride, _pp(Tp), float(max_corr_dist),
+                                         _precision(precision), _pp(A), _pp(b), _pp(stats), _stream(stream)),
+           "o3g_normal_equations_ex")
     return A.reshape(6, 6), b, stats
 
 
@@ -255,16 +278,70 @@ def _result(st, T, fit, rmse, iters):
 
 
 def icp_point_to_plane_grid(grid: Grid, src, init_T, max_corr_dist: float, max_iter: int, eps: float = 0.0,
-                            stream=None) -> dict:
-    """registration_icp(..., TransformationEstimationPointToPlane()) against a resident target grid."""
+                            stream=None, precision="f32") -> dict:
+    """registration_icp(..., TransformationEstimationPointToPlane()) against a resident target grid.
+
+    precision "f32" (float32 terms, compensated block sums) or "f64" (all float64).
+    """
     p, ns, stride = _cloud(src, "src")
     T0 = _pose(init_T)
     T = np.zeros(16)
     fit, rmse, iters = _f64(), _f64(), _i32()
-    st = _check(lib().o3g_icp_point_to_plane_grid(grid.handle, p, ns, stride, _pp(T0), float(max_corr_dist),
+    if _precision(precision) == PREC_F32_COMPENSATED:
+        st = lib().o3g_icp_point_to_plane_grid(grid.handle, p, ns, stride, _pp(T0), float(max_corr_dist),
+                                               int(max_iter), float(eps), _pp(T), ctypes.byref(fit),
+                                               ctypes.byref(rmse), ctypes.byref(iters), _stream(stream))
+    else:
+        st = lib().o3g_icp_point_to_plane_grid_ex(grid.handle, p, ns, stride, _pp(T0), float(max_corr_dist),
+                                                  int(max_iter), float(eps), PREC_F64, _pp(T), ctypes.byref(fit),
+                                                  ctypes.byref(rmse), ctypes.byref(iters), _stream(stream))
+    st = _check(st, "o3g_icp_point_to_plane_grid")
+    return _result(st, T, fit, rmse, iters)
+
+
+def evaluate_poses(grid: Grid, src, poses, max_corr_dist: float, stream=None):
+    """Hypothesis validation (Sec. 3.3, RANSAC): fitness, inlier rmse and inlier count of the whole source at each
+    4x4 pose.  Returns (fitness [H], rmse [H], inliers [H]) as numpy arrays."""
+    p, ns, stride = _cloud(src, "src")
+    P = np.ascontiguousarray(np.asarray(poses, np.float64).reshape(-1, 16))
+    H = len(P)
+    fit = np.zeros(max(H, 1))
+    rmse = np.zeros(max(H, 1))
+    cnt = np.zeros(max(H, 1), np.int64)
+    _check(lib().o3g_evaluate_poses(grid.handle, p, ns, stride, H, _pp(P if H else np.zeros((1, 16))),
+                                    float(max_corr_dist), _pp(fit), _pp(rmse),
+                                    cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _stream(stream)),
+           "o3g_evaluate_poses")
+    return fit[:H], rmse[:H], cnt[:H]
+
+
+def voxel_down_sample(pts, voxel: float, stream=None, with_counts: bool = False):
+    """voxel_down_sample (Sec. 3.1, Fig. 1) on the GPU: centroids (float32 [M, 3], device) of the occupied voxels
+    in increasing (ix, iy, iz) order, and with_counts=True also the points per voxel (int32 [M])."""
+    torch = _torch()
+    p, n, stride = _cloud(pts, "pts")
+    out = torch.empty((max(n, 1), 3), dtype=torch.float32, device="cuda")
+    cnt = torch.empty((max(n, 1),), dtype=torch.int32, device="cuda") if with_counts else None
+    m = ctypes.c_int64()
+    _check(lib().o3g_voxel_down_sample(p, n, stride, float(voxel), _vp(out.data_ptr()),
+                                       _vp(cnt.data_ptr()) if cnt is not None else None, ctypes.byref(m),
+                                       _stream(stream)), "o3g_voxel_down_sample")
+    out = out[: m.value]
+    return (out, cnt[: m.value]) if with_counts else out
+
+
+def icp_point_to_point_grid(grid: Grid, src, init_T, max_corr_dist: float, max_iter: int, eps: float = 0.0,
+                            stream=None) -> dict:
+    """registration_icp(..., TransformationEstimationPointToPoint()) against a resident target grid
+    (normals not needed).  Returns dict(status, T, fitness, rmse, iters)."""
+    p, ns, stride = _cloud(src, "src")
+    T0 = _pose(init_T)
+    T = np.zeros(16)
+    fit, rmse, iters = _f64(), _f64(), _i32()
+    st = _check(lib().o3g_icp_point_to_point_grid(grid.handle, p, ns, stride, _pp(T0), float(max_corr_dist),
                                                   int(max_iter), float(eps), _pp(T), ctypes.byref(fit),
                                                   ctypes.byref(rmse), ctypes.byref(iters), _stream(stream)),
-                "o3g_icp_point_to_plane_grid")
+                "o3g_icp_point_to_point_grid")
     return _result(st, T, fit, rmse, iters)
 
 

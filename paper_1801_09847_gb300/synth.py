@@ -353,7 +353,8 @@ def fuse_segment(room: Room, poses: list, seed_words: tuple, voxel: float, noise
                  workers: int | None = None, intr: dict = PRIMESENSE):
     """Ray-cast every pose of a trajectory segment, move the points to world coordinates and fuse them at
     `voxel` m.  Frame k draws its depth noise from SeedSequence(seed_words + (k,)), so the result does not
-    depend on `workers` (frames are rendered in a spawn-context process pool when workers > 1)."""
+    depend on `workers` (frames are rendered in a spawn-context process pool when workers > 1, which, as
+    for any spawn pool, needs the calling script's top-level code behind ``if __name__ == "__main__":``)."""
     jobs = [(room, T, tuple(seed_words) + (k,), noise_k, intr) for k, T in enumerate(poses)]
     if workers is None:
         workers = min(16, len(jobs), os.cpu_count() or 1)
