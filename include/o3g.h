@@ -262,6 +262,20 @@ O3G_API int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid* co
                                              int32_t* out_iters, int32_t* out_status, void* stream);
 
 /*
+ * Launch configuration of the iteration kernels per size class (the knob the
+ * autotuner sets; no counterpart in the paper).  size_class = floor(log2(work
+ * tiles of a launch)), 0..31, a tile being 128 source points (of one pair, or of
+ * one pose in o3g_evaluate_poses).  cfg: 0 automatic (the latency form -- large
+ * shared-memory stage, 5 blocks per SM -- while every tile of the launch is
+ * resident at once in it, else the throughput form -- smaller stage, 7 blocks
+ * per SM), 1 latency form, 2 throughput form.  Process-wide; results do not
+ * depend on it (both forms compute the same thing in the same order), only the
+ * time does.  o3g_get_tile_config returns the setting or O3G_ERR_ARG.
+ */
+O3G_API int32_t o3g_set_tile_config(int32_t size_class, int32_t cfg);
+O3G_API int32_t o3g_get_tile_config(int32_t size_class);
+
+/*
  * Hypothesis validation (the step RANSAC-based global registration spends its
  * time in, Sec. 3.3): for each candidate pose T_h, the correspondence step of
  * o3g_correspondences at T_h over the whole source, then

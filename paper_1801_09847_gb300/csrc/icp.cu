@@ -17,6 +17,7 @@
 //      device.  The next launch reads the new pose.
 // The pose never leaves the device between iterations.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <deque>
 #include <map>
@@ -228,11 +229,22 @@ __device__ void box_search_global(const GridView& g, float cell, float px, float
 // round trips, and stages only cells some thread needs.  Returns false, with
 // nothing changed, when the staged set does not fit: the caller then searches
 // from global memory.  All threads of the block must call this.
-constexpr int kStageCols = 128;  // columns of the bounding box
-constexpr int kStageZ = 15;      // z-cells per column
-constexpr int kStagePts = 1792;  // staged points (28 KB)
+constexpr int kStageZ = 15;  // z-cells per column
 
+// Two stage sizes, one per launch configuration.  Latency: every tile of a
+// launch is resident at once (5 blocks per SM), so a large stage keeps blocks
+// off the slower global search.  Throughput: more tiles than resident blocks,
+// so a smaller stage and register budget buy 7 blocks per SM.
+struct CfgLatency {
+  static constexpr int kPts = 1792, kCols = 128, kMinBlocks = 5;
+};
+struct CfgThroughput {
+  static constexpr int kPts = 1024, kCols = 64, kMinBlocks = 7;
+};
+
+template <class Cfg>
 struct Stage {
+  static constexpr int kStagePts = Cfg::kPts, kStageCols = Cfg::kCols;
   float4 pts[kStagePts];
   uint32_t off[kStageCols][kStageZ + 1];  // global cell_start of each z-cell of each column
   uint32_t base[kStageCols + 1];          // staged position of each column's first staged point
@@ -261,8 +273,10 @@ __device__ __forceinline__ void column_range(const GridView& g, float cell, floa
   zh = min(bz, cell_coord(__fadd_rn(pz, rz), g.inv_cell) - g.lo_z);
 }
 
+template <class St>
 __device__ bool staged_search(const GridView& g, float cell, float px, float py, float pz, float r, bool live,
-                              Nearest& nb, Stage& S) {
+                              Nearest& nb, St& S) {
+  constexpr int kStageCols = St::kStageCols, kStagePts = St::kStagePts;
   const float margin = search_margin(cell, r, px, py, pz);
   const float reach = __fadd_rn(fast_sqrt(__fmul_rn(nb.d2, 1.0001f)), margin);
   int ax = 0, bx = -1, ay = 0, by = -1, az = 0, bz = -1;
@@ -384,50 +398,71 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 
-// Compensated value pairs: the exact value is s + c.
+
+// Rows of per-correspondence factors, one per thread of a tile (kRow floats;
+// slot kOne holds 1, slot kZero 0).  Sum k of the block partial is, over the
+// rows, x y + (the rounding error of x y) + x yl + xl y with (x, xl, y, yl) =
+// the row slots kTerm[kind][k]: a product of two factors for the normal
+// equations (J_a J_b, J_a r, r^2; the lows point at zeros), a factor times one
+// for plain sums (d2, the match flag), and the exact product of two
+// (high, low) pairs for the point-to-point moments.  Every term therefore
+// enters as an exact (value, error) pair.
+constexpr int kRow = 18, kOne = 16, kZero = 17;
+__constant__ unsigned char kTerm[2][32][4] = {
+    {  // point-to-plane: J0..J5 in slots 0-5, r in 6, d2 in 7, match flag in 8
+     {0, 0, 17, 17}, {0, 1, 17, 17}, {0, 2, 17, 17}, {0, 3, 17, 17}, {0, 4, 17, 17}, {0, 5, 17, 17},
+     {1, 1, 17, 17}, {1, 2, 17, 17}, {1, 3, 17, 17}, {1, 4, 17, 17}, {1, 5, 17, 17},
+     {2, 2, 17, 17}, {2, 3, 17, 17}, {2, 4, 17, 17}, {2, 5, 17, 17},
+     {3, 3, 17, 17}, {3, 4, 17, 17}, {3, 5, 17, 17},
+     {4, 4, 17, 17}, {4, 5, 17, 17},
+     {5, 5, 17, 17},
+     {0, 6, 17, 17}, {1, 6, 17, 17}, {2, 6, 17, 17}, {3, 6, 17, 17}, {4, 6, 17, 17}, {5, 6, 17, 17},
+     {6, 6, 17, 17}, {7, 16, 17, 17}, {8, 16, 17, 17}, {17, 17, 17, 17}, {17, 17, 17, 17}},
+    {  // point-to-point: a high 0-2, a low 3-5, b high 6-8, b low 9-11, |a|^2 12, |b|^2 13, d2 14, flag 15
+     {0, 16, 3, 17}, {1, 16, 4, 17}, {2, 16, 5, 17}, {6, 16, 9, 17}, {7, 16, 10, 17}, {8, 16, 11, 17},
+     {0, 6, 3, 9}, {0, 7, 3, 10}, {0, 8, 3, 11},
+     {1, 6, 4, 9}, {1, 7, 4, 10}, {1, 8, 4, 11},
+     {2, 6, 5, 9}, {2, 7, 5, 10}, {2, 8, 5, 11},
+     {12, 16, 17, 17}, {13, 16, 17, 17},
+     {17, 17, 17, 17}, {17, 17, 17, 17}, {17, 17, 17, 17}, {17, 17, 17, 17}, {17, 17, 17, 17},
+     {17, 17, 17, 17}, {17, 17, 17, 17}, {17, 17, 17, 17}, {17, 17, 17, 17}, {17, 17, 17, 17},
+     {17, 17, 17, 17}, {14, 16, 17, 17}, {15, 16, 17, 17}, {17, 17, 17, 17}, {17, 17, 17, 17}}};
+
+// Compensated pair arithmetic: the exact value is s + c.
 __device__ __forceinline__ void add_pair(float& s, float& c, float s2, float c2) {
   float e;
   two_sum(s, s2, s, e);
   c = c + c2 + e;
 }
 
-// Block reduction of 32 compensated values per thread (29 sums, |C| as a float
-// count below 2^24 per block, two zeros) into one float64 partial per block.
-// Within a warp, a butterfly reduce-scatter: at each of 5 steps every lane keeps
-// half of its values, sends the other half to its partner and adds what it
-// receives, so lane j ends with the warp total of value j after 31 exchanges
-// (instead of 32 x 5 for a tree per value).  Warps are then combined in order.
-// Every step is a fixed sequence, so the result does not depend on timing.
-__device__ void block_reduce_store(float (&v)[32], float (&c)[32], double* __restrict__ out) {
-  __shared__ float ws[kThreads / 32][32];
-  __shared__ float wc[kThreads / 32][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int half = 16; half >= 1; half >>= 1) {
-    const bool upper = (lane & half) != 0;
-#pragma unroll
-    for (int j = 0; j < half; ++j) {
-      const float send_s = upper ? v[j] : v[j + half];
-      const float send_c = upper ? c[j] : c[j + half];
-      const float keep_s = upper ? v[j + half] : v[j];
-      const float keep_c = upper ? c[j + half] : c[j];
-      const float rs = __shfl_xor_sync(0xffffffffu, send_s, half);
-      const float rc = __shfl_xor_sync(0xffffffffu, send_c, half);
-      float s = keep_s, cc = keep_c;
-      add_pair(s, cc, rs, rc);
-      v[j] = s;
-      c[j] = cc;
-    }
+// Block partial of the 32 sums from the tile's rows.  Thread t forms sum
+// t % 32 over rows 32 (t / 32) .. 32 (t / 32) + 31 in order, as a compensated
+// float32 pair; the four quarters are then added in order and the pair
+// rounded to float64.  A fixed sequence, so the result does not depend on
+// timing; only a few registers per thread.
+__device__ void block_reduce_rows(const float* __restrict__ rows, int kind, double* __restrict__ out) {
+  static_assert(kThreads == 128, "four quarters of 32 rows");
+  __shared__ float qs[4][32], qc[4][32];
+  const int k = threadIdx.x & 31, quarter = threadIdx.x >> 5;
+  const uchar4 ix = *reinterpret_cast<const uchar4*>(kTerm[kind][k]);
+  float s = 0.f, c = 0.f;
+  const float* r = rows + quarter * 32 * kRow;
+#pragma unroll 4
+  for (int j = 0; j < 32; ++j, r += kRow) {
+    const float x = r[ix.x], y = r[ix.y], xl = r[ix.z], yl = r[ix.w];
+    const float hi = __fmul_rn(x, y);
+    const float lo = fmaf(x, y, -hi) + fmaf(x, yl, xl * y);
+    float e;
+    two_sum(s, hi, s, e);
+    c += lo + e;
   }
-  // lane j holds the warp total of value j (bits of j select the kept halves)
-  ws[warp][lane] = v[0];
-  wc[warp][lane] = c[0];
+  qs[quarter][k] = s;
+  qc[quarter][k] = c;
   __syncthreads();
-  const int t = threadIdx.x;
-  if (t < kPartial) {
-    float s = ws[0][t], cc = wc[0][t];
-    for (int w = 1; w < kThreads / 32; ++w) add_pair(s, cc, ws[w][t], wc[w][t]);
-    out[t] = static_cast<double>(s) + static_cast<double>(cc);
+  if (threadIdx.x < kPartial) {
+    float ts = qs[0][k], tc = qc[0][k];
+    for (int q = 1; q < 4; ++q) add_pair(ts, tc, qs[q][k], qc[q][k]);
+    out[k] = static_cast<double>(ts) + static_cast<double>(tc);
   }
 }
 
@@ -889,42 +924,10 @@ struct PairDesc {
   float* d2_out;
 };
 
-// Point-to-point terms of one correspondence, about the reference point c =
+// Point-to-point terms of one correspondence about the reference point c =
 // P.ctr (near the clouds, so the moments do not cancel): a = p - c, b = q - c,
-// a b^T (row-major), |a|^2, |b|^2, d2 and 1, in the slots solve_update_p2p reads.
-// The float32 form carries every term as an exact pair v + e: a and b by TwoSum,
-// each product by TwoProduct (the FMA gives the rounding error of a*b) plus the
-// cross terms of the low parts, so the compensated block sums see the exact
-// moments up to 2^-48 relative.  |a|^2 and |b|^2 only scale the degeneracy test
-// and stay plain float32.
-__device__ __forceinline__ void p2p_terms(const PairDesc& P, float3 p, float4 q, float d2, float (&v)[32],
-                                          float (&e)[32]) {
-  float ah[3], al[3], bh[3], bl[3];
-  const float pv[3] = {p.x, p.y, p.z}, qv[3] = {q.x, q.y, q.z};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    two_sum(pv[k], -P.ctr[k], ah[k], al[k]);
-    two_sum(qv[k], -P.ctr[k], bh[k], bl[k]);
-    v[k] = ah[k];
-    e[k] = al[k];
-    v[3 + k] = bh[k];
-    e[3 + k] = bl[k];
-  }
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const float hh = __fmul_rn(ah[i], bh[j]);
-      v[6 + 3 * i + j] = hh;
-      e[6 + 3 * i + j] = fmaf(ah[i], bl[j], fmaf(al[i], bh[j], fmaf(ah[i], bh[j], -hh)));
-    }
-  v[15] = ah[0] * ah[0] + ah[1] * ah[1] + ah[2] * ah[2];
-  v[16] = bh[0] * bh[0] + bh[1] * bh[1] + bh[2] * bh[2];
-  v[28] = d2;
-  v[29] = 1.f;
-}
-
-// The all-float64 form: a and b are exact in float64, the products round once.
+// a b^T (row-major), |a|^2, |b|^2, d2 and 1, in the slots solve_update_p2p
+// reads.  All float64: a and b are exact, the products round once.
 __device__ __forceinline__ void p2p_terms(const PairDesc& P, float3 p, float4 q, float d2, double (&v)[32]) {
   const double a[3] = {static_cast<double>(p.x) - P.ctr[0], static_cast<double>(p.y) - P.ctr[1],
                        static_cast<double>(p.z) - P.ctr[2]};
@@ -949,8 +952,8 @@ __device__ __forceinline__ void p2p_terms(const PairDesc& P, float3 p, float4 q,
 // mode kIterate: skipped once the pair is done; the other modes always run.
 // kCorrOnly writes corr/d2 and no sums.  The last tile of the pair to finish
 // performs the pair's solve and update (see finish).  Block-uniform control flow.
-template <bool F64>
-__device__ void icp_tile(const PairDesc& P, int j, int mode, Stage& stage) {
+template <bool F64, class St>
+__device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
   if (mode == kIterate && P.st->done) return;
   float R[9], t[3];
 #pragma unroll
@@ -1017,35 +1020,52 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, Stage& stage) {
     }
     block_reduce_store_f64(v, partial);
   } else {
-    float v[32], c[32];
+    // per-correspondence factors as one row per thread in shared memory (the
+    // staged points are no longer needed), then the transposed reduction
+    __syncthreads();  // every thread has finished reading the staged points
+    float* rows = reinterpret_cast<float*>(stage.pts);
+    float* row = rows + threadIdx.x * kRow;
 #pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = c[k] = 0.f;
-    if (bp >= 0 && P.kind == kPointToPoint) {
-      p2p_terms(P, p, P.g.pts[bp], bd2, v, c);
-    } else if (bp >= 0) {
+    for (int k = 0; k < kRow; ++k) row[k] = 0.f;
+    row[kOne] = 1.f;
+    if (bp >= 0) {
       const float4 q = P.g.pts[bp];
-      const float4 n = P.g.nrm[bp];
-      const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
-      const float res = dx * n.x + dy * n.y + dz * n.z;
-      float J[6];
-      J[0] = p.y * n.z - p.z * n.y;
-      J[1] = p.z * n.x - p.x * n.z;
-      J[2] = p.x * n.y - p.y * n.x;
-      J[3] = n.x;
-      J[4] = n.y;
-      J[5] = n.z;
-      int k = 0;
+      if (P.kind == kPointToPoint) {
+        // a = p - c and b = q - c as exact pairs (c = P.ctr, near the clouds)
+        const float pv[3] = {p.x, p.y, p.z}, qv[3] = {q.x, q.y, q.z};
+        float aa = 0.f, bb = 0.f;
 #pragma unroll
-      for (int a = 0; a < 6; ++a)
-#pragma unroll
-        for (int b = a; b < 6; ++b) v[k++] = J[a] * J[b];
-#pragma unroll
-      for (int a = 0; a < 6; ++a) v[21 + a] = J[a] * res;
-      v[27] = res * res;
-      v[28] = bd2;
-      v[29] = 1.f;
+        for (int k = 0; k < 3; ++k) {
+          float ah, al, bh, bl;
+          two_sum(pv[k], -P.ctr[k], ah, al);
+          two_sum(qv[k], -P.ctr[k], bh, bl);
+          row[k] = ah;
+          row[3 + k] = al;
+          row[6 + k] = bh;
+          row[9 + k] = bl;
+          aa += ah * ah;
+          bb += bh * bh;
+        }
+        row[12] = aa;
+        row[13] = bb;
+        row[14] = bd2;
+        row[15] = 1.f;
+      } else {
+        const float4 n = P.g.nrm[bp];
+        const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+        row[0] = p.y * n.z - p.z * n.y;
+        row[1] = p.z * n.x - p.x * n.z;
+        row[2] = p.x * n.y - p.y * n.x;
+        row[3] = n.x;
+        row[4] = n.y;
+        row[5] = n.z;
+        row[6] = dx * n.x + dy * n.y + dz * n.z;
+        row[7] = bd2;
+        row[8] = 1.f;
+      }
     }
-    block_reduce_store(v, c, partial);
+    __syncthreads();
+    block_reduce_rows(rows, P.kind, partial);
   }
   // The last block of each group of kGroup blocks sums the group (float64, block
   // order); the last group to finish sums the groups and finishes the launch.
@@ -1079,12 +1099,13 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, Stage& stage) {
 // `one` owns every tile.  The pair of a tile comes from tile_pair.  Tiles of
 // different pairs are independent; each pair's partial sums sit in fixed per-tile
 // slots, so every pair's result is the same alone and in any batch.
-// F64 selects the all-float64 per-correspondence arithmetic (precision study).
-template <bool F64>
-__global__ void __launch_bounds__(kThreads, 5) k_icp_iter(PairDesc one, const PairDesc* __restrict__ pairs,
-                                                       const int* __restrict__ tile_pair,
-                                                       const int* __restrict__ ntiles_total, int mode) {
-  __shared__ Stage stage;
+// F64 selects the all-float64 per-correspondence arithmetic (precision study);
+// Cfg the stage size and the blocks per SM the registers are budgeted for.
+template <bool F64, class Cfg>
+__global__ void __launch_bounds__(kThreads, Cfg::kMinBlocks) k_icp_iter(PairDesc one, const PairDesc* __restrict__ pairs,
+                                                                     const int* __restrict__ tile_pair,
+                                                                     const int* __restrict__ ntiles_total, int mode) {
+  __shared__ Stage<Cfg> stage;
   __shared__ PairDesc P;
   const int n = pairs ? *ntiles_total : one.ntiles;
   for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
@@ -1095,21 +1116,58 @@ __global__ void __launch_bounds__(kThreads, 5) k_icp_iter(PairDesc one, const Pa
   }
 }
 
-// Blocks of the persistent iteration kernel: every tile at once when they fit
-// on the GPU together, else as many as are resident (they loop over tiles).
-template <bool F64 = false>
-int persistent_blocks(int ntiles) {
+// Blocks of one configuration of the persistent iteration kernel that are
+// resident on the GPU together.
+template <bool F64, class Cfg>
+int resident_blocks() {
   static int resident = 0;
   if (resident == 0) {
     int dev = 0, sms = kNumSMs, per_sm = 1;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_icp_iter<F64>, kThreads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_icp_iter<F64, Cfg>, kThreads, 0) != cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
     (void)cudaGetLastError();
     resident = sms * per_sm;
   }
-  return ntiles < resident ? (ntiles < 1 ? 1 : ntiles) : resident;
+  return resident;
+}
+
+// Grid of a persistent launch: every tile at once when they fit on the GPU
+// together, else as many blocks as are resident (they loop over tiles).
+inline int grid_for(int ntiles, int resident) { return ntiles < resident ? (ntiles < 1 ? 1 : ntiles) : resident; }
+
+// Launch configuration per size class, class = floor(log2(tiles of the
+// launch)): 0 automatic (the latency form while every tile of the launch is
+// resident at once in it, else the throughput form), 1 latency, 2 throughput.
+std::atomic<int> g_tile_cfg[32];
+
+inline int size_class(int ntiles) {
+  int c = 0;
+  while (c < 31 && (2LL << c) <= ntiles) ++c;
+  return c;
+}
+
+bool throughput_form(int ntiles) {
+  const int pin = g_tile_cfg[size_class(ntiles)].load(std::memory_order_relaxed);
+  if (pin == 1) return false;
+  if (pin == 2) return true;
+  return ntiles > resident_blocks<false, CfgLatency>();
+}
+
+// One launch of the iteration kernel over `ntiles` work items on stream s.
+void launch_iter(bool f64, int ntiles, const PairDesc& one, const PairDesc* pairs, const int* tile_pair,
+                 const int* d_ntiles, int mode, cudaStream_t s) {
+  if (f64) {
+    k_icp_iter<true, CfgLatency><<<grid_for(ntiles, resident_blocks<true, CfgLatency>()), kThreads, 0, s>>>(
+        one, pairs, tile_pair, d_ntiles, mode);
+  } else if (throughput_form(ntiles)) {
+    k_icp_iter<false, CfgThroughput><<<grid_for(ntiles, resident_blocks<false, CfgThroughput>()), kThreads, 0, s>>>(
+        one, pairs, tile_pair, d_ntiles, mode);
+  } else {
+    k_icp_iter<false, CfgLatency><<<grid_for(ntiles, resident_blocks<false, CfgLatency>()), kThreads, 0, s>>>(
+        one, pairs, tile_pair, d_ntiles, mode);
+  }
 }
 
 inline int iter_blocks(int64_t ns) {
@@ -1186,8 +1244,7 @@ struct Work {
     P.hints = (mode == kIterate || mode == kEvaluate) ? hints.as<int32_t>() : nullptr;
     P.corr_out = corr;
     P.d2_out = d2;
-    if (f64) k_icp_iter<true><<<persistent_blocks<true>(nblk), kThreads, 0, s>>>(P, nullptr, nullptr, nullptr, mode);
-    else k_icp_iter<false><<<persistent_blocks<false>(nblk), kThreads, 0, s>>>(P, nullptr, nullptr, nullptr, mode);
+    launch_iter(f64, nblk, P, nullptr, nullptr, nullptr, mode, s);
     count_launch();
     return O3G_OK;
   }
@@ -1492,7 +1549,7 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const 
     P.hints = nullptr;
     P.corr_out = nullptr;
     P.d2_out = nullptr;
-    k_icp_iter<false><<<persistent_blocks(nblk), kThreads, 0, s>>>(P, nullptr, nullptr, nullptr, mode);
+    launch_iter(false, nblk, P, nullptr, nullptr, nullptr, mode, s);
     count_launch();
   }
   O3G_TRY(cudaGetLastError());
@@ -1549,12 +1606,10 @@ cudaError_t graph_stream(cudaStream_t* out) {
 // through a captured CUDA graph when capture works, else directly.
 int32_t run_iterations(const PairDesc* descs, const int* tile_pair, const int* d_ntiles, int ntiles, int max_iter,
                        double eps, cudaStream_t s) {
-  const int blocks = persistent_blocks(ntiles);
   PairDesc dummy{};
   auto enqueue = [&](cudaStream_t q) {
     for (int it = 0; it <= max_iter; ++it)
-      k_icp_iter<false><<<blocks, kThreads, 0, q>>>(dummy, descs, tile_pair, d_ntiles,
-                                                    it < max_iter ? kIterate : kEvaluate);
+      launch_iter(false, ntiles, dummy, descs, tile_pair, d_ntiles, it < max_iter ? kIterate : kEvaluate, q);
   };
   cudaStream_t cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -1877,8 +1932,8 @@ int32_t launch_slots(o3g_server* sv, const std::vector<int>& ks, int mode) {
   O3G_TRY(cudaMemcpyAsync(sv->descs, d.data(), sizeof(PairDesc) * d.size(), cudaMemcpyHostToDevice, s));
   O3G_TRY(cudaMemcpyAsync(sv->tiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice, s));
   PairDesc dummy{};
-  k_icp_iter<false><<<persistent_blocks(static_cast<int>(t0)), kThreads, 0, s>>>(
-      dummy, static_cast<const PairDesc*>(sv->descs), sv->tiles, sv->tiles + t0, mode);
+  launch_iter(false, static_cast<int>(t0), dummy, static_cast<const PairDesc*>(sv->descs), sv->tiles, sv->tiles + t0,
+              mode, s);
   count_launch();
   O3G_TRY(cudaGetLastError());
   return O3G_OK;
@@ -2114,11 +2169,12 @@ __global__ void k_pose_round(const double* __restrict__ poses, int n, PoseF* __r
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 5) k_eval_poses(GridView g, float cell, float r,
+template <class Cfg>
+__global__ void __launch_bounds__(kThreads, Cfg::kMinBlocks) k_eval_poses(GridView g, float cell, float r,
                                                              const float4* __restrict__ src4, int ns, int ntiles,
                                                              const PoseF* __restrict__ poses, int n_poses,
                                                              double* __restrict__ partials) {
-  __shared__ Stage stage;
+  __shared__ Stage<Cfg> stage;
   __shared__ double ws[kThreads / 32][2];
   const int64_t items = static_cast<int64_t>(ntiles) * n_poses;
   const float r2 = __fmul_rn(r, r);
@@ -2183,18 +2239,19 @@ __global__ void k_eval_sum(const double* __restrict__ partials, int ntiles, int 
   }
 }
 
-int eval_blocks(int64_t items) {
+template <class Cfg>
+int eval_resident() {
   static int resident = 0;
   if (resident == 0) {
     int dev = 0, sms = kNumSMs, per_sm = 1;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_poses, kThreads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_poses<Cfg>, kThreads, 0) != cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
     (void)cudaGetLastError();
     resident = sms * per_sm;
   }
-  return items < resident ? static_cast<int>(items < 1 ? 1 : items) : resident;
+  return resident;
 }
 
 }  // namespace
@@ -2231,9 +2288,15 @@ extern "C" int32_t o3g_evaluate_poses(const o3g_grid* g, const float* d_src, int
   {
     TimedRegion tr(O3G_KERNEL_EVAL, s);
     k_pose_round<<<(n_poses + 127) / 128, 128, 0, s>>>(d_poses.as<double>(), n_poses, d_posef.as<PoseF>());
-    k_eval_poses<<<eval_blocks(items), kThreads, 0, s>>>(g->view(), g->cell, static_cast<float>(max_corr_dist),
-                                                         src.pts, static_cast<int>(ns), ntiles, d_posef.as<PoseF>(),
-                                                         n_poses, part.as<double>());
+    const int it = static_cast<int>(std::min<int64_t>(items, 0x7fffffff));
+    if (throughput_form(it))
+      k_eval_poses<CfgThroughput><<<grid_for(it, eval_resident<CfgThroughput>()), kThreads, 0, s>>>(
+          g->view(), g->cell, static_cast<float>(max_corr_dist), src.pts, static_cast<int>(ns), ntiles,
+          d_posef.as<PoseF>(), n_poses, part.as<double>());
+    else
+      k_eval_poses<CfgLatency><<<grid_for(it, eval_resident<CfgLatency>()), kThreads, 0, s>>>(
+          g->view(), g->cell, static_cast<float>(max_corr_dist), src.pts, static_cast<int>(ns), ntiles,
+          d_posef.as<PoseF>(), n_poses, part.as<double>());
     k_eval_sum<<<(n_poses + 3) / 4, 128, 0, s>>>(part.as<double>(), ntiles, n_poses, static_cast<int>(ns),
                                                  out.as<double>());
     count_launch(3);
@@ -2254,4 +2317,18 @@ extern "C" int32_t o3g_evaluate_poses(const o3g_grid* g, const float* d_src, int
     if (out_inliers) out_inliers[k] = static_cast<int64_t>(h[3 * k + 2]);
   }
   return O3G_OK;
+}
+
+extern "C" int32_t o3g_set_tile_config(int32_t size_class, int32_t cfg) {
+  if (size_class < 0 || size_class > 31 || cfg < 0 || cfg > 2) {
+    o3g::set_error("o3g_set_tile_config: size class %d or configuration %d out of range", size_class, cfg);
+    return O3G_ERR_ARG;
+  }
+  o3g::g_tile_cfg[size_class].store(cfg, std::memory_order_relaxed);
+  return O3G_OK;
+}
+
+extern "C" int32_t o3g_get_tile_config(int32_t size_class) {
+  if (size_class < 0 || size_class > 31) return O3G_ERR_ARG;
+  return o3g::g_tile_cfg[size_class].load(std::memory_order_relaxed);
 }

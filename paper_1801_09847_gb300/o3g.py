@@ -53,6 +53,8 @@ _SIGNATURES = {
     "o3g_correspondences": ([_vp, _vp, _i64, _i32, _f64p, _f32, _vp, _vp, _vp], _i32),
     "o3g_normal_equations": ([_vp, _vp, _i64, _i32, _f64p, _f32, _f64p, _f64p, _f64p, _vp], _i32),
     "o3g_normal_equations_ex": ([_vp, _vp, _i64, _i32, _f64p, _f32, _i32, _f64p, _f64p, _f64p, _vp], _i32),
+    "o3g_set_tile_config": ([_i32, _i32], _i32),
+    "o3g_get_tile_config": ([_i32], _i32),
     "o3g_evaluate_poses": ([_vp, _vp, _i64, _i32, _i32, _f64p, _f64, _f64p, _f64p,
                             ctypes.POINTER(ctypes.c_int64), _vp], _i32),
     "o3g_voxel_down_sample": ([_vp, _i64, _i32, _f32, _vp, _vp, ctypes.POINTER(ctypes.c_int64), _vp], _i32),
@@ -297,6 +299,23 @@ def icp_point_to_plane_grid(grid: Grid, src, init_T, max_corr_dist: float, max_i
                                                   ctypes.byref(rmse), ctypes.byref(iters), _stream(stream))
     st = _check(st, "o3g_icp_point_to_plane_grid")
     return _result(st, T, fit, rmse, iters)
+
+
+TILE_AUTO, TILE_LATENCY, TILE_THROUGHPUT = 0, 1, 2
+
+
+def size_class(tiles: int) -> int:
+    """floor(log2(tiles)) clamped to 0..31: the index o3g_set_tile_config uses."""
+    return max(0, min(31, int(tiles).bit_length() - 1))
+
+
+def set_tile_config(size_class: int, cfg: int) -> None:
+    """Pins the iteration kernel's launch form for one size class (TILE_AUTO / TILE_LATENCY / TILE_THROUGHPUT)."""
+    _check(lib().o3g_set_tile_config(int(size_class), int(cfg)), "o3g_set_tile_config")
+
+
+def get_tile_config(size_class: int) -> int:
+    return _check(lib().o3g_get_tile_config(int(size_class)), "o3g_get_tile_config")
 
 
 def evaluate_poses(grid: Grid, src, poses, max_corr_dist: float, stream=None):

@@ -515,3 +515,26 @@ def test_host_entry_with_gpu_normals_matches_oracle_pipeline(o3g, room):
     ang, dt = synth.pose_error(res["T"], ref["T"])
     assert ang < 1e-3 and dt < 1e-3, (ang, dt)
     assert res["fitness"] == pytest.approx(ref["fitness"], abs=1e-3)
+
+
+def test_launch_forms_give_identical_results(o3g):
+    """The latency and throughput forms of the iteration kernel differ only in stage size and occupancy: the
+    correspondences are exact either way and the sums run in the same order, so results are bit-identical."""
+    pr = synth.room_frame_pair()
+    nrm = oracle.estimate_normals(pr.tgt, 0.05, 30)
+    grid = o3g.build_grid(cuda(pr.tgt), pr.max_corr_dist * 1.002)
+    grid.set_normals(cuda(nrm))
+    cls = o3g.size_class((len(pr.src) + 127) // 128)
+    out = []
+    try:
+        for cfg in (o3g.TILE_LATENCY, o3g.TILE_THROUGHPUT):
+            o3g.set_tile_config(cls, cfg)
+            assert o3g.get_tile_config(cls) == cfg
+            out.append(o3g.icp_point_to_plane_grid(grid, cuda(pr.src), np.eye(4), pr.max_corr_dist, 10))
+            out.append(o3g.icp_point_to_point_grid(grid, cuda(pr.src), np.eye(4), pr.max_corr_dist, 5))
+    finally:
+        o3g.set_tile_config(cls, o3g.TILE_AUTO)
+    assert np.array_equal(out[0]["T"], out[2]["T"]) and out[0]["rmse"] == out[2]["rmse"]
+    assert np.array_equal(out[1]["T"], out[3]["T"]) and out[1]["fitness"] == out[3]["fitness"]
+    with pytest.raises(o3g.O3GError):
+        o3g.set_tile_config(40, 0)
