@@ -283,6 +283,7 @@ def run_ours(args, ws, rank, local):
 
 # ---------------------------------------------------------- batched workload
 
+FORM_NAMES = {0: "auto", 1: "latency", 2: "throughput"}
 BATCH_WORKLOAD = ("256 sphere-plus-plane pairs, sizes log-uniform in 2k-200k points, independent seeds and "
                   "5 deg / 0.05 m perturbations, analytic target normals; point-to-plane ICP max_corr_dist 0.05, "
                   "30 iterations, all pairs in one batched call (one persistent launch per iteration, "
@@ -300,10 +301,18 @@ def run_batched(args, ws, rank, local):
     dev = torch.device("cuda", local)
     pairs = synth.sphere_plane_batch(args.batch_pairs, 2000, 200000, seed0=1000 + 100000 * rank)
     srcs = [torch.from_numpy(p.src).to(dev) for p in pairs]
+    tgts = [torch.from_numpy(p.tgt).to(dev) for p in pairs]
+    nrms = [torch.from_numpy(p.tgt_nrm).to(dev) for p in pairs]
+    tune = None
+    cell_factor = args.cell_factor
+    if not args.no_autotune:
+        from paper_1801_09847_gb300 import autotune
+        tune = autotune.tune_batch(tgts, nrms, srcs, 0.05)
+        cell_factor = tune["cell_factor"]
     grids = []
-    for p in pairs:
-        g = o3g.build_grid(torch.from_numpy(p.tgt).to(dev), p.max_corr_dist * args.cell_factor)
-        g.set_normals(torch.from_numpy(p.tgt_nrm).to(dev))
+    for t, n in zip(tgts, nrms):
+        g = o3g.build_grid(t, 0.05 * cell_factor)
+        g.set_normals(n)
         grids.append(g)
     n_src = sum(len(p.src) for p in pairs)
     init = [np.eye(4)] * len(pairs)
@@ -357,7 +366,13 @@ def run_batched(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": BATCH_WORKLOAD, "pairs": len(pairs), "n_source_total": n_src, "iterations": iters,
-                   "l2": "flushed (512 MiB write) before every step"},
+                   "l2": "flushed (512 MiB write) before every step", "cell_factor": cell_factor,
+                   "launch_form": FORM_NAMES[o3g.get_tile_config(
+                       o3g.size_class(sum((len(p.src) + 127) // 128 for p in pairs)))]},
+        "autotune": None if tune is None else {
+            "size_class": tune["size_class"], "tiles": tune["tiles"], "cell_factor": tune["cell_factor"],
+            "form": FORM_NAMES[tune["form"]],
+            "ms_per_5_iteration_call": {f"{cf}/{FORM_NAMES[fm]}": ms for (cf, fm), ms in tune["timings_ms"].items()}},
         "pairs_per_s": len(pairs) / (ms_b / 1e3),
         "single_pair_loop": {"ms_per_step": ms_s, "pairs_per_s": len(pairs) / (ms_s / 1e3),
                              "value": n_src * iters / (ms_s / 1e3), "results_bit_identical": same},
@@ -622,6 +637,185 @@ def run_fragment(args, ws, rank, local):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------- the rows after the ICP step
+
+def _timed_steps(fn, steps, flush, stream):
+    """Mean CUDA-event time (ms) of `steps` calls of fn, L2 flushed before each, and the last result."""
+    import torch
+    torch.cuda.synchronize()
+    total, out = 0.0, None
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / steps, out
+
+
+def _line(args, metric, value, unit, ms, workload, extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": workload, "l2": "flushed (512 MiB write) before every step"}}
+    line.update(extra)
+    print(json.dumps(line))
+
+
+def run_extra(args, ws, rank, local):
+    """One line per row beyond the point-to-plane step: point-to-point ICP, voxel downsampling, RANSAC hypothesis
+    validation, batched normals.  Single GPU (these rows are measured, not scaled)."""
+    import torch
+
+    import oracle
+    from paper_1801_09847_gb300 import build, o3g, synth
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    peak, which = peaks()
+    threads = oracle.default_threads()
+    oracle.build()
+    wl = args.workload
+    l0 = o3g.launch_count()
+    if wl == "p2p":
+        pr = synth.room_frame_pair()
+        src, tgt = torch.from_numpy(pr.src).to(dev), torch.from_numpy(pr.tgt).to(dev)
+
+        def step():
+            g = o3g.build_grid(tgt, pr.max_corr_dist * args.cell_factor)
+            res = o3g.icp_point_to_point_grid(g, src, np.eye(4), pr.max_corr_dist, pr.max_iter)
+            g.free()
+            return res
+        for _ in range(args.warmup):
+            step()
+        l0 = o3g.launch_count()
+        ms, res = _timed_steps(step, args.steps, flush, stream)
+        launches = o3g.launch_count() - l0
+        o3g.timing_enable(True)
+        o3g.timing_read(o3g.KERNEL_ICP_CORR, reset=True)
+        _timed_steps(step, 3, flush, stream)
+        o3g.timing_enable(False)
+        k_ms, k_n = o3g.timing_read(o3g.KERNEL_ICP_CORR, reset=True)
+        ns = len(pr.src)
+        alg = ns * (12.0 + 12.0 * res["fitness"])
+        avg_s = k_ms / max(k_n, 1) / 1e3
+        g_sample = synth.rng(99)
+        idx = np.sort(g_sample.choice(ns, 8192, replace=False))
+        t0 = time.perf_counter()
+        ref = oracle.icp_point_to_point(np.ascontiguousarray(pr.src[idx]), pr.tgt, np.eye(4), pr.max_corr_dist,
+                                        pr.max_iter, threads=threads)
+        t_ora = time.perf_counter() - t0
+        _line(args, "ICP point-pairs/s per iteration (point-to-point)", ns * res["iters"] / (ms / 1e3), UNIT, ms,
+              "RGB-D frame pair (as the headline line), point-to-point ICP (Horn's closed form), max_corr_dist 0.05, "
+              "30 iterations; step = grid build + ICP + evaluation",
+              {"gpu_launches": launches,
+               "roofline": {"bound": "hbm", "achieved": alg / avg_s / 1e9, "peak": peak, "unit": "GB/s",
+                            "frac": alg / avg_s / 1e9 / peak, "traffic": None, "kernel": "k_icp_iter",
+                            "peak_source": which, "avg_launch_us": avg_s * 1e6,
+                            "algorithmic_bytes_per_launch": alg},
+               "result": {"fitness": res["fitness"], "rmse": res["rmse"], "status": res["status"]},
+               "cpu_baseline": {"value": len(idx) * ref["iters"] / t_ora, "unit": UNIT, "cores": threads,
+                                "kind": "oracle", "sample": f"oracle point-to-point ICP on a seeded {len(idx)}-point "
+                                                            f"source sample, {ref['iters']} iterations"}})
+    elif wl == "voxel":
+        g = synth.rng(2)
+        room = synth.make_room(g)
+        raw = synth.back_project(synth.depth_frame(room, np.eye(4), g)).astype(np.float32)
+        pts = torch.from_numpy(raw).to(dev)
+        for _ in range(args.warmup):
+            o3g.voxel_down_sample(pts, 0.01)
+        l0 = o3g.launch_count()
+        ms, out = _timed_steps(lambda: o3g.voxel_down_sample(pts, 0.01), args.steps, flush, stream)
+        launches = o3g.launch_count() - l0
+        n, m = len(raw), int(out.shape[0])
+        alg = 12.0 * n + 12.0 * m
+        t0 = time.perf_counter()
+        c_ref, _ = oracle.voxel_down_sample(raw, 0.01)
+        t_ora = time.perf_counter() - t0
+        same = bool(np.array_equal(out.cpu().numpy(), c_ref))
+        _line(args, "voxel downsampling input points/s", n / (ms / 1e3), "points/s", ms,
+              f"raw 640x480 ray-cast RGB-D frame ({n} points) thinned at 0.01 m ({m} voxels)",
+              {"gpu_launches": launches,
+               "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                            "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": None,
+                            "kernel": "whole o3g_voxel_down_sample call (coordinates, radix sort, heads, means)",
+                            "peak_source": which, "algorithmic_bytes_per_call": alg},
+               "result": {"voxels": m, "bit_identical_to_oracle": same},
+               "cpu_baseline": {"value": n / t_ora, "unit": "points/s", "cores": 1, "kind": "oracle",
+                                "sample": "oracle voxel downsampling of the whole frame (single thread)"}})
+    elif wl == "ransac":
+        pr = synth.room_frame_pair()
+        src, tgt = torch.from_numpy(pr.src).to(dev), torch.from_numpy(pr.tgt).to(dev)
+        grid = o3g.build_grid(tgt, pr.max_corr_dist * args.cell_factor)
+        gh = synth.rng(140)
+        poses = [pr.T_gt] + [synth.perturbation(gh, float(gh.uniform(0.5, 60)), float(gh.uniform(0.005, 0.5)))
+                             @ pr.T_gt for _ in range(args.hypotheses - 1)]
+        for _ in range(args.warmup):
+            o3g.evaluate_poses(grid, src, poses, pr.max_corr_dist)
+        l0 = o3g.launch_count()
+        ms, (fit, rmse, cnt) = _timed_steps(lambda: o3g.evaluate_poses(grid, src, poses, pr.max_corr_dist),
+                                            args.steps, flush, stream)
+        launches = o3g.launch_count() - l0
+        ns, H = len(pr.src), len(poses)
+        alg = ns * H * 12.0 + float(np.sum(cnt)) * 12.0
+        sub = poses[:4]
+        t0 = time.perf_counter()
+        f_ref, _, c_ref = oracle.evaluate_poses(pr.src, pr.tgt, sub, pr.max_corr_dist, threads=threads,
+                                                nn_method="grid")
+        t_ora = time.perf_counter() - t0
+        _line(args, "hypothesis validation point evaluations/s", ns * H / (ms / 1e3), "point-evaluations/s", ms,
+              f"RGB-D frame pair, {H} candidate poses (the true one and random 0.5-60 deg / 5-500 mm "
+              f"perturbations of it), fitness + inlier rmse of all {ns} source points per pose, max_corr_dist 0.05",
+              {"gpu_launches": launches, "hypotheses_per_s": H / (ms / 1e3),
+               "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                            "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": None, "kernel": "k_eval_poses",
+                            "peak_source": which, "algorithmic_bytes_per_call": alg},
+               "result": {"best_pose": int(np.argmax(fit)), "best_fitness": float(np.max(fit)),
+                          "counts_equal_oracle_first4": bool(np.array_equal(cnt[:4], c_ref))},
+               "cpu_baseline": {"value": ns * len(sub) / t_ora, "unit": "point-evaluations/s", "cores": threads,
+                                "kind": "oracle", "sample": f"oracle evaluation (exact grid search) of the first "
+                                                            f"{len(sub)} poses on the whole source"}})
+    elif wl == "normals_batch":
+        pairs = synth.sphere_plane_batch(args.batch_pairs, 2000, 200000, seed0=1000)
+        tgts = [torch.from_numpy(p.tgt).to(dev) for p in pairs]
+        grids = [o3g.build_grid(t, 0.1) for t in tgts]
+
+        def batched():
+            o3g.estimate_normals_batch(grids, 0.1, 30)
+
+        def loop():
+            for g in grids:
+                g.estimate_normals(0.1, 30, out=False)
+        for _ in range(args.warmup):
+            batched()
+            loop()
+        l0 = o3g.launch_count()
+        ms, _ = _timed_steps(batched, args.steps, flush, stream)
+        launches = o3g.launch_count() - l0
+        ms_loop, _ = _timed_steps(loop, max(1, args.steps // 2), flush, stream)
+        n = sum(len(p.tgt) for p in pairs)
+        alg = 24.0 * n
+        sample = pairs[0].tgt
+        t0 = time.perf_counter()
+        oracle.estimate_normals(sample, 0.1, 30, threads=threads)
+        t_ora = time.perf_counter() - t0
+        _line(args, "normal estimation points/s (batched)", n / (ms / 1e3), "points/s", ms,
+              f"{len(pairs)} sphere-plus-plane clouds (log-uniform 2k-200k points, {n} in all), hybrid radius 0.1, "
+              f"30 neighbours, all in one launch",
+              {"gpu_launches": launches,
+               "one_launch_per_cloud": {"ms_per_step": ms_loop, "value": n / (ms_loop / 1e3)},
+               "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                            "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": None, "kernel": "k_normals_batch",
+                            "peak_source": which, "algorithmic_bytes_per_call": alg},
+               "cpu_baseline": {"value": len(sample) / t_ora, "unit": "points/s", "cores": threads, "kind": "oracle",
+                                "sample": f"oracle normals (brute force) of the first cloud ({len(sample)} points)"}})
+
+
 # ------------------------------------------------------------ CPU oracle
 
 
@@ -692,15 +886,19 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["rgbd_frame", "batched", "serving", "fragment"], default="rgbd_frame",
+    ap.add_argument("--workload", choices=["rgbd_frame", "batched", "serving", "fragment", "p2p", "voxel", "ransac",
+                                           "normals_batch"], default="rgbd_frame",
                     help="rgbd_frame: the headline single-pair line; batched: 256 uneven pairs per call; "
                          "serving: continuous-batching server under Poisson arrivals; fragment: the 2M-point "
-                         "precision study (float32+compensated vs float64 against the oracle)")
+                         "precision study (float32+compensated vs float64 against the oracle); p2p, voxel, ransac, "
+                         "normals_batch: the rows after the point-to-plane step")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--batch-pairs", type=int, default=256)
+    ap.add_argument("--hypotheses", type=int, default=1000, help="ransac: candidate poses per call")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="batched: skip the cell-size / launch-form tuning")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-sample", type=int, default=2048)
     ap.add_argument("--cell-factor", type=float, default=1.002, help="grid cell = factor x max_corr_dist")
@@ -716,6 +914,9 @@ def main():
         run_serving(args, ws, rank, local)
     elif args.workload == "fragment":
         run_fragment(args, ws, rank, local)
+    elif args.workload in ("p2p", "voxel", "ransac", "normals_batch"):
+        if rank == 0:
+            run_extra(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

@@ -120,6 +120,30 @@ O3G_API int32_t o3g_estimate_normals(o3g_grid* grid, float radius, int32_t max_n
                              float* d_nrm_out, int32_t nrm_stride, void* stream);
 
 /*
+ * Normal estimation for many clouds in one launch (the step before every
+ * registration, Sec. 3.3: both clouds of a pair, or every target of a batch).
+ * Cloud c gets exactly what o3g_estimate_normals(grids[c], radius[c], max_nn,
+ * viewpoints + 3 c, d_out[c], out_strides[c]) would give it.  grids: host
+ * array of n_grids handles; radius: host array; viewpoints: host n_grids x 3
+ * or NULL (origins); d_out: host array of device pointers (entries may be
+ * NULL) or NULL; out_strides: host array or NULL (3).  max_nn > 32 runs one
+ * launch per cloud.  Synchronous.
+ */
+O3G_API int32_t o3g_estimate_normals_batch(int32_t n_grids, o3g_grid* const* grids, const float* radius, int32_t max_nn,
+                                           const float* viewpoints, float* const* d_out, const int32_t* out_strides,
+                                           void* stream);
+
+/*
+ * Hybrid kNN queries against many grids in one launch: query set c (d_qry[c],
+ * nq[c] rows of strides[c] floats) against grids[c] with radius[c], outputs as
+ * o3g_knn_hybrid gives them in d_idx[c], d_d2[c], d_cnt[c].  All arrays are
+ * host arrays of n_grids entries.  Synchronous.
+ */
+O3G_API int32_t o3g_knn_hybrid_batch(int32_t n_grids, const o3g_grid* const* grids, const float* const* d_qry,
+                                     const int64_t* nq, const int32_t* strides, const float* radius, int32_t max_nn,
+                                     int32_t* const* d_idx, float* const* d_d2, int32_t* const* d_cnt, void* stream);
+
+/*
  * Correspondence step of registration_icp at a given pose (Sec. 3.3):
  * p_i = R s_i + t in float32 with R, t rounded to nearest from T and each row
  * evaluated as ((R0 sx + R1 sy) + R2 sz) + t, no fused multiply-add; then the

@@ -11,6 +11,8 @@
 // thread per point with an insertion-sorted list in local memory.
 #include <cmath>
 
+#include <vector>
+
 #include "o3g_internal.cuh"
 
 namespace o3g {
@@ -264,16 +266,14 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-__global__ void __launch_bounds__(kThreads) k_normals_warp(GridView g, const int32_t* __restrict__ pos_of,
-                                                           float radius, int max_nn, float vx, float vy, float vz,
-                                                           float4* __restrict__ nrm_sorted, float* __restrict__ out,
-                                                           int out_stride) {
-  __shared__ uint64_t stage_all[kWarpsPerBlock][64];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int k = blockIdx.x * kWarpsPerBlock + warp;
-  if (k >= g.n) return;
+// Normal of sorted point k of grid g, computed by one whole warp (stage: that
+// warp's 64 staging slots).  Lane 0 stores it.
+__device__ void warp_normal(const GridView& g, const int32_t* __restrict__ pos_of, int k, float radius, int max_nn,
+                            float vx, float vy, float vz, float4* __restrict__ nrm_sorted, float* __restrict__ out,
+                            int out_stride, uint64_t* stage) {
+  const int lane = threadIdx.x & 31;
   const float4 q = g.pts[k];
-  const uint64_t key = warp_knn(g, q.x, q.y, q.z, radius, max_nn, stage_all[warp]);
+  const uint64_t key = warp_knn(g, q.x, q.y, q.z, radius, max_nn, stage);
   const bool have = key != kNoKey;
   const int m = __popc(__ballot_sync(0xffffffffu, have));
   float3 n = make_float3(0.f, 0.f, 1.f);
@@ -315,15 +315,68 @@ __global__ void __launch_bounds__(kThreads) k_normals_warp(GridView g, const int
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_knn_warp(GridView g, const float* __restrict__ qry, int nq, int stride,
-                                                       float radius, int max_nn, int32_t* __restrict__ idx,
-                                                       float* __restrict__ dd, int32_t* __restrict__ cnt) {
+__global__ void __launch_bounds__(kThreads) k_normals_warp(GridView g, const int32_t* __restrict__ pos_of,
+                                                           float radius, int max_nn, float vx, float vy, float vz,
+                                                           float4* __restrict__ nrm_sorted, float* __restrict__ out,
+                                                           int out_stride) {
   __shared__ uint64_t stage_all[kWarpsPerBlock][64];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * kWarpsPerBlock + warp;
-  if (i >= nq) return;
+  const int warp = threadIdx.x >> 5;
+  const int k = blockIdx.x * kWarpsPerBlock + warp;
+  if (k >= g.n) return;
+  warp_normal(g, pos_of, k, radius, max_nn, vx, vy, vz, nrm_sorted, out, out_stride, stage_all[warp]);
+}
+
+// One cloud of a batched normals or kNN launch.
+struct NormalsJob {
+  GridView g;
+  const int32_t* pos_of;
+  float4* nrm_sorted;
+  float* out;        // normals: by original index, or null;  kNN: unused
+  const float* qry;  // kNN: query rows (stride floats each)
+  int32_t* idx;      // kNN outputs
+  float* dd;
+  int32_t* cnt;
+  int n;             // points (normals) or queries (kNN)
+  int stride;        // out stride (normals) or query stride (kNN)
+  float radius, vx, vy, vz;
+};
+
+// Job of global warp w: the last job whose first warp is <= w (binary search
+// over the jobs' first warps, ascending).
+__device__ __forceinline__ int job_of(const int64_t* __restrict__ first, int njobs, int64_t w) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Normals of many clouds in one launch: warp w takes point w - first[j] of
+// job j, so every point gets exactly the computation the one-cloud launch gives it.
+__global__ void __launch_bounds__(kThreads) k_normals_batch(const NormalsJob* __restrict__ jobs,
+                                                            const int64_t* __restrict__ first, int njobs,
+                                                            int64_t total, int max_nn) {
+  __shared__ uint64_t stage_all[kWarpsPerBlock][64];
+  const int warp = threadIdx.x >> 5;
+  const int64_t w = static_cast<int64_t>(blockIdx.x) * kWarpsPerBlock + warp;
+  if (w >= total) return;
+  const int j = job_of(first, njobs, w);
+  const NormalsJob& J = jobs[j];
+  const int k = static_cast<int>(w - first[j]);
+  if (k >= J.n) return;
+  warp_normal(J.g, J.pos_of, k, J.radius, max_nn, J.vx, J.vy, J.vz, J.nrm_sorted, J.out, J.stride,
+              stage_all[warp]);
+}
+
+// Hybrid kNN of query i, computed by one whole warp.
+__device__ void warp_query(const GridView& g, const float* __restrict__ qry, int i, int stride, float radius,
+                           int max_nn, int32_t* __restrict__ idx, float* __restrict__ dd, int32_t* __restrict__ cnt,
+                           uint64_t* stage) {
+  const int lane = threadIdx.x & 31;
   const float* q = qry + static_cast<int64_t>(i) * stride;
-  const uint64_t key = warp_knn(g, q[0], q[1], q[2], radius, max_nn, stage_all[warp]);
+  const uint64_t key = warp_knn(g, q[0], q[1], q[2], radius, max_nn, stage);
   const bool have = key != kNoKey;
   const int m = __popc(__ballot_sync(0xffffffffu, have));
   if (lane < max_nn) {
@@ -331,6 +384,32 @@ __global__ void __launch_bounds__(kThreads) k_knn_warp(GridView g, const float* 
     dd[static_cast<int64_t>(i) * max_nn + lane] = have ? __uint_as_float(static_cast<uint32_t>(key >> 32)) : 0.f;
   }
   if (lane == 0) cnt[i] = m;
+}
+
+__global__ void __launch_bounds__(kThreads) k_knn_warp(GridView g, const float* __restrict__ qry, int nq, int stride,
+                                                       float radius, int max_nn, int32_t* __restrict__ idx,
+                                                       float* __restrict__ dd, int32_t* __restrict__ cnt) {
+  __shared__ uint64_t stage_all[kWarpsPerBlock][64];
+  const int warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * kWarpsPerBlock + warp;
+  if (i >= nq) return;
+  warp_query(g, qry, i, stride, radius, max_nn, idx, dd, cnt, stage_all[warp]);
+}
+
+// Hybrid kNN queries against many grids in one launch (warp w: query
+// w - first[j] of job j).
+__global__ void __launch_bounds__(kThreads) k_knn_batch(const NormalsJob* __restrict__ jobs,
+                                                        const int64_t* __restrict__ first, int njobs, int64_t total,
+                                                        int max_nn) {
+  __shared__ uint64_t stage_all[kWarpsPerBlock][64];
+  const int warp = threadIdx.x >> 5;
+  const int64_t w = static_cast<int64_t>(blockIdx.x) * kWarpsPerBlock + warp;
+  if (w >= total) return;
+  const int j = job_of(first, njobs, w);
+  const NormalsJob& J = jobs[j];
+  const int i = static_cast<int>(w - first[j]);
+  if (i >= J.n) return;
+  warp_query(J.g, J.qry, i, J.stride, J.radius, max_nn, J.idx, J.dd, J.cnt, stage_all[warp]);
 }
 
 template <int KMAX>
@@ -475,4 +554,126 @@ extern "C" int32_t o3g_knn_hybrid(const o3g_grid* g, const float* d_qry, int64_t
                                                           d_idx, d_d2, d_cnt);
   O3G_TRY(cudaGetLastError());
   return O3G_OK;
+}
+
+namespace {
+
+// Launches one batched warp kernel over the jobs (first warp of each job from
+// their sizes), synchronously on s.
+template <class Launch>
+int32_t run_jobs(std::vector<NormalsJob>& jobs, int max_nn, cudaStream_t s, Launch launch) {
+  std::vector<int64_t> first(jobs.size());
+  int64_t total = 0;
+  for (size_t j = 0; j < jobs.size(); ++j) {
+    first[j] = total;
+    total += jobs[j].n;
+  }
+  if (total == 0) return O3G_OK;
+  DevBuf d_jobs(s), d_first(s);
+  O3G_TRY(d_jobs.alloc(sizeof(NormalsJob) * jobs.size()));
+  O3G_TRY(d_first.alloc(sizeof(int64_t) * first.size()));
+  O3G_TRY(cudaMemcpyAsync(d_jobs.p, jobs.data(), sizeof(NormalsJob) * jobs.size(), cudaMemcpyHostToDevice, s));
+  O3G_TRY(cudaMemcpyAsync(d_first.p, first.data(), sizeof(int64_t) * first.size(), cudaMemcpyHostToDevice, s));
+  launch(d_jobs.as<NormalsJob>(), d_first.as<int64_t>(), static_cast<int>(jobs.size()), total,
+         warp_blocks(total));
+  count_launch();
+  O3G_TRY(cudaGetLastError());
+  O3G_TRY(cudaStreamSynchronize(s));
+  return O3G_OK;
+}
+
+}  // namespace
+
+extern "C" int32_t o3g_estimate_normals_batch(int32_t n_grids, o3g_grid* const* grids, const float* radius,
+                                              int32_t max_nn, const float* viewpoints, float* const* d_out,
+                                              const int32_t* out_strides, void* stream) {
+  const char* fn = "o3g_estimate_normals_batch";
+  if (n_grids < 0 || (n_grids > 0 && (!grids || !radius)) || max_nn < 1 || max_nn > O3G_MAX_NN) {
+    set_error("%s: invalid argument", fn);
+    return O3G_ERR_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<NormalsJob> jobs(static_cast<size_t>(n_grids));
+  for (int c = 0; c < n_grids; ++c) {
+    const int stride = out_strides ? out_strides[c] : 3;
+    if (!grids[c] || !(radius[c] >= 0.f) || !std::isfinite(radius[c]) || (d_out && d_out[c] && stride < 3)) {
+      set_error("%s: invalid grid, radius or output stride for cloud %d", fn, c);
+      return O3G_ERR_ARG;
+    }
+    const float* v = viewpoints ? viewpoints + 3 * c : nullptr;
+    if (v && !(std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]))) {
+      set_error("%s: viewpoint %d is not finite", fn, c);
+      return O3G_ERR_NONFINITE;
+    }
+    NormalsJob& J = jobs[c];
+    J = NormalsJob{};
+    J.g = grids[c]->view();
+    J.pos_of = grids[c]->pos_of;
+    J.nrm_sorted = grids[c]->nrm;
+    J.out = d_out ? d_out[c] : nullptr;
+    J.n = static_cast<int>(grids[c]->n);
+    J.stride = stride;
+    J.radius = radius[c];
+    J.vx = v ? v[0] : 0.f;
+    J.vy = v ? v[1] : 0.f;
+    J.vz = v ? v[2] : 0.f;
+  }
+  if (max_nn > 32) {  // the thread-per-point form, one launch per cloud
+    for (int c = 0; c < n_grids; ++c)
+      O3G_TRY_STATUS(estimate_normals_impl(grids[c], radius[c], max_nn, viewpoints ? viewpoints + 3 * c : nullptr,
+                                           jobs[c].out, jobs[c].stride, s));
+    O3G_TRY(cudaStreamSynchronize(s));
+    return O3G_OK;
+  }
+  {
+    TimedRegion tr(O3G_KERNEL_NORMALS, s);
+    O3G_TRY_STATUS(run_jobs(jobs, max_nn, s, [&](const NormalsJob* dj, const int64_t* df, int nj, int64_t total,
+                                                 int blocks) {
+      k_normals_batch<<<blocks, kThreads, 0, s>>>(dj, df, nj, total, max_nn);
+    }));
+  }
+  for (int c = 0; c < n_grids; ++c) grids[c]->has_normals = true;
+  return O3G_OK;
+}
+
+extern "C" int32_t o3g_knn_hybrid_batch(int32_t n_grids, const o3g_grid* const* grids, const float* const* d_qry,
+                                        const int64_t* nq, const int32_t* strides, const float* radius,
+                                        int32_t max_nn, int32_t* const* d_idx, float* const* d_d2,
+                                        int32_t* const* d_cnt, void* stream) {
+  const char* fn = "o3g_knn_hybrid_batch";
+  if (n_grids < 0 || (n_grids > 0 && (!grids || !d_qry || !nq || !strides || !radius || !d_idx || !d_d2 || !d_cnt)) ||
+      max_nn < 1 || max_nn > O3G_MAX_NN) {
+    set_error("%s: invalid argument", fn);
+    return O3G_ERR_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<NormalsJob> jobs(static_cast<size_t>(n_grids));
+  for (int c = 0; c < n_grids; ++c) {
+    if (!grids[c] || nq[c] < 0 || nq[c] > 0x7fffffffLL - kThreads ||
+        (nq[c] > 0 && (!d_qry[c] || !d_idx[c] || !d_d2[c] || !d_cnt[c])) || strides[c] < 3 || !(radius[c] >= 0.f) ||
+        !std::isfinite(radius[c])) {
+      set_error("%s: invalid arguments for query set %d", fn, c);
+      return O3G_ERR_ARG;
+    }
+    NormalsJob& J = jobs[c];
+    J = NormalsJob{};
+    J.g = grids[c]->view();
+    J.qry = d_qry[c];
+    J.idx = d_idx[c];
+    J.dd = d_d2[c];
+    J.cnt = d_cnt[c];
+    J.n = static_cast<int>(nq[c]);
+    J.stride = strides[c];
+    J.radius = radius[c];
+  }
+  if (max_nn > 32) {
+    for (int c = 0; c < n_grids; ++c)
+      O3G_TRY_STATUS(o3g_knn_hybrid(grids[c], d_qry[c], nq[c], strides[c], radius[c], max_nn, d_idx[c], d_d2[c],
+                                    d_cnt[c], stream));
+    O3G_TRY(cudaStreamSynchronize(s));
+    return O3G_OK;
+  }
+  return run_jobs(jobs, max_nn, s, [&](const NormalsJob* dj, const int64_t* df, int nj, int64_t total, int blocks) {
+    k_knn_batch<<<blocks, kThreads, 0, s>>>(dj, df, nj, total, max_nn);
+  });
 }

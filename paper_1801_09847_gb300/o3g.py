@@ -53,6 +53,8 @@ _SIGNATURES = {
     "o3g_correspondences": ([_vp, _vp, _i64, _i32, _f64p, _f32, _vp, _vp, _vp], _i32),
     "o3g_normal_equations": ([_vp, _vp, _i64, _i32, _f64p, _f32, _f64p, _f64p, _f64p, _vp], _i32),
     "o3g_normal_equations_ex": ([_vp, _vp, _i64, _i32, _f64p, _f32, _i32, _f64p, _f64p, _f64p, _vp], _i32),
+    "o3g_estimate_normals_batch": ([_i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp], _i32),
+    "o3g_knn_hybrid_batch": ([_i32, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp], _i32),
     "o3g_set_tile_config": ([_i32, _i32], _i32),
     "o3g_get_tile_config": ([_i32], _i32),
     "o3g_evaluate_poses": ([_vp, _vp, _i64, _i32, _i32, _f64p, _f64, _f64p, _f64p,
@@ -299,6 +301,63 @@ def icp_point_to_plane_grid(grid: Grid, src, init_T, max_corr_dist: float, max_i
                                                   ctypes.byref(rmse), ctypes.byref(iters), _stream(stream))
     st = _check(st, "o3g_icp_point_to_plane_grid")
     return _result(st, T, fit, rmse, iters)
+
+
+def _ptrs(values):
+    arr = (ctypes.c_void_p * max(len(values), 1))()
+    for k, v in enumerate(values):
+        arr[k] = v
+    return arr
+
+
+def estimate_normals_batch(grids, radius, max_nn: int, viewpoints=None, outs=None, stream=None) -> None:
+    """Normals of many clouds in one launch (o3g_estimate_normals_batch); each grid then carries its normals.
+
+    radius: one per grid or a scalar; viewpoints: n x 3 or None (origins); outs: optional list of float32 CUDA
+    tensors (n_c x k, k >= 3, or None entries) that also receive the normals by original index."""
+    n = len(grids)
+    rad = np.ascontiguousarray(np.broadcast_to(np.asarray(radius, np.float32), (n,)))
+    vp = None if viewpoints is None else np.ascontiguousarray(np.asarray(viewpoints, np.float32).reshape(n, 3))
+    handles = _ptrs([g.handle.value for g in grids])
+    out_ptrs, strides = None, None
+    if outs is not None:
+        vals, st = [], np.full(max(n, 1), 3, np.int32)
+        for k, o in enumerate(outs):
+            if o is None:
+                vals.append(None)
+                continue
+            p, m, stride = _cloud(o, f"outs[{k}]")
+            if m != grids[k].info()[0]:
+                raise ValueError(f"outs[{k}] must have one row per point of grids[{k}]")
+            vals.append(p.value)
+            st[k] = stride
+        out_ptrs, strides = _ptrs(vals), st
+    _check(lib().o3g_estimate_normals_batch(n, handles, rad.ctypes.data_as(ctypes.c_void_p), int(max_nn),
+                                            vp.ctypes.data_as(ctypes.c_void_p) if vp is not None else None,
+                                            out_ptrs, strides.ctypes.data_as(ctypes.c_void_p) if strides is not None
+                                            else None, _stream(stream)), "o3g_estimate_normals_batch")
+
+
+def knn_hybrid_batch(grids, queries, radius, max_nn: int, stream=None) -> list:
+    """Hybrid kNN of many query sets against their grids in one launch: [(idx, d2, cnt)] per set."""
+    torch = _torch()
+    n = len(grids)
+    rad = np.ascontiguousarray(np.broadcast_to(np.asarray(radius, np.float32), (n,)))
+    qp, nq, st, outs = [], np.zeros(max(n, 1), np.int64), np.zeros(max(n, 1), np.int32), []
+    for k, q in enumerate(queries):
+        p, m, stride = _cloud(q, f"queries[{k}]")
+        qp.append(p.value)
+        nq[k], st[k] = m, stride
+        outs.append((torch.empty((m, max_nn), dtype=torch.int32, device="cuda"),
+                     torch.empty((m, max_nn), dtype=torch.float32, device="cuda"),
+                     torch.empty((m,), dtype=torch.int32, device="cuda")))
+    _check(lib().o3g_knn_hybrid_batch(n, _ptrs([g.handle.value for g in grids]), _ptrs(qp),
+                                      nq.ctypes.data_as(ctypes.c_void_p), st.ctypes.data_as(ctypes.c_void_p),
+                                      rad.ctypes.data_as(ctypes.c_void_p), int(max_nn),
+                                      _ptrs([o[0].data_ptr() for o in outs]), _ptrs([o[1].data_ptr() for o in outs]),
+                                      _ptrs([o[2].data_ptr() for o in outs]), _stream(stream)),
+           "o3g_knn_hybrid_batch")
+    return outs
 
 
 TILE_AUTO, TILE_LATENCY, TILE_THROUGHPUT = 0, 1, 2

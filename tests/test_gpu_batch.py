@@ -122,3 +122,36 @@ def test_batch_errors(o3g, problems):
                                        [np.eye(4), np.eye(4)], 0.05, 3)
     assert res[0]["status"] == o3g.ERR_NONFINITE and res[1]["status"] >= 0
     assert o3g.icp_point_to_plane_batch([], [], [], 0.05, 3) == []
+
+
+def test_autotune_picks_a_measured_candidate_and_pins_it(o3g, problems):
+    import torch
+    from paper_1801_09847_gb300 import autotune
+    # problem tuples: (grid, src device, T0, r, src, tgt, nrm); every radius here is 0.05
+    assert all(p[3] == 0.05 for p in problems)
+    tgts = [cuda(p[5]) for p in problems]
+    nrms = [cuda(p[6]) for p in problems]
+    srcs = [p[1] for p in problems]
+    cls = o3g.size_class(autotune.batch_tiles(srcs))
+    try:
+        res = autotune.tune_batch(tgts, nrms, srcs, 0.05, iters=2, reps=1, cell_factors=(1.002, 1.5))
+        assert set(res["timings_ms"]) == {(cf, f) for cf in (1.002, 1.5) for f in autotune.DEFAULT_FORMS}
+        assert res["timings_ms"][(res["cell_factor"], res["form"])] == min(res["timings_ms"].values())
+        assert res["size_class"] == cls and o3g.get_tile_config(cls) == res["form"]
+        # tuning changes time only: the tuned batch gives the untuned results
+        grids = []
+        for t, n in zip(tgts, nrms):
+            g = o3g.build_grid(t, 0.05 * res["cell_factor"])
+            g.set_normals(n)
+            grids.append(g)
+        tuned = o3g.icp_point_to_plane_batch(grids, srcs, [np.eye(4)] * len(srcs), 0.05, 10)
+        o3g.set_tile_config(cls, o3g.TILE_AUTO)
+        plain = []
+        for t, n in zip(tgts, nrms):
+            g = o3g.build_grid(t, 0.05 * 1.002)
+            g.set_normals(n)
+            plain.append(g)
+        ref = o3g.icp_point_to_plane_batch(plain, srcs, [np.eye(4)] * len(srcs), 0.05, 10)
+        assert all(np.array_equal(a["T"], b["T"]) for a, b in zip(tuned, ref))
+    finally:
+        o3g.set_tile_config(cls, o3g.TILE_AUTO)
