@@ -408,6 +408,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // (high, low) pairs for the point-to-point moments.  Every term therefore
 // enters as an exact (value, error) pair.
 constexpr int kRow = 18, kOne = 16, kZero = 17;
+static_assert(kOne == 16 && kZero == 17, "kTerm names the one and zero slots by number");
 __constant__ unsigned char kTerm[2][32][4] = {
     {  // point-to-plane: J0..J5 in slots 0-5, r in 6, d2 in 7, match flag in 8
      {0, 0, 17, 17}, {0, 1, 17, 17}, {0, 2, 17, 17}, {0, 3, 17, 17}, {0, 4, 17, 17}, {0, 5, 17, 17},
@@ -1107,6 +1108,13 @@ __global__ void __launch_bounds__(kThreads, Cfg::kMinBlocks) k_icp_iter(PairDesc
                                                                      const int* __restrict__ ntiles_total, int mode) {
   __shared__ Stage<Cfg> stage;
   __shared__ PairDesc P;
+  // Launched as a programmatic dependent of the previous iteration, this grid
+  // may be placed on the GPU before that one ends; everything it reads (the
+  // pose, the hints, the counters) is the previous grid's output, so wait for
+  // its completion here.  Then let the next iteration start placing its blocks.
+  // Both are no-ops for an ordinary launch.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int n = pairs ? *ntiles_total : one.ntiles;
   for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
     if (threadIdx.x == 0) P = pairs ? pairs[tile_pair[tile]] : one;
@@ -1155,19 +1163,39 @@ bool throughput_form(int ntiles) {
   return ntiles > resident_blocks<false, CfgLatency>();
 }
 
-// One launch of the iteration kernel over `ntiles` work items on stream s.
-void launch_iter(bool f64, int ntiles, const PairDesc& one, const PairDesc* pairs, const int* tile_pair,
-                 const int* d_ntiles, int mode, cudaStream_t s) {
-  if (f64) {
-    k_icp_iter<true, CfgLatency><<<grid_for(ntiles, resident_blocks<true, CfgLatency>()), kThreads, 0, s>>>(
-        one, pairs, tile_pair, d_ntiles, mode);
-  } else if (throughput_form(ntiles)) {
-    k_icp_iter<false, CfgThroughput><<<grid_for(ntiles, resident_blocks<false, CfgThroughput>()), kThreads, 0, s>>>(
-        one, pairs, tile_pair, d_ntiles, mode);
-  } else {
-    k_icp_iter<false, CfgLatency><<<grid_for(ntiles, resident_blocks<false, CfgLatency>()), kThreads, 0, s>>>(
-        one, pairs, tile_pair, d_ntiles, mode);
+template <bool F64, class Cfg>
+void launch_form(int ntiles, const PairDesc& one, const PairDesc* pairs, const int* tile_pair, const int* d_ntiles,
+                 int mode, cudaStream_t s, bool dependent) {
+  const int grid = grid_for(ntiles, resident_blocks<F64, Cfg>());
+  if (!dependent) {
+    k_icp_iter<F64, Cfg><<<grid, kThreads, 0, s>>>(one, pairs, tile_pair, d_ntiles, mode);
+    return;
   }
+  // programmatic dependent launch: the grid is placed while the previous
+  // iteration's tail (group sums, solve) still runs, and waits in the kernel
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_icp_iter<F64, Cfg>, one, pairs, tile_pair, d_ntiles, mode) != cudaSuccess) {
+    (void)cudaGetLastError();
+    k_icp_iter<F64, Cfg><<<grid, kThreads, 0, s>>>(one, pairs, tile_pair, d_ntiles, mode);
+  }
+}
+
+// One launch of the iteration kernel over `ntiles` work items on stream s;
+// `dependent`: as a programmatic dependent of the preceding kernel of s.
+void launch_iter(bool f64, int ntiles, const PairDesc& one, const PairDesc* pairs, const int* tile_pair,
+                 const int* d_ntiles, int mode, cudaStream_t s, bool dependent = false) {
+  if (f64) launch_form<true, CfgLatency>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent);
+  else if (throughput_form(ntiles))
+    launch_form<false, CfgThroughput>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent);
+  else launch_form<false, CfgLatency>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent);
 }
 
 inline int iter_blocks(int64_t ns) {
@@ -1221,7 +1249,7 @@ struct Work {
     return O3G_OK;
   }
   int32_t launch(const o3g_grid* g, int ns, float r, double eps, int mode, int32_t* corr, float* d2,
-                 cudaStream_t s, bool f64 = false, int kind = kPointToPlane) {
+                 cudaStream_t s, bool f64 = false, int kind = kPointToPlane, bool dependent = false) {
     double* pp = partials.as<double>();
     PairDesc P;
     P.g = g->view();
@@ -1244,7 +1272,7 @@ struct Work {
     P.hints = (mode == kIterate || mode == kEvaluate) ? hints.as<int32_t>() : nullptr;
     P.corr_out = corr;
     P.d2_out = d2;
-    launch_iter(f64, nblk, P, nullptr, nullptr, nullptr, mode, s);
+    launch_iter(f64, nblk, P, nullptr, nullptr, nullptr, mode, s, dependent);
     count_launch();
     return O3G_OK;
   }
@@ -1282,9 +1310,9 @@ int32_t icp_run(const o3g_grid* g, const float* d_src, int64_t ns, int32_t strid
   const int n = static_cast<int>(ns);
   for (int it = 0; it < max_iter; ++it) {
     TimedRegion tr(O3G_KERNEL_ICP_CORR, s);
-    w.launch(g, n, r, eps, kIterate, nullptr, nullptr, s, f64, kind);
+    w.launch(g, n, r, eps, kIterate, nullptr, nullptr, s, f64, kind, it > 0);
   }
-  w.launch(g, n, r, eps, kEvaluate, nullptr, nullptr, s, f64, kind);
+  w.launch(g, n, r, eps, kEvaluate, nullptr, nullptr, s, f64, kind, max_iter > 0);
   O3G_TRY(cudaGetLastError());
   IcpState h;
   int aux[8];
