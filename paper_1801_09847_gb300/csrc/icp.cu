@@ -255,8 +255,8 @@ struct Stage {
 
 // The z-range [zl, zh] (grid-relative) a query at p must scan in column
 // (x, y) for its current bound, or zl > zh when the column cannot hold a
-// candidate.  The same expression serves the planning and the scan, and the
-// bound only shrinks in between, so the scanned range stays inside the planned one.
+// candidate.  The same expression serves the planning and the scan; the scan
+// clamps its range to the planned one (see staged_search).
 __device__ __forceinline__ void column_range(const GridView& g, float cell, float px, float py, float pz,
                                              float margin, float bound, int x, int y, int az, int bz, int& zl,
                                              int& zh) {
@@ -380,8 +380,15 @@ __device__ bool staged_search(const GridView& g, float cell, float px, float py,
     for (int y = ay; y <= by; ++y) {
       int zl, zh;
       column_range(g, cell, px, py, pz, margin, nb.d2, x, y, az, bz, zl, zh);
-      if (zl > zh) continue;
       const int t = (x - AX) * NCY + (y - AY);
+      // Clamp to the planned range: only its offsets were loaded.  The bound
+      // has only shrunk since planning, but x * rsqrt(x) is not monotone to
+      // the last ulp, so the recomputed range may reach one cell further; the
+      // planned range, from the larger bound with its rounding margin, already
+      // holds every point within the current bound.
+      zl = max(zl, S.zlo[t] + AZ);
+      zh = min(zh, S.zhi[t] + AZ);
+      if (zl > zh) continue;
       const int shift = static_cast<int>(S.base[t]) - static_cast<int>(S.off[t][S.zlo[t]]);
       const uint32_t gb = S.off[t][zl - AZ], ge = S.off[t][zh + 1 - AZ];
       for (uint32_t k = gb; k < ge; ++k) consider(nb, S.pts[static_cast<int>(k) + shift], static_cast<int>(k), px, py, pz);
@@ -1105,9 +1112,11 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
 template <bool F64, class Cfg>
 __global__ void __launch_bounds__(kThreads, Cfg::kMinBlocks) k_icp_iter(PairDesc one, const PairDesc* __restrict__ pairs,
                                                                      const int* __restrict__ tile_pair,
-                                                                     const int* __restrict__ ntiles_total, int mode) {
+                                                                     const int* __restrict__ ntiles_total, int mode,
+                                                                     unsigned* __restrict__ queue, int parity) {
   __shared__ Stage<Cfg> stage;
   __shared__ PairDesc P;
+  __shared__ int s_next;
   // Launched as a programmatic dependent of the previous iteration, this grid
   // may be placed on the GPU before that one ends; everything it reads (the
   // pose, the hints, the counters) is the previous grid's output, so wait for
@@ -1116,11 +1125,21 @@ __global__ void __launch_bounds__(kThreads, Cfg::kMinBlocks) k_icp_iter(PairDesc
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int n = pairs ? *ntiles_total : one.ntiles;
-  for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
+  // Tiles [0, gridDim.x) go to the blocks in order; the rest are claimed one
+  // at a time from queue[parity], so blocks that drew cheap tiles take more
+  // (results do not depend on which block runs a tile: each tile has its own
+  // partial slot).  queue[parity ^ 1] is the counter of the next launch on
+  // this queue; the previous launch, which used it, has finished here.
+  if (queue && blockIdx.x == 0 && threadIdx.x == 0) queue[parity ^ 1] = 0u;
+  int tile = blockIdx.x;
+  while (tile < n) {
     if (threadIdx.x == 0) P = pairs ? pairs[tile_pair[tile]] : one;
     __syncthreads();
     icp_tile<F64>(P, tile - P.tile0, mode, stage);
+    if (threadIdx.x == 0)
+      s_next = queue ? static_cast<int>(gridDim.x + atomicAdd(&queue[parity], 1u)) : tile + static_cast<int>(gridDim.x);
     __syncthreads();
+    tile = s_next;
   }
 }
 
@@ -1163,12 +1182,19 @@ bool throughput_form(int ntiles) {
   return ntiles > resident_blocks<false, CfgLatency>();
 }
 
+// The dynamic tile queue of a sequence of launches: two counters, zero
+// before the first launch; launch k of the sequence passes parity k & 1.
+struct TileQueue {
+  unsigned* counters = nullptr;  // may be null: blocks then stride over tiles statically
+  int parity = 0;
+};
+
 template <bool F64, class Cfg>
 void launch_form(int ntiles, const PairDesc& one, const PairDesc* pairs, const int* tile_pair, const int* d_ntiles,
-                 int mode, cudaStream_t s, bool dependent) {
+                 int mode, cudaStream_t s, bool dependent, TileQueue q) {
   const int grid = grid_for(ntiles, resident_blocks<F64, Cfg>());
   if (!dependent) {
-    k_icp_iter<F64, Cfg><<<grid, kThreads, 0, s>>>(one, pairs, tile_pair, d_ntiles, mode);
+    k_icp_iter<F64, Cfg><<<grid, kThreads, 0, s>>>(one, pairs, tile_pair, d_ntiles, mode, q.counters, q.parity);
     return;
   }
   // programmatic dependent launch: the grid is placed while the previous
@@ -1182,20 +1208,21 @@ void launch_form(int ntiles, const PairDesc& one, const PairDesc* pairs, const i
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, k_icp_iter<F64, Cfg>, one, pairs, tile_pair, d_ntiles, mode) != cudaSuccess) {
+  if (cudaLaunchKernelEx(&cfg, k_icp_iter<F64, Cfg>, one, pairs, tile_pair, d_ntiles, mode, q.counters, q.parity) !=
+      cudaSuccess) {
     (void)cudaGetLastError();
-    k_icp_iter<F64, Cfg><<<grid, kThreads, 0, s>>>(one, pairs, tile_pair, d_ntiles, mode);
+    k_icp_iter<F64, Cfg><<<grid, kThreads, 0, s>>>(one, pairs, tile_pair, d_ntiles, mode, q.counters, q.parity);
   }
 }
 
 // One launch of the iteration kernel over `ntiles` work items on stream s;
 // `dependent`: as a programmatic dependent of the preceding kernel of s.
 void launch_iter(bool f64, int ntiles, const PairDesc& one, const PairDesc* pairs, const int* tile_pair,
-                 const int* d_ntiles, int mode, cudaStream_t s, bool dependent = false) {
-  if (f64) launch_form<true, CfgLatency>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent);
+                 const int* d_ntiles, int mode, cudaStream_t s, bool dependent = false, TileQueue q = TileQueue{}) {
+  if (f64) launch_form<true, CfgLatency>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent, q);
   else if (throughput_form(ntiles))
-    launch_form<false, CfgThroughput>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent);
-  else launch_form<false, CfgLatency>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent);
+    launch_form<false, CfgThroughput>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent, q);
+  else launch_form<false, CfgLatency>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent, q);
 }
 
 inline int iter_blocks(int64_t ns) {
@@ -1232,8 +1259,10 @@ struct Work {
   DevBuf partials;  // nblk block partials, then ngroups group sums
   DevBuf counters;  // ngroups arrival counters
   DevBuf hints;     // per source point: sorted target position of its last match, or -1
+  DevBuf queue;     // the dynamic tile queue (2 counters)
   int nblk = 1, ngroups = 1;
-  explicit Work(cudaStream_t s) : src(s), state(s), partials(s), counters(s), hints(s) {}
+  int launches = 0;  // launches so far (the queue parity)
+  explicit Work(cudaStream_t s) : src(s), state(s), partials(s), counters(s), hints(s), queue(s) {}
   int32_t prepare(const float* d_src, int64_t ns, int32_t stride, float cell, const double* T, cudaStream_t s) {
     O3G_TRY_STATUS(sort_cloud(d_src, ns, stride, s, &src));
     nblk = iter_blocks(ns);
@@ -1242,6 +1271,8 @@ struct Work {
     O3G_TRY(partials.alloc(sizeof(double) * kPartial * (nblk + ngroups)));
     O3G_TRY(counters.alloc(sizeof(unsigned) * ngroups));
     O3G_TRY(cudaMemsetAsync(counters.p, 0, sizeof(unsigned) * ngroups, s));
+    O3G_TRY(queue.alloc(sizeof(unsigned) * 2));
+    O3G_TRY(cudaMemsetAsync(queue.p, 0, sizeof(unsigned) * 2, s));
     O3G_TRY(hints.alloc(sizeof(int32_t) * (ns > 0 ? ns : 1)));
     O3G_TRY(cudaMemsetAsync(hints.p, 0xff, sizeof(int32_t) * (ns > 0 ? ns : 1), s));
     k_init_state<<<1, 32, 0, s>>>(state.as<IcpState>(), to_pose(T));
@@ -1272,7 +1303,9 @@ struct Work {
     P.hints = (mode == kIterate || mode == kEvaluate) ? hints.as<int32_t>() : nullptr;
     P.corr_out = corr;
     P.d2_out = d2;
-    launch_iter(f64, nblk, P, nullptr, nullptr, nullptr, mode, s, dependent);
+    launch_iter(f64, nblk, P, nullptr, nullptr, nullptr, mode, s, dependent,
+                TileQueue{queue.as<unsigned>(), launches & 1});
+    ++launches;
     count_launch();
     return O3G_OK;
   }
@@ -1633,11 +1666,12 @@ cudaError_t graph_stream(cudaStream_t* out) {
 // Launches `iters` iteration steps and one evaluation step of the batch on s,
 // through a captured CUDA graph when capture works, else directly.
 int32_t run_iterations(const PairDesc* descs, const int* tile_pair, const int* d_ntiles, int ntiles, int max_iter,
-                       double eps, cudaStream_t s) {
+                       double eps, unsigned* queue, cudaStream_t s) {
   PairDesc dummy{};
   auto enqueue = [&](cudaStream_t q) {
     for (int it = 0; it <= max_iter; ++it)
-      launch_iter(false, ntiles, dummy, descs, tile_pair, d_ntiles, it < max_iter ? kIterate : kEvaluate, q);
+      launch_iter(false, ntiles, dummy, descs, tile_pair, d_ntiles, it < max_iter ? kIterate : kEvaluate, q, false,
+                  TileQueue{queue, it & 1});
   };
   cudaStream_t cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -1720,7 +1754,7 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   O3G_TRY(d_aux.alloc(sizeof(int) * 8 * n_pairs));
   O3G_TRY(d_states.alloc(sizeof(IcpState) * n_pairs));
   O3G_TRY(d_part.alloc(sizeof(double) * kPartial * (tiles_total + groups_total)));
-  O3G_TRY(d_cnt.alloc(sizeof(unsigned) * groups_total));
+  O3G_TRY(d_cnt.alloc(sizeof(unsigned) * (groups_total + 2)));  // group counters, then the tile queue
   O3G_TRY(d_hints.alloc(sizeof(int32_t) * (total > 0 ? total : 1)));
   O3G_TRY(d_descs.alloc(sizeof(PairDesc) * n_pairs));
   O3G_TRY(d_tiles.alloc(sizeof(int) * (tiles_total + 1)));
@@ -1763,7 +1797,7 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   O3G_TRY(cudaMemcpyAsync(d_descs.p, descs.data(), sizeof(PairDesc) * n_pairs, cudaMemcpyHostToDevice, s));
   O3G_TRY(cudaMemcpyAsync(d_tiles.p, tile_pair.data(), sizeof(int) * (tiles_total + 1), cudaMemcpyHostToDevice, s));
   O3G_TRY(cudaMemcpyAsync(d_poses.p, init_T, sizeof(double) * 16 * n_pairs, cudaMemcpyHostToDevice, s));
-  O3G_TRY(cudaMemsetAsync(d_cnt.p, 0, sizeof(unsigned) * groups_total, s));
+  O3G_TRY(cudaMemsetAsync(d_cnt.p, 0, sizeof(unsigned) * (groups_total + 2), s));
   O3G_TRY(cudaMemsetAsync(d_hints.p, 0xff, sizeof(int32_t) * (total > 0 ? total : 1), s));
   O3G_TRY_STATUS(sort_clouds_batch(reinterpret_cast<const float* const*>(d_ptrs.p), d_strides.as<int32_t>(),
                                    d_off.as<int64_t>(), n_pairs, total, s, d_src4.as<float4>(), d_aux.as<int>()));
@@ -1772,7 +1806,8 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   {
     TimedRegion tr(O3G_KERNEL_ICP_BATCH, s);
     O3G_TRY_STATUS(run_iterations(d_descs.as<PairDesc>(), d_tiles.as<int>(), d_tiles.as<int>() + tiles_total,
-                                  static_cast<int>(tiles_total), max_iter, eps, s));
+                                  static_cast<int>(tiles_total), max_iter, eps, d_cnt.as<unsigned>() + groups_total,
+                                  s));
   }
   std::vector<IcpState> h(n_pairs);
   std::vector<int> aux(8 * n_pairs);
@@ -1845,6 +1880,8 @@ struct o3g_server {
   void* descs = nullptr;    // max_active PairDesc
   int* tiles = nullptr;     // tile table (+1 count), grows
   int64_t tiles_cap = 0;
+  unsigned* queue = nullptr;  // the dynamic tile queue of the server's launches (2 counters)
+  int64_t launches = 0;
   std::map<int64_t, Result> finished;
 };
 
@@ -1961,7 +1998,8 @@ int32_t launch_slots(o3g_server* sv, const std::vector<int>& ks, int mode) {
   O3G_TRY(cudaMemcpyAsync(sv->tiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice, s));
   PairDesc dummy{};
   launch_iter(false, static_cast<int>(t0), dummy, static_cast<const PairDesc*>(sv->descs), sv->tiles, sv->tiles + t0,
-              mode, s);
+              mode, s, false, TileQueue{sv->queue, static_cast<int>(sv->launches & 1)});
+  ++sv->launches;
   count_launch();
   O3G_TRY(cudaGetLastError());
   return O3G_OK;
@@ -1988,8 +2026,12 @@ extern "C" int32_t o3g_server_create(int32_t max_active, int64_t hbm_budget_byte
   sv->slots.resize(max_active);
   cudaError_t e = dmalloc(&sv->states, sizeof(IcpState) * max_active, sv->s);
   if (e == cudaSuccess) e = dmalloc(&sv->descs, sizeof(PairDesc) * max_active, sv->s);
+  if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void**>(&sv->queue), sizeof(unsigned) * 2, sv->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sv->queue, 0, sizeof(unsigned) * 2, sv->s);
   if (e != cudaSuccess) {
     dfree(sv->states, sv->s);
+    dfree(sv->descs, sv->s);
+    dfree(sv->queue, sv->s);
     delete sv;
     return cuda_fail(e, "o3g_server_create");
   }
@@ -2005,6 +2047,7 @@ extern "C" int32_t o3g_server_destroy(o3g_server* sv) {
   dfree(sv->states, sv->s);
   dfree(sv->descs, sv->s);
   dfree(sv->tiles, sv->s);
+  dfree(sv->queue, sv->s);
   (void)cudaStreamSynchronize(sv->s);
   delete sv;
   return O3G_OK;
