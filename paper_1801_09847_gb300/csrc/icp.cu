@@ -107,14 +107,6 @@ __global__ void k_init_states(IcpState* st, const double* __restrict__ poses, in
   }
 }
 
-// Lower bound (with a rounding margin) of |c - x| over the cell slab
-// [(lo + i) * cell, (lo + i + 1) * cell) along one axis.
-__device__ __forceinline__ float slab_gap(float x, int i_abs, float cell, float margin) {
-  const float a = __fmul_rn(static_cast<float>(i_abs), cell);
-  const float b = __fmul_rn(static_cast<float>(i_abs + 1), cell);
-  const float g = fmaxf(fmaxf(a - x, x - b), 0.f);
-  return fmaxf(g - margin, 0.f);
-}
 
 // Scans sorted target positions [beg, end) and keeps the minimum of (d2, original index).
 __device__ __forceinline__ void scan_run(const float4* __restrict__ pts, uint32_t beg, uint32_t end, float px,
@@ -166,10 +158,6 @@ __device__ __forceinline__ void first_bound(const GridView& g, float px, float p
     if (h[k] >= 0) consider(nb, q[k], h[k], px, py, pz);
 }
 
-__device__ __forceinline__ float search_margin(float cell, float r, float px, float py, float pz) {
-  return __fadd_rn(__fmul_rn(__fadd_rn(cell, r), 1e-5f),
-                   __fmul_rn(fmaxf(fmaxf(fabsf(px), fabsf(py)), fabsf(pz)), 4e-6f));
-}
 
 // The rest of the exact search from global memory, given the first bound: the
 // home cell first when there is no bound yet, then every cell that can still

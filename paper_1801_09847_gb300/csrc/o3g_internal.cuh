@@ -95,6 +95,7 @@ struct GridView {
   int lo_x, lo_y, lo_z;      // smallest occupied cell coordinate per axis
   int sx, sy, sz;            // cell span per axis
   float inv_cell;
+  float cell;                // cell edge (inv_cell = 1 / cell, rounded)
   int n;
 };
 
@@ -121,6 +122,22 @@ __device__ __forceinline__ bool column_z(const GridView& g, int col_xy, int& zl,
   zl = max(zl, static_cast<int>(e & 0xffffu));
   zh = min(zh, static_cast<int>(e >> 16));
   return zl <= zh;
+}
+
+// Lower bound (with a rounding margin) of |c - x| over the cell slab
+// [(lo + i) * cell, (lo + i + 1) * cell) along one axis.
+__device__ __forceinline__ float slab_gap(float x, int i_abs, float cell, float margin) {
+  const float a = __fmul_rn(static_cast<float>(i_abs), cell);
+  const float b = __fmul_rn(static_cast<float>(i_abs + 1), cell);
+  const float g = fmaxf(fmaxf(a - x, x - b), 0.f);
+  return fmaxf(g - margin, 0.f);
+}
+
+// Rounding margin of the exact searches: covers the float32 rounding of the
+// distance, of the bound and of the cell arithmetic for a query at p.
+__device__ __forceinline__ float search_margin(float cell, float r, float px, float py, float pz) {
+  return __fadd_rn(__fmul_rn(__fadd_rn(cell, r), 1e-5f),
+                   __fmul_rn(fmaxf(fmaxf(fabsf(px), fabsf(py)), fabsf(pz)), 4e-6f));
 }
 
 // d2 = (dx*dx + dy*dy) + dz*dz with d = p - q, every operation rounded on its own.
@@ -179,6 +196,7 @@ struct o3g_grid {
     v.sy = span[1];
     v.sz = span[2];
     v.inv_cell = inv_cell;
+    v.cell = cell;
     v.n = static_cast<int>(n);
     return v;
   }
