@@ -1133,18 +1133,18 @@ __global__ void __launch_bounds__(kThreads, Cfg::kMinBlocks) k_icp_iter(PairDesc
 
 // Blocks of one configuration of the persistent iteration kernel that are
 // resident on the GPU together.
+// (computed once, thread-safely, on first use)
 template <bool F64, class Cfg>
 int resident_blocks() {
-  static int resident = 0;
-  if (resident == 0) {
+  static const int resident = [] {
     int dev = 0, sms = kNumSMs, per_sm = 1;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_icp_iter<F64, Cfg>, kThreads, 0) != cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
     (void)cudaGetLastError();
-    resident = sms * per_sm;
-  }
+    return sms * per_sm;
+  }();
   return resident;
 }
 
@@ -2300,16 +2300,15 @@ __global__ void k_eval_sum(const double* __restrict__ partials, int ntiles, int 
 
 template <class Cfg>
 int eval_resident() {
-  static int resident = 0;
-  if (resident == 0) {
+  static const int resident = [] {
     int dev = 0, sms = kNumSMs, per_sm = 1;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_poses<Cfg>, kThreads, 0) != cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
     (void)cudaGetLastError();
-    resident = sms * per_sm;
-  }
+    return sms * per_sm;
+  }();
   return resident;
 }
 
