@@ -10,8 +10,9 @@ the same arithmetic in the same order):
   ``o3g.TILE_THROUGHPUT``: smaller stage, 7 blocks per SM), pinned with
   ``o3g.set_tile_config``.
 
-Block size (128 threads) and points per thread (1) are fixed by the kernel's
-reduction layout and are not searched.
+Block size (128 threads) and points per thread (1) are not searched: the tile
+partition fixes the summation order of the block partials, so changing it
+would change results in the last bits, which the two knobs above never do.
 
 ``tune_batch`` times a short batched call (a few iterations, CUDA events on
 the current stream) for every candidate, pins the fastest form for the batch's
