@@ -487,42 +487,54 @@ __device__ void block_reduce_store_f64(double (&v)[32], double* __restrict__ out
   }
 }
 
-// sin and cos of a small angle by their Taylor series (|x| <= 0.25: the first
-// omitted terms, x^15/15! and x^14/14!, are below 1e-19), else the library call.
-__device__ __forceinline__ void sincos_step(double x, double* s, double* c) {
-  if (fabs(x) > 0.25) {
-    sincos(x, s, c);
-    return;
-  }
-  const double x2 = x * x;
-  // sin x = x + x^3 (-1/3! + x^2/5! - x^4/7! + x^6/9! - x^8/11! + x^10/13!), Horner in x^2
-  double ps = 1.0 / 6227020800.0;         // 1/13!
-  ps = ps * x2 - 1.0 / 39916800.0;        // -1/11!
-  ps = ps * x2 + 1.0 / 362880.0;          // 1/9!
-  ps = ps * x2 - 1.0 / 5040.0;            // -1/7!
-  ps = ps * x2 + 1.0 / 120.0;             // 1/5!
-  ps = ps * x2 - 1.0 / 6.0;               // -1/3!
-  *s = x + x * x2 * ps;
-  // cos x = 1 - x^2 (1/2! - x^2/4! + x^4/6! - x^6/8! + x^8/10! - x^10/12! + x^12/14!)
-  double pc = 1.0 / 87178291200.0;        // 1/14!
-  pc = pc * x2 - 1.0 / 479001600.0;       // -1/12!
-  pc = pc * x2 + 1.0 / 3628800.0;         // 1/10!
-  pc = pc * x2 - 1.0 / 40320.0;           // -1/8!
-  pc = pc * x2 + 1.0 / 720.0;             // 1/6!
-  pc = pc * x2 - 1.0 / 24.0;              // -1/4!
-  pc = pc * x2 + 0.5;                     // 1/2!
-  *c = 1.0 - x2 * pc;
+// On this GPU a float64 add, multiply, fma, compare or min/max keeps a warp
+// busy for dozens of cycles however few of its lanes are active, while integer,
+// float32, conversion and shuffle instructions are short.  The serial float64
+// code below (the solve at the end of every iteration) is therefore written to
+// issue few float64 instructions: independent entries sit on different lanes of
+// one warp, and comparisons are made on integer bit patterns.
+
+// A 64-bit integer ordered like the double it encodes (non-NaN values; -0 and
+// +0 map to the same key).
+__device__ __forceinline__ long long order_key(double v) {
+  long long b = __double_as_longlong(v);
+  if (b == static_cast<long long>(0x8000000000000000ULL)) b = 0;
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
 }
 
-// 1 / d for d > 0: a float32 seed refined by two Newton steps x <- x (2 - d x)
-// (relative error ~1e-7 -> ~1e-14 -> below double rounding), much shorter on
-// this GPU than the full float64 division; outside the float32 range, division.
+__device__ __forceinline__ bool not_finite(double v) {
+  return (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
+}
+
+// 1 / d.  For a positive d within 2^-100 .. 2^100: a float32 seed x (rounding
+// plus rcp.approx, relative error below 2^-22), then 1/d = x / (1 - e) with
+// e = 1 - d x, evaluated as x (1 + e + e^2): the omitted x e^3 / (1 - e) is
+// below 2^-66 relative, so three float64 operations give the quotient to
+// within rounding, against the dozens of a full division.  Otherwise (zero,
+// negative, tiny, huge, not finite) the division.
 __device__ __forceinline__ double recip(double d) {
-  if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;
-  double x = static_cast<double>(__frcp_rn(static_cast<float>(d)));
-  x = x * fma(-d, x, 2.0);
-  x = x * fma(-d, x, 2.0);
-  return x;
+  const int hi = __double2hiint(d);
+  const int ex = (hi >> 20) & 0x7ff;  // biased exponent
+  if (hi < 0 || ex < 1023 - 100 || ex > 1023 + 100) return 1.0 / d;
+  float xs;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(xs) : "f"(__double2float_rn(d)));
+  const double x = static_cast<double>(xs);
+  const double e = fma(-d, x, 1.0);
+  return fma(x, fma(e, e, e), x);
+}
+
+// The polynomial q(x^2) of sin x = x + x^3 q or cos x = 1 - x^2 q, truncated to
+// its first N Taylor coefficients, by Horner's rule in x^2.
+template <int N>
+__device__ __forceinline__ double sincos_q(double x2, bool is_sin) {
+  constexpr double kSinQ[7] = {-1.0 / 6.0,          1.0 / 120.0,          -1.0 / 5040.0,         1.0 / 362880.0,
+                               -1.0 / 39916800.0,   1.0 / 6227020800.0,   -1.0 / 1307674368000.0};
+  constexpr double kCosQ[7] = {1.0 / 2.0,           -1.0 / 24.0,          1.0 / 720.0,           -1.0 / 40320.0,
+                               1.0 / 3628800.0,     -1.0 / 479001600.0,   1.0 / 87178291200.0};
+  double q = is_sin ? kSinQ[N - 1] : kCosQ[N - 1];
+#pragma unroll
+  for (int k = N - 2; k >= 0; --k) q = fma(q, x2, is_sin ? kSinQ[k] : kCosQ[k]);
+  return q;
 }
 
 // Float64 sums of `count` partials of kPartial doubles each (rows `first`,
@@ -558,79 +570,109 @@ __device__ __forceinline__ double sym6(const double* sums, int i, int j) {
   return sums[a * 6 - (a * (a - 1)) / 2 + (c - a)];
 }
 
-// The Gauss-Newton update on one warp, in float64 (Eq. 2): Gauss-Jordan
-// elimination without pivoting on [A | -b], lane j holding column j in
-// registers.  Its pivots are the Schur complements an LDL^T factorisation
-// produces, so the frozen-pivot rule is the same: a pivot <= 1e-12 * max_j A_jj
-// eliminates nothing and its unknown is 0.  Then dR = Rz(gamma) Ry(beta)
-// Rx(alpha) and T <- [dR, t] T, spread over lanes.
+// The Gauss-Newton update on one warp, in float64 (Eq. 2).  A x = -b is solved
+// by sweeping the bordered symmetric matrix [A b; b^T 0] on pivots 0..5
+// (Goodnight's symmetric sweep on pivot p = a_kk: a_kk <- -1/p, row and
+// column k <- entry / p, every other a_ij <- a_ij - a_ik a_jk / p); after the
+// last pivot the border holds A^-1 b, so x = -border.  The pivots are the
+// Schur complements an LDL^T factorisation produces, so the frozen-pivot rule
+// is the same: a pivot <= 1e-12 * max_j A_jj is not swept and its unknown is 0
+// (the others then solve the system without it).  Lane l < 28 holds entry
+// (i, j), i >= j, of the lower triangle, l = i (i + 1) / 2 + j, so a sweep step
+// costs five float64 operations for the whole matrix.  Then sin and cos of the
+// three angles on lanes 0..5 (as many Taylor terms as the largest angle needs
+// for a truncation error below 2^-60; the library call from 0.25 rad), dR =
+// Rz(gamma) Ry(beta) Rx(alpha) one entry per lane, and T <- [dR, t] T on lanes
+// 4 r + c.
 __device__ void solve_update(const double* sums, IcpState* __restrict__ st, double eps) {
   const int lane = threadIdx.x & 31;
   const double Tpre = lane < 12 ? st->T[lane] : 0.0;  // pose rows 0..2, fetched early
-  double a[6];
+  // this lane's entry; lanes 28..31 hold a copy of entry (0, 0) that nothing reads
+  const int tl = lane < 28 ? lane : 0;
+  const int i = (tl >= 1) + (tl >= 3) + (tl >= 6) + (tl >= 10) + (tl >= 15) + (tl >= 21);
+  const int j = tl - (i * (i + 1)) / 2;
+  double m = i < 6 ? sym6(sums, i, j) : (j < 6 ? sums[21 + j] : 0.0);
+  long long kmax = order_key(sums[0]);
 #pragma unroll
-  for (int i = 0; i < 6; ++i) a[i] = lane < 6 ? sym6(sums, i, lane) : (lane == 6 ? -sums[21 + i] : 0.0);
-  double mx = sums[0];
-#pragma unroll
-  for (int j = 1; j < 6; ++j) mx = fmax(mx, sym6(sums, j, j));
-  const double thr = 1e-12 * mx;
-  double inv[6];
-  bool frozen_any = false;
+  for (int d = 1; d < 6; ++d) kmax = max(kmax, order_key(sym6(sums, d, d)));
+  const double thr = 1e-12 * __longlong_as_double(kmax ^ ((kmax >> 63) & 0x7fffffffffffffffLL));
+  const long long kthr = order_key(thr);
+  unsigned frozen = 0u;
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    const double piv = shfl_d(a[k], k);
-    const bool fz = !(piv > thr);
-    frozen_any = frozen_any || fz;
-    const double ik = fz ? 0.0 : recip(piv);
-    inv[k] = ik;
-    double colk[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) colk[i] = shfl_d(a[i], k);
-    const double rk = a[k];
-    if (!fz) {
-#pragma unroll
-      for (int i = 0; i < 6; ++i)
-        if (i != k) a[i] = fma(-colk[i] * ik, rk, a[i]);
+    const double p = shfl_d(m, (k * (k + 3)) / 2);
+    if (!(order_key(p) > kthr)) {  // p <= thr
+      frozen |= 1u << k;
+      continue;
     }
+    const double rp = recip(p);
+    const double aik = shfl_d(m, i >= k ? (i * (i + 1)) / 2 + k : (k * (k + 1)) / 2 + i);
+    const double ajk = shfl_d(m, j >= k ? (j * (j + 1)) / 2 + k : (k * (k + 1)) / 2 + j);
+    const bool on_i = i == k, on_j = j == k;
+    // pivot: -1/p;  row or column k: entry / p;  any other entry: entry - a_ik (a_jk / p)
+    const double X = (on_i && on_j) ? -1.0 : ((on_i || on_j) ? m : ajk);
+    const double Y = (on_i || on_j) ? 1.0 : -aik;
+    const double Z = (on_i || on_j) ? 0.0 : m;
+    m = fma(Y, X * rp, Z);
   }
-  // lane 6 holds the reduced right-hand side; x_k = rhs_k / pivot_k (0 when frozen)
-  double xi[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) xi[i] = shfl_d(a[i] * inv[i], 6);
-  double sn = 0.0, cs = 1.0;
-  if (lane < 3) sincos_step(lane == 0 ? xi[0] : (lane == 1 ? xi[1] : xi[2]), &sn, &cs);
-  const double sa = shfl_d(sn, 0), ca = shfl_d(cs, 0), sb = shfl_d(sn, 1), cb = shfl_d(cs, 1);
-  const double sg = shfl_d(sn, 2), cg = shfl_d(cs, 2);
-  // row r of dR for lanes 4r .. 4r+3, column c = lane % 4 of T
-  const int r = (lane >> 2) < 3 ? (lane >> 2) : 0, c = lane & 3;
-  double d0, d1, d2;
-  if (r == 0) {
-    d0 = cg * cb;
-    d1 = cg * sb * sa - sg * ca;
-    d2 = cg * sb * ca + sg * sa;
-  } else if (r == 1) {
-    d0 = sg * cb;
-    d1 = sg * sb * sa + cg * ca;
-    d2 = sg * sb * ca - cg * sa;
+  // x_k = -(border entry (6, k)) on lane 21 + k, 0 for a frozen pivot
+  const int kx = lane - 21;
+  const double xv = (kx >= 0 && kx < 6 && !((frozen >> kx) & 1u)) ? -m : 0.0;
+  // sin (lanes 0..2) and cos (lanes 3..5) of alpha, beta, gamma
+  const bool is_sin = lane < 3;
+  const double xa = shfl_d(xv, 21 + lane % 3);
+  const unsigned hx = is_sin ? (static_cast<unsigned>(__double2hiint(xa)) & 0x7fffffffu) : 0u;
+  const unsigned hmax = __reduce_max_sync(0xffffffffu, hx);  // high word of the largest |angle|
+  double f;
+  if (hmax >= 0x3FD00000u) {  // some |angle| >= 2^-2
+    double sn, cs;
+    sincos(xa, &sn, &cs);
+    f = is_sin ? sn : cs;
   } else {
-    d0 = -sb;
-    d1 = cb * sa;
-    d2 = cb * ca;
+    const double x2 = xa * xa;
+    double q;
+    if (hmax < 0x3EB00000u) q = sincos_q<1>(x2, is_sin);       // all |angle| < 2^-20
+    else if (hmax < 0x3F300000u) q = sincos_q<2>(x2, is_sin);  // < 2^-12
+    else if (hmax < 0x3F800000u) q = sincos_q<3>(x2, is_sin);  // < 2^-7
+    else if (hmax < 0x3FB00000u) q = sincos_q<4>(x2, is_sin);  // < 2^-4
+    else q = sincos_q<6>(x2, is_sin);                          // < 2^-2
+    f = fma((is_sin ? xa : -1.0) * x2, q, is_sin ? xa : 1.0);
   }
+  const double sa = shfl_d(f, 0), sb = shfl_d(f, 1), sg = shfl_d(f, 2);
+  const double ca = shfl_d(f, 3), cb = shfl_d(f, 4), cg = shfl_d(f, 5);
+  // entry e = 3 row + column of dR on lane e (lanes 9..31 repeat entry 8) as a1 a2 a3 + b1 b2:
+  // row 0: cg cb, cg sb sa - sg ca, cg sb ca + sg sa;  row 1: sg cb, sg sb sa + cg ca,
+  // sg sb ca - cg sa;  row 2: -sb, cb sa, cb ca
+  const int e = lane < 9 ? lane : 8;
+  const double a1 = e < 3 ? cg : (e < 6 ? sg : (e == 6 ? -1.0 : cb));
+  const double a2 = (e == 0 || e == 3) ? cb : (e == 7 ? sa : (e == 8 ? ca : sb));
+  const double a3 = (e == 1 || e == 4) ? sa : ((e == 2 || e == 5) ? ca : 1.0);
+  const double b1 = e == 1 ? -sg : (e == 2 ? sg : (e == 4 ? cg : (e == 5 ? -cg : 0.0)));
+  const double b2 = (e == 1 || e == 4) ? ca : ((e == 2 || e == 5) ? sa : 0.0);
+  const double dR = fma(b1, b2, (a1 * a2) * a3);
+  // row r of dR times column c of T (plus t_r in column 3) on lane 4 r + c
+  const int r = (lane >> 2) < 3 ? (lane >> 2) : 0, c = lane & 3;
+  const double d0 = shfl_d(dR, 3 * r), d1 = shfl_d(dR, 3 * r + 1), d2 = shfl_d(dR, 3 * r + 2);
   const double t0 = shfl_d(Tpre, c), t1 = shfl_d(Tpre, 4 + c), t2 = shfl_d(Tpre, 8 + c);
-  double tn = d0 * t0 + d1 * t1 + d2 * t2;
-  if (c == 3) tn += r == 0 ? xi[3] : (r == 1 ? xi[4] : xi[5]);
+  const double xt = shfl_d(xv, 24 + r);
+  const double tn = fma(d2, t2, fma(d1, t1, fma(d0, t0, c == 3 ? xt : 0.0)));
   if (lane < 12) {
     st->T[lane] = tn;
     if (c < 3) st->R[3 * r + c] = __double2float_rn(tn);
     else st->t[r] = __double2float_rn(tn);
   }
+  // converged when |(alpha, beta, gamma)|^2 < eps^2 and |t|^2 < eps^2 (eps > 0)
+  bool done = false;
+  if (order_key(eps) > 0) {
+    const double sq = xv * xv;
+    const double s3 = (sq + __shfl_down_sync(0xffffffffu, sq, 1)) + __shfl_down_sync(0xffffffffu, sq, 2);
+    const unsigned small = __ballot_sync(0xffffffffu, order_key(s3) < order_key(eps * eps));
+    done = ((small >> 21) & 1u) && ((small >> 24) & 1u);
+  }
   if (lane == 0) {
-    if (frozen_any) st->degenerate = 1;
+    if (frozen) st->degenerate = 1;
     st->iters += 1;
-    const double w2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
-    const double v2 = xi[3] * xi[3] + xi[4] * xi[4] + xi[5] * xi[5];
-    if (eps > 0.0 && fmax(w2, v2) < eps * eps) st->done = 1;
+    if (done) st->done = 1;
   }
 }
 
@@ -887,8 +929,8 @@ __device__ void finish(const double* __restrict__ gsums, int ngroups, IcpState* 
     return;
   }
   if (threadIdx.x >= 32) return;
-  const bool bad = __any_sync(0xffffffffu, threadIdx.x < 27 && !isfinite(sums[threadIdx.x]));
-  if (bad || count < (kind == kPointToPoint ? 3.0 : 6.0)) {
+  const bool bad = __any_sync(0xffffffffu, threadIdx.x < 27 && not_finite(sums[threadIdx.x]));
+  if (bad || order_key(count) < order_key(kind == kPointToPoint ? 3.0 : 6.0)) {
     if (threadIdx.x == 0) {
       if (bad) st->nonfinite = 1;
       else st->few_corr = 1;
@@ -900,11 +942,15 @@ __device__ void finish(const double* __restrict__ gsums, int ngroups, IcpState* 
   else solve_update(sums, st, eps);
 }
 
+// The convergence threshold as the device reads it: eps if eps > 0, else 0
+// (never; also for NaN), so that the device tests it on its bit pattern.
+inline double stop_eps(double eps) { return eps > 0.0 ? eps : 0.0; }
+
 // Everything one registration problem brings to an iteration launch.
 struct PairDesc {
   GridView g;
   float cell, r;
-  double eps;          // convergence threshold of this pair (<= 0: never)
+  double eps;          // convergence threshold of this pair (0: never; see stop_eps)
   int kind;            // kPointToPlane or kPointToPoint
   float ctr[3];        // point-to-point: reference point subtracted before the moments
   const float4* src4;  // cell-sorted source, .w = original index bits
@@ -1274,7 +1320,7 @@ struct Work {
     P.g = g->view();
     P.cell = g->cell;
     P.r = r;
-    P.eps = eps;
+    P.eps = stop_eps(eps);
     P.kind = kind;
     // the centre of the grid's box: near every point that can find a partner
     for (int k = 0; k < 3; ++k)
@@ -1584,7 +1630,7 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const 
     P.g = gv;
     P.cell = g->cell;
     P.r = r;
-    P.eps = eps;
+    P.eps = stop_eps(eps);
     P.kind = kPointToPlane;
     P.ctr[0] = P.ctr[1] = P.ctr[2] = 0.f;
     P.src4 = src4;
@@ -1759,7 +1805,7 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
     P.g = tgts[p]->view();
     P.cell = tgts[p]->cell;
     P.r = static_cast<float>(max_corr_dist[p]);
-    P.eps = eps;
+    P.eps = stop_eps(eps);
     P.kind = kPointToPlane;
     P.ctr[0] = P.ctr[1] = P.ctr[2] = 0.f;
     P.src4 = d_src4.as<float4>() + off[p];
@@ -1947,7 +1993,7 @@ PairDesc slot_desc(o3g_server* sv, int k, int tile0) {
   P.g = sl.grid->view();
   P.cell = sl.grid->cell;
   P.r = sl.r;
-  P.eps = sl.eps;
+  P.eps = stop_eps(sl.eps);
   P.kind = kPointToPlane;
   P.ctr[0] = P.ctr[1] = P.ctr[2] = 0.f;
   P.src4 = sl.src4;
