@@ -357,6 +357,9 @@ O3G_API int32_t o3g_voxel_down_sample(const float* d_xyz, int64_t n, int32_t str
  */
 typedef struct o3g_server o3g_server;
 O3G_API int32_t o3g_server_create(int32_t max_active, int64_t hbm_budget_bytes, void* stream, o3g_server** out);
+/* The device-memory estimate a request of ns source and nt target points is
+ * admitted against (bytes; ns, nt >= 0, else -1).  No device work. */
+O3G_API int64_t o3g_server_request_bytes(int64_t ns, int64_t nt);
 O3G_API int32_t o3g_server_destroy(o3g_server* server);
 O3G_API int32_t o3g_server_submit(o3g_server* server, const float* h_src, int64_t ns, const float* h_tgt, int64_t nt,
                                   const float* h_tgt_nrm, float normal_radius, int32_t normal_max_nn,
@@ -381,7 +384,7 @@ O3G_API int32_t o3g_server_completed(o3g_server* server, int64_t* ids, int32_t c
  * two differences: the source is processed in the caller's order (the sums of
  * J^T J and J^T r therefore round differently, within the usual tolerances),
  * and all working memory is one library-owned static device array of
- * 4,736,256 bytes (4.5 MiB) that every GPU loading the library holds until the
+ * 4,203,520 bytes (4.0 MiB) that every GPU loading the library holds until the
  * process exits.
  *   - ns > O3G_NOALLOC_MAX_POINTS gives O3G_ERR_ARG; nothing is allocated.
  *   - The first call on a device looks up that array's device address for the

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <cstring>
 #include <new>
 
 #include "o3g_internal.cuh"
@@ -23,16 +24,23 @@ constexpr int kThreads = 256;
 
 // --------------------------------------------------------------- bbox
 
+// bb: cell coordinate minima (0-2) and maxima (3-5), the non-finite flag (6),
+// and the coordinate minima (7-9) and maxima (10-12) as float_key values.
 __global__ void k_bbox_init(int* bb) {
-  if (threadIdx.x < 3) bb[threadIdx.x] = INT_MAX;
-  else if (threadIdx.x < 6) bb[threadIdx.x] = INT_MIN;
-  else if (threadIdx.x == 6) bb[6] = 0;
+  const int t = threadIdx.x;
+  if (t < 3 || (t >= 7 && t < 10)) bb[t] = INT_MAX;
+  else if (t < 6 || (t >= 10 && t < 13)) bb[t] = INT_MIN;
+  else if (t == 6) bb[6] = 0;
 }
+
+// An int ordered like the float it encodes (non-NaN); its own inverse.
+__host__ __device__ __forceinline__ int float_key(int bits) { return bits ^ ((bits >> 31) & 0x7fffffff); }
 
 __global__ void __launch_bounds__(kThreads) k_bbox(const float* __restrict__ xyz, int n, int stride, float inv,
                                                    int* __restrict__ bb) {
   int mn0 = INT_MAX, mn1 = INT_MAX, mn2 = INT_MAX;
   int mx0 = INT_MIN, mx1 = INT_MIN, mx2 = INT_MIN;
+  int fn[3] = {INT_MAX, INT_MAX, INT_MAX}, fx[3] = {INT_MIN, INT_MIN, INT_MIN};
   int bad = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float* p = xyz + static_cast<int64_t>(i) * stride;
@@ -48,6 +56,13 @@ __global__ void __launch_bounds__(kThreads) k_bbox(const float* __restrict__ xyz
     mx0 = max(mx0, cx);
     mx1 = max(mx1, cy);
     mx2 = max(mx2, cz);
+    const int kx = float_key(__float_as_int(x)), ky = float_key(__float_as_int(y)), kz = float_key(__float_as_int(z));
+    fn[0] = min(fn[0], kx);
+    fn[1] = min(fn[1], ky);
+    fn[2] = min(fn[2], kz);
+    fx[0] = max(fx[0], kx);
+    fx[1] = max(fx[1], ky);
+    fx[2] = max(fx[2], kz);
   }
   const unsigned full = 0xffffffffu;
   mn0 = __reduce_min_sync(full, mn0);
@@ -57,6 +72,11 @@ __global__ void __launch_bounds__(kThreads) k_bbox(const float* __restrict__ xyz
   mx1 = __reduce_max_sync(full, mx1);
   mx2 = __reduce_max_sync(full, mx2);
   bad = __reduce_or_sync(full, bad);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    fn[a] = __reduce_min_sync(full, fn[a]);
+    fx[a] = __reduce_max_sync(full, fx[a]);
+  }
   if ((threadIdx.x & 31) == 0) {
     if (mn0 != INT_MAX) {
       atomicMin(bb + 0, mn0);
@@ -65,6 +85,11 @@ __global__ void __launch_bounds__(kThreads) k_bbox(const float* __restrict__ xyz
       atomicMax(bb + 3, mx0);
       atomicMax(bb + 4, mx1);
       atomicMax(bb + 5, mx2);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        atomicMin(bb + 7 + a, fn[a]);
+        atomicMax(bb + 10 + a, fx[a]);
+      }
     }
     if (bad) atomicOr(bb + 6, 1);
   }
@@ -301,10 +326,18 @@ __global__ void __launch_bounds__(kThreads) k_set_normals(const float* __restric
                                                           const float4* __restrict__ pts, int n,
                                                           float4* __restrict__ out) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  int o = __float_as_int(pts[k].w);
-  const float* q = nrm + static_cast<int64_t>(o) * stride;
-  out[k] = make_float4(q[0], q[1], q[2], 0.f);
+  float len = 0.f;
+  if (k < n) {
+    int o = __float_as_int(pts[k].w);
+    const float* q = nrm + static_cast<int64_t>(o) * stride;
+    out[k] = make_float4(q[0], q[1], q[2], 0.f);
+    len = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+  }
+  // out[n].x (zeroed before the launch): the largest normal length, the bound
+  // the ICP sums are scaled by.  Non-negative floats order like their bits as
+  // ints; a NaN length (sqrtf's NaN is positive) orders above every number.
+  const int bits = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned>(__float_as_int(len))));
+  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(&out[n].x), bits);
 }
 
 inline int blocks_for(int64_t n, int per_block) {
@@ -660,6 +693,7 @@ static int32_t build_impl(const float* d_xyz, int64_t n64, int stride, float cel
     O3G_TRY(cudaMemsetAsync(g->cell_start, 0, 2 * sizeof(uint32_t), s));
     O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->pts), sizeof(float4), s));
     O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->nrm), sizeof(float4), s));
+    O3G_TRY(cudaMemsetAsync(g->nrm, 0, sizeof(float4), s));
     O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->pos_of), sizeof(int32_t), s));
     O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->col_z), sizeof(uint32_t), s));
     O3G_TRY(cudaMemsetAsync(g->col_z, 0, sizeof(uint32_t), s));
@@ -669,9 +703,9 @@ static int32_t build_impl(const float* d_xyz, int64_t n64, int stride, float cel
   }
   // 1. bounding box; enlarge the cell while the dense table would be too big.
   DevBuf bb(s);
-  O3G_TRY(bb.alloc(8 * sizeof(int)));
+  O3G_TRY(bb.alloc(16 * sizeof(int)));
   const int64_t cap = std::min<int64_t>(32LL * n + (1LL << 20), (1LL << 31) - 2);
-  int h[7];
+  int h[13];
   int64_t span[3], cells = 0;
   float inv = 0.f;
   for (int attempt = 0;; ++attempt) {
@@ -686,7 +720,7 @@ static int32_t build_impl(const float* d_xyz, int64_t n64, int stride, float cel
     k_bbox<<<nb, kThreads, 0, s>>>(d_xyz, n, stride, inv, bb.as<int>());
     count_launch(2);
     O3G_TRY(cudaGetLastError());
-    O3G_TRY(cudaMemcpyAsync(h, bb.p, 7 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    O3G_TRY(cudaMemcpyAsync(h, bb.p, 13 * sizeof(int), cudaMemcpyDeviceToHost, s));
     O3G_TRY(cudaStreamSynchronize(s));
     if (h[6]) {
       set_error("o3g_build_grid: non-finite point coordinate");
@@ -709,6 +743,9 @@ static int32_t build_impl(const float* d_xyz, int64_t n64, int stride, float cel
   for (int a = 0; a < 3; ++a) {
     g->lo[a] = h[a];
     g->span[a] = static_cast<int>(span[a]);
+    int lo_bits = float_key(h[7 + a]), hi_bits = float_key(h[10 + a]);
+    std::memcpy(&g->box_lo[a], &lo_bits, sizeof(float));
+    std::memcpy(&g->box_hi[a], &hi_bits, sizeof(float));
   }
   g->cells = cells;
 
@@ -731,7 +768,8 @@ static int32_t build_impl(const float* d_xyz, int64_t n64, int stride, float cel
   // 4-5. cell table and sorted points
   O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->cell_start), sizeof(uint32_t) * (cells + 1), s));
   O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->pts), sizeof(float4) * n, s));
-  O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->nrm), sizeof(float4) * n, s));
+  O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->nrm), sizeof(float4) * (n + 1), s));
+  O3G_TRY(cudaMemsetAsync(g->nrm + n, 0, sizeof(float4), s));
   O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->pos_of), sizeof(int32_t) * n, s));
   int nbc = blocks_for(cells + 1, kThreads);
   if (nbc > kNumSMs * 16) nbc = kNumSMs * 16;
@@ -813,6 +851,7 @@ extern "C" int32_t o3g_grid_set_normals(o3g_grid* g, const float* d_nrm, int64_t
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (n > 0) {
+    O3G_TRY(cudaMemsetAsync(g->nrm + n, 0, sizeof(float4), s));
     k_set_normals<<<blocks_for(n, kThreads), kThreads, 0, s>>>(d_nrm, stride, g->pts, static_cast<int>(n), g->nrm);
     count_launch();
     O3G_TRY(cudaGetLastError());

@@ -9,11 +9,13 @@
 //      every pruning bound carries a margin for float32 rounding, and ties are
 //      kept, so the result is the minimum of (d2, original index));
 //   3. r = (p - q) . n, J = [p x n ; n]; the 21 upper entries of J^T J, J^T r,
-//      r^2, d2 and |C| summed per thread with TwoSum compensation, then across
-//      the block by a fixed shuffle tree, into one float64 partial per block;
-//   4. the last block to finish (atomic arrival counter, no waiting) sums the
-//      partials in float64 in block order, solves (J^T J) xi = -J^T r by LDL^T
-//      with the frozen-pivot rule, and updates T <- [Rz Ry Rx(xi), t] T on the
+//      r^2, d2 and |C| as exact (value, error) pairs, summed over the tile's
+//      rows in a fixed order into one compensated float32 pair per sum, which
+//      is added as a 64-bit fixed-point integer (exact, order-free) to the
+//      pair's accumulators;
+//   4. the last tile to finish (atomic arrival counter, no waiting) converts the
+//      totals to float64, solves (J^T J) xi = -J^T r with the frozen-pivot
+//      rule (the pivots of LDL^T), and updates T <- [Rz Ry Rx(xi), t] T on the
 //      device.  The next launch reads the new pose.
 // The pose never leaves the device between iterations.
 #include <algorithm>
@@ -33,8 +35,9 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr int kPPT = 1;       // source points per thread
-constexpr int kPartial = 32;  // doubles per block partial
-constexpr int kGroup = 32;    // block partials summed together by a group's last block
+constexpr int kPartial = 32;  // sum columns of a block partial (column kBadCol: see add_fixed)
+constexpr int kAccRows = 32;  // fixed-point accumulator rows of a pair (its tiles spread over them)
+constexpr int kBadCol = 31;   // accumulator column counting partials outside their bound
 
 struct Pose {
   double m[16];
@@ -50,7 +53,7 @@ struct IcpState {
   int degenerate;  // some pivot was frozen
   int few_corr;    // stopped with < 6 correspondences
   int nonfinite;   // the normal equations were not finite
-  unsigned arrived;  // groups of the current launch whose sum is stored
+  unsigned arrived;  // tiles of the current launch whose sums are added
   double A[36];
   double b[6];
   double stats[3];  // sum r^2, sum d2, |C|
@@ -436,7 +439,7 @@ __device__ __forceinline__ void add_pair(float& s, float& c, float s2, float c2)
 // float32 pair; the four quarters are then added in order and the pair
 // rounded to float64.  A fixed sequence, so the result does not depend on
 // timing; only a few registers per thread.
-__device__ void block_reduce_rows(const float* __restrict__ rows, int kind, double* __restrict__ out) {
+__device__ void block_reduce_rows(const float* __restrict__ rows, int kind, float& out_s, float& out_c) {
   static_assert(kThreads == 128, "four quarters of 32 rows");
   __shared__ float qs[4][32], qc[4][32];
   const int k = threadIdx.x & 31, quarter = threadIdx.x >> 5;
@@ -458,13 +461,15 @@ __device__ void block_reduce_rows(const float* __restrict__ rows, int kind, doub
   if (threadIdx.x < kPartial) {
     float ts = qs[0][k], tc = qc[0][k];
     for (int q = 1; q < 4; ++q) add_pair(ts, tc, qs[q][k], qc[q][k]);
-    out[k] = static_cast<double>(ts) + static_cast<double>(tc);
+    out_s = ts;
+    out_c = tc;
   }
 }
 
-// The all-float64 form of block_reduce_store: the same butterfly reduce-scatter
-// and in-order warp combination on doubles, plain float64 adds.
-__device__ void block_reduce_store_f64(double (&v)[32], double* __restrict__ out) {
+// The all-float64 form of the block partial: a butterfly reduce-scatter in each
+// warp, then the warps in order, plain float64 adds.  Column t ends on thread t
+// (t < kPartial) as `out`.
+__device__ void block_reduce_f64(double (&v)[32], double& out) {
   __shared__ double ws[kThreads / 32][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -483,7 +488,7 @@ __device__ void block_reduce_store_f64(double (&v)[32], double* __restrict__ out
   if (t < kPartial) {
     double s = ws[0][t];
     for (int w = 1; w < kThreads / 32; ++w) s += ws[w][t];
-    out[t] = s;
+    out = s;
   }
 }
 
@@ -500,10 +505,6 @@ __device__ __forceinline__ long long order_key(double v) {
   long long b = __double_as_longlong(v);
   if (b == static_cast<long long>(0x8000000000000000ULL)) b = 0;
   return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
-}
-
-__device__ __forceinline__ bool not_finite(double v) {
-  return (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
 }
 
 // 1 / d.  For a positive d within 2^-100 .. 2^100: a float32 seed x (rounding
@@ -535,31 +536,6 @@ __device__ __forceinline__ double sincos_q(double x2, bool is_sin) {
 #pragma unroll
   for (int k = N - 2; k >= 0; --k) q = fma(q, x2, is_sin ? kSinQ[k] : kCosQ[k]);
   return q;
-}
-
-// Float64 sums of `count` partials of kPartial doubles each (rows `first`,
-// `first + 1`, ...), in row order: 128 threads = 32 columns x 4 interleaved row
-// subsets, combined in subset order.  Rows are taken 32 at a time and the 8
-// loads of a thread in each batch are issued before its first add, so the L2
-// latency is paid once per batch.  Result in out[0..kPartial).
-__device__ void sum_partials(const double* __restrict__ rows, int first, int count, double* out) {
-  __shared__ double sub[4][kPartial];
-  const int col = threadIdx.x & 31, q = threadIdx.x >> 5;
-  double acc = 0.0;
-  for (int b0 = 0; b0 < count; b0 += 32) {
-    double val[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int b = b0 + q + 4 * j;
-      val[j] = b < count ? __ldcg(rows + static_cast<size_t>(first + b) * kPartial + col) : 0.0;
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc += val[j];
-  }
-  sub[q][col] = acc;
-  __syncthreads();
-  if (threadIdx.x < kPartial) out[col] = ((sub[0][col] + sub[1][col]) + sub[2][col]) + sub[3][col];
-  __syncthreads();
 }
 
 __device__ __forceinline__ double shfl_d(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
@@ -598,7 +574,9 @@ __device__ void solve_update(const double* sums, IcpState* __restrict__ st, doub
   const double thr = 1e-12 * __longlong_as_double(kmax ^ ((kmax >> 63) & 0x7fffffffffffffffLL));
   const long long kthr = order_key(thr);
   unsigned frozen = 0u;
-#pragma unroll
+  // not unrolled: this runs once per launch on whichever SM finishes last, so its
+  // instructions are fetched cold, and one loop body is fetched once, not six times
+#pragma unroll 1
   for (int k = 0; k < 6; ++k) {
     const double p = shfl_d(m, (k * (k + 3)) / 2);
     if (!(order_key(p) > kthr)) {  // p <= thr
@@ -905,43 +883,6 @@ __device__ void solve_update_p2p(const double* sums, IcpState* __restrict__ st, 
   }
 }
 
-// Run by the last block of a launch once every group sum is stored: the float64
-// total in group order, then per mode the update, the stored normal equations,
-// or fitness / rmse.
-__device__ void finish(const double* __restrict__ gsums, int ngroups, IcpState* __restrict__ st, double eps,
-                       int mode, int ns, int kind, float cx, float cy, float cz) {
-  __shared__ double sums[kPartial];
-  sum_partials(gsums, 0, ngroups, sums);
-  if (threadIdx.x == 0) st->arrived = 0u;  // ready for the next launch
-  const double count = sums[29];
-  if (mode == kEvaluate) {
-    if (threadIdx.x == 0) {
-      st->fitness = ns > 0 ? count / static_cast<double>(ns) : 0.0;
-      st->rmse = count > 0.0 ? sqrt(sums[28] / count) : 0.0;
-    }
-    return;
-  }
-  if (mode == kEquations) {
-    const int t = threadIdx.x;
-    if (t < 36) st->A[t] = sym6(sums, t / 6, t % 6);
-    else if (t < 42) st->b[t - 36] = sums[21 + (t - 36)];
-    else if (t < 45) st->stats[t - 42] = sums[27 + (t - 42)];
-    return;
-  }
-  if (threadIdx.x >= 32) return;
-  const bool bad = __any_sync(0xffffffffu, threadIdx.x < 27 && not_finite(sums[threadIdx.x]));
-  if (bad || order_key(count) < order_key(kind == kPointToPoint ? 3.0 : 6.0)) {
-    if (threadIdx.x == 0) {
-      if (bad) st->nonfinite = 1;
-      else st->few_corr = 1;
-      st->done = 1;
-    }
-    return;
-  }
-  if (kind == kPointToPoint) solve_update_p2p(sums, st, eps, cx, cy, cz);
-  else solve_update(sums, st, eps);
-}
-
 // The convergence threshold as the device reads it: eps if eps > 0, else 0
 // (never; also for NaN), so that the device tests it on its bit pattern.
 inline double stop_eps(double eps) { return eps > 0.0 ? eps : 0.0; }
@@ -958,13 +899,147 @@ struct PairDesc {
   int ntiles;          // ceil(ns / kThreads), at least 1
   int tile0;           // first global tile of this pair
   IcpState* st;
-  double* partials;    // ntiles x kPartial
-  double* gsums;       // ceil(ntiles / kGroup) x kPartial
-  unsigned* group_cnt;  // ceil(ntiles / kGroup) arrival counters
+  unsigned long long* acc;  // nacc x kPartial fixed-point sums (see add_fixed), zero between launches
+  int nacc;                 // accumulator rows: min(kAccRows, ntiles)
+  float bnd_a, bnd_b;       // per-correspondence bounds the sums are scaled by (see set_sums)
   int32_t* hints;      // per source point: sorted target position of its last match, or -1; may be null
   int32_t* corr_out;   // kCorrOnly outputs (by original source index)
   float* d2_out;
 };
+
+// Fixed-point sums.  Every tile adds its partial of each sum column to one of
+// its pair's kAccRows accumulator rows as a 64-bit integer count of units 2^E
+// (E per column), by integer atomics.  Integer addition is exact and
+// associative, so the totals do not depend on the order in which tiles add
+// them, nor on which other pairs share the launch.  E rests on an a-priori
+// bound: a column's total is at most ns times a bound on one correspondence's
+// term, and E puts that bound below 2^62, so no accumulator overflows; a unit
+// is then at most 2^-61 of the bound, and each partial rounds by at most one
+// unit.
+
+// Bound on one correspondence's value in row slot `slot` (kTerm numbering).
+// Point-to-plane: |J_0..2| = |p x n| <= a L, |J_3..5| = |n| <= L, |r| <= R L,
+// d2 <= R^2, flag 1, where a bounds |p|, L the normals' length, R the radius.
+// Point-to-point: |a| <= a, |b| <= b (both parts of each), |a|^2, |b|^2,
+// d2 <= R^2, flag 1.
+__device__ __forceinline__ float slot_bound(int kind, int slot, float a, float b, float L, float R) {
+  if (slot == kOne) return 1.f;
+  if (slot == kZero) return 0.f;
+  if (kind == kPointToPlane) {
+    if (slot < 3) return a * L;
+    if (slot < 6) return L;
+    if (slot == 6) return R * L;
+    if (slot == 7) return R * R;
+    return 1.f;  // 8: the match flag
+  }
+  if (slot < 6) return a;   // a, high and low parts
+  if (slot < 12) return b;  // b, high and low parts
+  if (slot == 12) return a * a;
+  if (slot == 13) return b * b;
+  if (slot == 14) return R * R;
+  return 1.f;  // 15: the match flag
+}
+
+// E of sum column k: floor(log2(bound)) + 1 - 62, the bound computed in float32
+// with a 1% margin on every factor (nlen: the target normals' length bound).
+__device__ __forceinline__ int sum_exponent(const PairDesc& P, int k, float nlen) {
+  const uchar4 ix = *reinterpret_cast<const uchar4*>(kTerm[P.kind][k]);
+  const float R = P.r * 1.01f, L = nlen * 1.01f, a = P.bnd_a * 1.01f, b = P.bnd_b * 1.01f;
+  const float B = slot_bound(P.kind, ix.x, a, b, L, R) * slot_bound(P.kind, ix.y, a, b, L, R) *
+                  (static_cast<float>(max(P.ns, 1)) * 1.01f);
+  if (!(B > 0.f)) return 0;  // an empty column (or a NaN bound: the values are then flagged)
+  const int e = ((__float_as_int(B) >> 23) & 0xff) - 127;
+  return min(max(e + 1 - 62, -126), 126);
+}
+
+// Adds this lane's column k of the block partial, the exact pair ts + tc, to
+// accumulator row `acc` in units of 2^E.  A partial whose value is not below
+// 2^62 units (outside its bound, or not finite) is left out and counted in
+// column kBadCol, which the finish reports as non-finite sums.  Warp 0, lane k.
+__device__ __forceinline__ void add_fixed(unsigned long long* acc, int k, float ts, float tc, int E) {
+  const float sc = __int_as_float((127 - E) << 23);  // 2^-E
+  const float hs = ts * sc, hc = tc * sc;             // exact (an underflow is below one unit)
+  const bool ok = fabsf(hs) < 0x1p62f && fabsf(hc) < 0x1p62f;
+  long long v = ok ? __float2ll_rn(hs) + __float2ll_rn(hc) : 0;
+  const bool bad = __any_sync(0xffffffffu, !ok);
+  if (k == kBadCol) v = bad ? 1 : 0;
+  if (v != 0) atomicAdd(acc + k, static_cast<unsigned long long>(v));
+}
+
+// The same for a float64 partial.
+__device__ __forceinline__ void add_fixed_f64(unsigned long long* acc, int k, double s, int E) {
+  const double h = s * __longlong_as_double(static_cast<long long>(1023 - E) << 52);  // exact
+  const bool ok = (__double_as_longlong(h) & 0x7fffffffffffffffLL) < 0x43D0000000000000LL;  // |h| < 2^62
+  long long v = ok ? __double2ll_rn(h) : 0;
+  const bool bad = __any_sync(0xffffffffu, !ok);
+  if (k == kBadCol) v = bad ? 1 : 0;
+  if (v != 0) atomicAdd(acc + k, static_cast<unsigned long long>(v));
+}
+
+// Run by the last tile of a pair to arrive: the totals of every sum column
+// (integer adds, in any order) converted to float64 with one rounding, the
+// accumulator rows cleared for the next launch; then per mode the update, the
+// stored normal equations, or fitness / rmse.
+__device__ void finish(const PairDesc& P, int mode, float nlen) {
+  static_assert(kThreads == 128 && kPartial == 32 && kAccRows % 4 == 0, "4 x 32 threads over the rows");
+  __shared__ long long sub[4][kPartial];
+  __shared__ double sums[kPartial];
+  __shared__ bool bad;
+  const int col = threadIdx.x & 31, q = threadIdx.x >> 5;
+  unsigned long long v[kAccRows / 4];
+#pragma unroll
+  for (int j = 0; j < kAccRows / 4; ++j) {
+    const int row = q + 4 * j;
+    v[j] = row < P.nacc ? __ldcg(P.acc + static_cast<size_t>(row) * kPartial + col) : 0ull;
+  }
+  unsigned long long t = 0ull;
+#pragma unroll
+  for (int j = 0; j < kAccRows / 4; ++j) {
+    t += v[j];
+    const int row = q + 4 * j;
+    if (row < P.nacc) P.acc[static_cast<size_t>(row) * kPartial + col] = 0ull;
+  }
+  sub[q][col] = static_cast<long long>(t);
+  IcpState* const st = P.st;
+  if (threadIdx.x == 0) st->arrived = 0u;  // ready for the next launch
+  __syncthreads();
+  if (threadIdx.x < kPartial) {
+    const long long tot = sub[0][col] + sub[1][col] + sub[2][col] + sub[3][col];
+    const int E = sum_exponent(P, col, nlen);
+    sums[col] = __ll2double_rn(tot) * __longlong_as_double(static_cast<long long>(1023 + E) << 52);
+    if (col == kBadCol) bad = tot != 0;
+  }
+  __syncthreads();
+  const double count = sums[29];
+  if (mode == kEvaluate) {
+    if (threadIdx.x == 0) {
+      if (bad) st->nonfinite = 1;
+      st->fitness = P.ns > 0 ? count / static_cast<double>(P.ns) : 0.0;
+      st->rmse = count > 0.0 ? sqrt(sums[28] / count) : 0.0;
+    }
+    return;
+  }
+  if (mode == kEquations) {
+    const int t2 = threadIdx.x;
+    if (t2 < 36) st->A[t2] = sym6(sums, t2 / 6, t2 % 6);
+    else if (t2 < 42) st->b[t2 - 36] = sums[21 + (t2 - 36)];
+    else if (t2 < 45) st->stats[t2 - 42] = sums[27 + (t2 - 42)];
+    else if (t2 == 45 && bad) st->nonfinite = 1;
+    return;
+  }
+  if (threadIdx.x >= 32) return;
+  if (bad || order_key(count) < order_key(P.kind == kPointToPoint ? 3.0 : 6.0)) {
+    if (threadIdx.x == 0) {
+      if (bad) st->nonfinite = 1;
+      else st->few_corr = 1;
+      st->done = 1;
+    }
+    return;
+  }
+  if (P.kind == kPointToPoint) solve_update_p2p(sums, st, P.eps, P.ctr[0], P.ctr[1], P.ctr[2]);
+  else solve_update(sums, st, P.eps);
+}
+
 
 // Point-to-point terms of one correspondence about the reference point c =
 // P.ctr (near the clouds, so the moments do not cancel): a = p - c, b = q - c,
@@ -1025,7 +1100,10 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
     }
   }
   if (mode == kCorrOnly) return;
-  double* const partial = P.partials + static_cast<size_t>(j) * kPartial;
+  // this tile's partial of every sum goes to accumulator row j % nacc, scaled by
+  // the bounds (nlen: the target normals' length bound)
+  unsigned long long* const acc = P.acc + static_cast<size_t>(j % P.nacc) * kPartial;
+  const float nlen = (P.kind == kPointToPlane && P.g.nrm) ? P.g.nrm[P.g.n].x : 0.f;
   if constexpr (F64) {
     // every term in float64 from the float32 p, q, n, each product and sum
     // rounded once in the oracle's order (no fused multiply-add)
@@ -1060,7 +1138,9 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
       v[28] = static_cast<double>(bd2);
       v[29] = 1.0;
     }
-    block_reduce_store_f64(v, partial);
+    double col = 0.0;
+    block_reduce_f64(v, col);
+    if (threadIdx.x < kPartial) add_fixed_f64(acc, threadIdx.x, col, sum_exponent(P, threadIdx.x, nlen));
   } else {
     // per-correspondence factors as one row per thread in shared memory (the
     // staged points are no longer needed), then the transposed reduction
@@ -1107,40 +1187,26 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
       }
     }
     __syncthreads();
-    block_reduce_rows(rows, P.kind, partial);
+    float ts = 0.f, tc = 0.f;
+    block_reduce_rows(rows, P.kind, ts, tc);
+    if (threadIdx.x < kPartial) add_fixed(acc, threadIdx.x, ts, tc, sum_exponent(P, threadIdx.x, nlen));
   }
-  // The last block of each group of kGroup blocks sums the group (float64, block
-  // order); the last group to finish sums the groups and finishes the launch.
+  // the last tile of the pair to arrive finishes the launch for the pair
   __shared__ bool last;
-  const int grp = j / kGroup;
-  const int ngroups = (P.ntiles + kGroup - 1) / kGroup;
-  const int in_group = min(kGroup, P.ntiles - grp * kGroup);
-  if (threadIdx.x < kPartial) __threadfence();  // the threads that stored the partial publish it
+  if (threadIdx.x < kPartial) __threadfence();  // the lanes that added the partial publish it
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&P.group_cnt[grp], 1u) == static_cast<unsigned>(in_group - 1);
+  if (threadIdx.x == 0) last = atomicAdd(&P.st->arrived, 1u) == static_cast<unsigned>(P.ntiles - 1);
   __syncthreads();
   if (!last) return;
   __threadfence();
-  __shared__ double gsum[kPartial];
-  sum_partials(P.partials, grp * kGroup, in_group, gsum);
-  if (threadIdx.x < kPartial) {
-    P.gsums[static_cast<size_t>(grp) * kPartial + threadIdx.x] = gsum[threadIdx.x];
-    __threadfence();
-  }
-  if (threadIdx.x == 0) P.group_cnt[grp] = 0u;
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&P.st->arrived, 1u) == static_cast<unsigned>(ngroups - 1);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  finish(P.gsums, ngroups, P.st, P.eps, mode, P.ns, P.kind, P.ctr[0], P.ctr[1], P.ctr[2]);
+  finish(P, mode, nlen);
 }
 
 // One ICP step of every pair: a persistent kernel whose blocks walk the global
 // tiles (tile, tile + gridDim.x, ...).  pairs == nullptr means the single pair
 // `one` owns every tile.  The pair of a tile comes from tile_pair.  Tiles of
-// different pairs are independent; each pair's partial sums sit in fixed per-tile
-// slots, so every pair's result is the same alone and in any batch.
+// different pairs are independent, and a pair's sums are exact integer sums of
+// its tiles' partials, so every pair's result is the same alone and in any batch.
 // F64 selects the all-float64 per-correspondence arithmetic (precision study);
 // Cfg the stage size and the blocks per SM the registers are budgeted for.
 template <bool F64, class Cfg>
@@ -1161,8 +1227,8 @@ __global__ void __launch_bounds__(kThreads, Cfg::kMinBlocks) k_icp_iter(PairDesc
   const int n = pairs ? *ntiles_total : one.ntiles;
   // Tiles [0, gridDim.x) go to the blocks in order; the rest are claimed one
   // at a time from queue[parity], so blocks that drew cheap tiles take more
-  // (results do not depend on which block runs a tile: each tile has its own
-  // partial slot).  queue[parity ^ 1] is the counter of the next launch on
+  // (results do not depend on which block runs a tile, nor on when it adds its
+  // partial).  queue[parity ^ 1] is the counter of the next launch on
   // this queue; the previous launch, which used it, has finished here.
   if (queue && blockIdx.x == 0 && threadIdx.x == 0) queue[parity ^ 1] = 0u;
   int tile = blockIdx.x;
@@ -1285,26 +1351,51 @@ int32_t check_src(const char* fn, const float* d_src, int64_t ns, int32_t stride
   return O3G_OK;
 }
 
+inline int accum_rows(int ntiles) { return ntiles < kAccRows ? (ntiles < 1 ? 1 : ntiles) : kAccRows; }
+
+// Points a pair's descriptor at its accumulator rows (accum_rows(P.ntiles) x
+// kPartial, zero) and sets the bounds its sums are scaled by, from the
+// target's coordinate box: point-to-plane, bnd_a >= |p| for every transformed
+// source point p within r of a target point (the box corner farthest from the
+// origin, plus r); point-to-point, bnd_a >= |p - c| and bnd_b >= |q - c| for
+// the reference point c = P.ctr.  Needs P.kind, P.ctr, P.r and P.ntiles.
+void set_sums(PairDesc& P, const o3g_grid* g, unsigned long long* acc) {
+  P.acc = acc;
+  P.nacc = accum_rows(P.ntiles);
+  const bool p2p = P.kind == kPointToPoint;
+  double far = 0.0;
+  for (int corner = 0; corner < 8; ++corner) {
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      const double x = ((corner >> a) & 1) ? g->box_hi[a] : g->box_lo[a];
+      const double d = x - (p2p ? static_cast<double>(P.ctr[a]) : 0.0);
+      d2 += d * d;
+    }
+    far = std::max(far, std::sqrt(d2));
+  }
+  // rounded up (the device adds a further 1% per factor)
+  P.bnd_a = static_cast<float>((far + static_cast<double>(P.r)) * 1.001 + 1e-30);
+  P.bnd_b = static_cast<float>(far * 1.001 + 1e-30);
+}
+
 // Everything one ICP-style call needs on the device: the cell-sorted source,
-// the iteration state and the block partials.
+// the iteration state and the fixed-point accumulators.
 struct Work {
   SortedCloud src;
   DevBuf state;
-  DevBuf partials;  // nblk block partials, then ngroups group sums
-  DevBuf counters;  // ngroups arrival counters
-  DevBuf hints;     // per source point: sorted target position of its last match, or -1
-  DevBuf queue;     // the dynamic tile queue (2 counters)
-  int nblk = 1, ngroups = 1;
+  DevBuf acc;    // accum_rows(nblk) x kPartial fixed-point sums
+  DevBuf hints;  // per source point: sorted target position of its last match, or -1
+  DevBuf queue;  // the dynamic tile queue (2 counters)
+  int nblk = 1;
   int launches = 0;  // launches so far (the queue parity)
-  explicit Work(cudaStream_t s) : src(s), state(s), partials(s), counters(s), hints(s), queue(s) {}
+  explicit Work(cudaStream_t s) : src(s), state(s), acc(s), hints(s), queue(s) {}
   int32_t prepare(const float* d_src, int64_t ns, int32_t stride, float cell, const double* T, cudaStream_t s) {
     O3G_TRY_STATUS(sort_cloud(d_src, ns, stride, s, &src));
     nblk = iter_blocks(ns);
-    ngroups = (nblk + kGroup - 1) / kGroup;
     O3G_TRY(state.alloc(sizeof(IcpState)));
-    O3G_TRY(partials.alloc(sizeof(double) * kPartial * (nblk + ngroups)));
-    O3G_TRY(counters.alloc(sizeof(unsigned) * ngroups));
-    O3G_TRY(cudaMemsetAsync(counters.p, 0, sizeof(unsigned) * ngroups, s));
+    const size_t acc_bytes = sizeof(unsigned long long) * kPartial * accum_rows(nblk);
+    O3G_TRY(acc.alloc(acc_bytes));
+    O3G_TRY(cudaMemsetAsync(acc.p, 0, acc_bytes, s));
     O3G_TRY(queue.alloc(sizeof(unsigned) * 2));
     O3G_TRY(cudaMemsetAsync(queue.p, 0, sizeof(unsigned) * 2, s));
     O3G_TRY(hints.alloc(sizeof(int32_t) * (ns > 0 ? ns : 1)));
@@ -1315,7 +1406,6 @@ struct Work {
   }
   int32_t launch(const o3g_grid* g, int ns, float r, double eps, int mode, int32_t* corr, float* d2,
                  cudaStream_t s, bool f64 = false, int kind = kPointToPlane, bool dependent = false) {
-    double* pp = partials.as<double>();
     PairDesc P;
     P.g = g->view();
     P.cell = g->cell;
@@ -1331,9 +1421,7 @@ struct Work {
     P.ntiles = nblk;
     P.tile0 = 0;
     P.st = state.as<IcpState>();
-    P.partials = pp;
-    P.gsums = pp + static_cast<size_t>(kPartial) * nblk;
-    P.group_cnt = counters.as<unsigned>();
+    set_sums(P, g, acc.as<unsigned long long>());
     P.hints = (mode == kIterate || mode == kEvaluate) ? hints.as<int32_t>() : nullptr;
     P.corr_out = corr;
     P.d2_out = d2;
@@ -1454,8 +1542,18 @@ extern "C" int32_t o3g_normal_equations_ex(const o3g_grid* g, const float* d_src
            precision == O3G_PREC_F64);
   O3G_TRY(cudaGetLastError());
   IcpState h;
+  int aux[8];
   O3G_TRY(cudaMemcpyAsync(&h, w.state.p, sizeof(IcpState), cudaMemcpyDeviceToHost, s));
+  O3G_TRY(cudaMemcpyAsync(aux, w.src.aux.p, sizeof(aux), cudaMemcpyDeviceToHost, s));
   O3G_TRY(cudaStreamSynchronize(s));
+  if (aux[6]) {
+    set_error("%s: non-finite source coordinate", fn);
+    return O3G_ERR_NONFINITE;
+  }
+  if (h.nonfinite) {
+    set_error("%s: a sum left its bound or was not finite (check the target normals)", fn);
+    return O3G_ERR_NONFINITE;
+  }
   for (int k = 0; k < 36; ++k) out_A[k] = h.A[k];
   for (int k = 0; k < 6; ++k) out_b[k] = h.b[k];
   for (int k = 0; k < 3; ++k) out_stats[k] = h.stats[k];
@@ -1525,16 +1623,12 @@ namespace o3g {
 namespace {
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
-constexpr int kNaMaxBlocks = (O3G_NOALLOC_MAX_POINTS + kThreads * kPPT - 1) / (kThreads * kPPT);
-constexpr int kNaMaxGroups = (kNaMaxBlocks + kGroup - 1) / kGroup;
 constexpr size_t kNaOffSrc = 0;
 constexpr size_t kNaOffState = align256(kNaOffSrc + sizeof(float4) * static_cast<size_t>(O3G_NOALLOC_MAX_POINTS));
-constexpr size_t kNaOffPartials = align256(kNaOffState + sizeof(IcpState));
-constexpr size_t kNaOffCounters =
-    align256(kNaOffPartials + sizeof(double) * kPartial * static_cast<size_t>(kNaMaxBlocks + kNaMaxGroups));
-constexpr size_t kNaOffFlag = align256(kNaOffCounters + sizeof(unsigned) * kNaMaxGroups);
+constexpr size_t kNaOffAcc = align256(kNaOffState + sizeof(IcpState));
+constexpr size_t kNaOffFlag = align256(kNaOffAcc + sizeof(unsigned long long) * kPartial * kAccRows);
 constexpr size_t kNaBytes = align256(kNaOffFlag + sizeof(int));
-static_assert(kNaBytes == 4736256, "update the size stated in o3g.h");
+static_assert(kNaBytes == 4203520, "update the size stated in o3g.h");
 
 // The working memory of o3g_icp_point_to_plane_grid_noalloc, shared by every call.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
@@ -1606,14 +1700,12 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float4* src4 = reinterpret_cast<float4*>(base + kNaOffSrc);
   IcpState* st = reinterpret_cast<IcpState*>(base + kNaOffState);
-  double* partials = reinterpret_cast<double*>(base + kNaOffPartials);
-  unsigned* counters = reinterpret_cast<unsigned*>(base + kNaOffCounters);
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(base + kNaOffAcc);
   int* bad = reinterpret_cast<int*>(base + kNaOffFlag);
   const int n = static_cast<int>(ns);
   const int nblk = iter_blocks(ns);
-  const int ngroups = (nblk + kGroup - 1) / kGroup;
-  // the arrival counters and the input flag must start at zero; the state is rewritten by k_init_state
-  O3G_TRY(cudaMemsetAsync(counters, 0, sizeof(unsigned) * ngroups, s));
+  // the accumulators and the input flag must start at zero; the state is rewritten by k_init_state
+  O3G_TRY(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * kPartial * accum_rows(nblk), s));
   O3G_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
   if (n > 0) {
     k_pack_src<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(d_src, n, stride, src4, bad);
@@ -1623,7 +1715,6 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const 
   count_launch();
   const float r = static_cast<float>(max_corr_dist);
   const GridView gv = g->view();
-  double* gsums = partials + static_cast<size_t>(kPartial) * nblk;
   for (int it = 0; it <= max_iter; ++it) {
     const int mode = it < max_iter ? kIterate : kEvaluate;
     PairDesc P;
@@ -1638,9 +1729,7 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const 
     P.ntiles = nblk;
     P.tile0 = 0;
     P.st = st;
-    P.partials = partials;
-    P.gsums = gsums;
-    P.group_cnt = counters;
+    set_sums(P, g, acc);
     P.hints = nullptr;
     P.corr_out = nullptr;
     P.d2_out = nullptr;
@@ -1755,8 +1844,8 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   }
   if (n_pairs == 0) return O3G_OK;
   std::vector<int64_t> off(n_pairs + 1, 0);
-  std::vector<int> ntiles(n_pairs), ngroups(n_pairs);
-  int64_t tiles_total = 0, groups_total = 0;
+  std::vector<int> ntiles(n_pairs);
+  int64_t tiles_total = 0, rows_total = 0;
   for (int p = 0; p < n_pairs; ++p) {
     if (!tgts[p] || !tgts[p]->has_normals || !(max_corr_dist[p] >= 0.0) || !std::isfinite(max_corr_dist[p])) {
       set_error("%s: pair %d: missing target grid, target normals or a valid max_corr_dist", fn, p);
@@ -1769,9 +1858,8 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
     }
     off[p + 1] = off[p] + ns[p];
     ntiles[p] = iter_blocks(ns[p]);
-    ngroups[p] = (ntiles[p] + kGroup - 1) / kGroup;
     tiles_total += ntiles[p];
-    groups_total += ngroups[p];
+    rows_total += accum_rows(ntiles[p]);
   }
   if (off[n_pairs] > 0x7fffffffLL - kThreads || tiles_total > 0x7fffffffLL) {
     set_error("%s: %lld source points in total exceed the supported size", fn, static_cast<long long>(off[n_pairs]));
@@ -1779,7 +1867,7 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t total = off[n_pairs];
-  DevBuf d_ptrs(s), d_strides(s), d_off(s), d_src4(s), d_aux(s), d_states(s), d_part(s), d_cnt(s), d_hints(s),
+  DevBuf d_ptrs(s), d_strides(s), d_off(s), d_src4(s), d_aux(s), d_states(s), d_acc(s), d_cnt(s), d_hints(s),
       d_descs(s), d_tiles(s), d_poses(s);
   O3G_TRY(d_ptrs.alloc(sizeof(float*) * n_pairs));
   O3G_TRY(d_strides.alloc(sizeof(int32_t) * n_pairs));
@@ -1787,8 +1875,8 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   O3G_TRY(d_src4.alloc(sizeof(float4) * (total > 0 ? total : 1)));
   O3G_TRY(d_aux.alloc(sizeof(int) * 8 * n_pairs));
   O3G_TRY(d_states.alloc(sizeof(IcpState) * n_pairs));
-  O3G_TRY(d_part.alloc(sizeof(double) * kPartial * (tiles_total + groups_total)));
-  O3G_TRY(d_cnt.alloc(sizeof(unsigned) * (groups_total + 2)));  // group counters, then the tile queue
+  O3G_TRY(d_acc.alloc(sizeof(unsigned long long) * kPartial * rows_total));
+  O3G_TRY(d_cnt.alloc(sizeof(unsigned) * 2));  // the tile queue
   O3G_TRY(d_hints.alloc(sizeof(int32_t) * (total > 0 ? total : 1)));
   O3G_TRY(d_descs.alloc(sizeof(PairDesc) * n_pairs));
   O3G_TRY(d_tiles.alloc(sizeof(int) * (tiles_total + 1)));
@@ -1797,9 +1885,8 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   std::vector<PairDesc> descs(n_pairs);
   std::vector<int> tile_pair(tiles_total + 1);
   IcpState* states = d_states.as<IcpState>();
-  double* part = d_part.as<double>();
-  unsigned* cnt = d_cnt.as<unsigned>();
-  int64_t t0 = 0, g0 = 0;
+  unsigned long long* acc = d_acc.as<unsigned long long>();
+  int64_t t0 = 0, a0 = 0;
   for (int p = 0; p < n_pairs; ++p) {
     PairDesc& P = descs[p];
     P.g = tgts[p]->view();
@@ -1813,15 +1900,13 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
     P.ntiles = ntiles[p];
     P.tile0 = static_cast<int>(t0);
     P.st = states + p;
-    P.partials = part + static_cast<size_t>(kPartial) * t0;
-    P.gsums = part + static_cast<size_t>(kPartial) * (tiles_total + g0);
-    P.group_cnt = cnt + g0;
+    set_sums(P, tgts[p], acc + static_cast<size_t>(kPartial) * a0);
     P.hints = d_hints.as<int32_t>() + off[p];
     P.corr_out = nullptr;
     P.d2_out = nullptr;
     for (int k = 0; k < ntiles[p]; ++k) tile_pair[t0 + k] = p;
     t0 += ntiles[p];
-    g0 += ngroups[p];
+    a0 += P.nacc;
   }
   tile_pair[tiles_total] = static_cast<int>(tiles_total);  // read by the kernel as the tile count
   std::vector<int32_t> h_strides(strides, strides + n_pairs);
@@ -1831,7 +1916,8 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   O3G_TRY(cudaMemcpyAsync(d_descs.p, descs.data(), sizeof(PairDesc) * n_pairs, cudaMemcpyHostToDevice, s));
   O3G_TRY(cudaMemcpyAsync(d_tiles.p, tile_pair.data(), sizeof(int) * (tiles_total + 1), cudaMemcpyHostToDevice, s));
   O3G_TRY(cudaMemcpyAsync(d_poses.p, init_T, sizeof(double) * 16 * n_pairs, cudaMemcpyHostToDevice, s));
-  O3G_TRY(cudaMemsetAsync(d_cnt.p, 0, sizeof(unsigned) * (groups_total + 2), s));
+  O3G_TRY(cudaMemsetAsync(d_cnt.p, 0, sizeof(unsigned) * 2, s));
+  O3G_TRY(cudaMemsetAsync(d_acc.p, 0, sizeof(unsigned long long) * kPartial * rows_total, s));
   O3G_TRY(cudaMemsetAsync(d_hints.p, 0xff, sizeof(int32_t) * (total > 0 ? total : 1), s));
   O3G_TRY_STATUS(sort_clouds_batch(reinterpret_cast<const float* const*>(d_ptrs.p), d_strides.as<int32_t>(),
                                    d_off.as<int64_t>(), n_pairs, total, s, d_src4.as<float4>(), d_aux.as<int>()));
@@ -1840,8 +1926,7 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   {
     TimedRegion tr(O3G_KERNEL_ICP_BATCH, s);
     O3G_TRY_STATUS(run_iterations(d_descs.as<PairDesc>(), d_tiles.as<int>(), d_tiles.as<int>() + tiles_total,
-                                  static_cast<int>(tiles_total), max_iter, eps, d_cnt.as<unsigned>() + groups_total,
-                                  s));
+                                  static_cast<int>(tiles_total), max_iter, eps, d_cnt.as<unsigned>(), s));
   }
   std::vector<IcpState> h(n_pairs);
   std::vector<int> aux(8 * n_pairs);
@@ -1888,9 +1973,8 @@ struct o3g_server {
     float4* src4 = nullptr;
     int* src_aux = nullptr;
     int32_t* hints = nullptr;
-    double* partials = nullptr;  // ntiles block partials, then ngroups group sums
-    unsigned* counters = nullptr;
-    int ns = 0, ntiles = 1, ngroups = 1;
+    unsigned long long* acc = nullptr;  // accum_rows(ntiles) x kPartial fixed-point sums
+    int ns = 0, ntiles = 1;
     int max_iter = 0;
     double eps = 0.0;
     float r = 0.f;
@@ -1924,9 +2008,9 @@ namespace {
 
 // Device memory a request will hold while admitted (upper bound before its grid exists).
 int64_t request_bytes(int64_t ns, int64_t nt) {
-  const int64_t tiles = iter_blocks(ns), groups = (tiles + kGroup - 1) / kGroup;
-  return ns * (16 + 4 + 12) + tiles * kPartial * 8 + groups * (kPartial * 8 + 4) + nt * (16 + 16 + 4 + 12 + 12) +
-         4 * (32 * nt + (1 << 20)) + sizeof(IcpState);
+  const int64_t rows = accum_rows(iter_blocks(ns));
+  return ns * (16 + 4 + 12) + rows * kPartial * 8 + nt * (16 + 16 + 4 + 12 + 12) + 4 * (32 * nt + (1 << 20)) +
+         sizeof(IcpState);
 }
 
 void release_slot(o3g_server* sv, o3g_server::Slot& sl) {
@@ -1934,8 +2018,7 @@ void release_slot(o3g_server* sv, o3g_server::Slot& sl) {
   dfree(sl.src4, sv->s);
   dfree(sl.src_aux, sv->s);
   dfree(sl.hints, sv->s);
-  dfree(sl.partials, sv->s);
-  dfree(sl.counters, sv->s);
+  dfree(sl.acc, sv->s);
   sv->used -= sl.bytes;
   sl = o3g_server::Slot();
 }
@@ -1949,7 +2032,6 @@ int32_t admit(o3g_server* sv, int k, o3g_server::Request& rq) {
   sl.id = rq.id;
   sl.ns = static_cast<int>(ns);
   sl.ntiles = iter_blocks(ns);
-  sl.ngroups = (sl.ntiles + kGroup - 1) / kGroup;
   sl.max_iter = rq.max_iter;
   sl.eps = rq.eps;
   sl.r = static_cast<float>(rq.r);
@@ -1976,9 +2058,9 @@ int32_t admit(o3g_server* sv, int k, o3g_server::Request& rq) {
   sc.aux.p = nullptr;
   O3G_TRY(dmalloc(reinterpret_cast<void**>(&sl.hints), sizeof(int32_t) * (ns > 0 ? ns : 1), s));
   O3G_TRY(cudaMemsetAsync(sl.hints, 0xff, sizeof(int32_t) * (ns > 0 ? ns : 1), s));
-  O3G_TRY(dmalloc(reinterpret_cast<void**>(&sl.partials), sizeof(double) * kPartial * (sl.ntiles + sl.ngroups), s));
-  O3G_TRY(dmalloc(reinterpret_cast<void**>(&sl.counters), sizeof(unsigned) * sl.ngroups, s));
-  O3G_TRY(cudaMemsetAsync(sl.counters, 0, sizeof(unsigned) * sl.ngroups, s));
+  const size_t acc_bytes = sizeof(unsigned long long) * kPartial * accum_rows(sl.ntiles);
+  O3G_TRY(dmalloc(reinterpret_cast<void**>(&sl.acc), acc_bytes, s));
+  O3G_TRY(cudaMemsetAsync(sl.acc, 0, acc_bytes, s));
   k_init_state<<<1, 32, 0, s>>>(static_cast<IcpState*>(sv->states) + k, to_pose(rq.T0));
   count_launch();
   O3G_TRY(cudaGetLastError());
@@ -2001,9 +2083,7 @@ PairDesc slot_desc(o3g_server* sv, int k, int tile0) {
   P.ntiles = sl.ntiles;
   P.tile0 = tile0;
   P.st = static_cast<IcpState*>(sv->states) + k;
-  P.partials = sl.partials;
-  P.gsums = sl.partials + static_cast<size_t>(kPartial) * sl.ntiles;
-  P.group_cnt = sl.counters;
+  set_sums(P, sl.grid, sl.acc);
   P.hints = sl.hints;
   P.corr_out = nullptr;
   P.d2_out = nullptr;
@@ -2041,6 +2121,11 @@ int32_t launch_slots(o3g_server* sv, const std::vector<int>& ks, int mode) {
 
 }  // namespace
 }  // namespace o3g
+
+extern "C" int64_t o3g_server_request_bytes(int64_t ns, int64_t nt) {
+  if (ns < 0 || nt < 0 || ns > 0x7fffffffLL || nt > 0x7fffffffLL) return -1;
+  return o3g::request_bytes(ns, nt);
+}
 
 extern "C" int32_t o3g_server_create(int32_t max_active, int64_t hbm_budget_bytes, void* stream, o3g_server** out) {
   using namespace o3g;

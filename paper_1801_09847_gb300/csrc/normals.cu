@@ -322,6 +322,7 @@ __global__ void __launch_bounds__(kThreads) k_normals_warp(GridView g, const int
   __shared__ uint64_t stage_all[kWarpsPerBlock][64];
   const int warp = threadIdx.x >> 5;
   const int k = blockIdx.x * kWarpsPerBlock + warp;
+  if (k == 0 && threadIdx.x == 0) nrm_sorted[g.n] = make_float4(1.f, 0.f, 0.f, 0.f);  // length bound: unit normals
   if (k >= g.n) return;
   warp_normal(g, pos_of, k, radius, max_nn, vx, vy, vz, nrm_sorted, out, out_stride, stage_all[warp]);
 }
@@ -366,6 +367,7 @@ __global__ void __launch_bounds__(kThreads) k_normals_batch(const NormalsJob* __
   const NormalsJob& J = jobs[j];
   const int k = static_cast<int>(w - first[j]);
   if (k >= J.n) return;
+  if (k == 0 && (threadIdx.x & 31) == 0) J.nrm_sorted[J.n] = make_float4(1.f, 0.f, 0.f, 0.f);  // length bound
   warp_normal(J.g, J.pos_of, k, J.radius, max_nn, J.vx, J.vy, J.vz, J.nrm_sorted, J.out, J.stride,
               stage_all[warp]);
 }
@@ -417,6 +419,7 @@ __global__ void __launch_bounds__(kThreads) k_normals(GridView g, float radius, 
                                                       float vz, float4* __restrict__ nrm_sorted,
                                                       float* __restrict__ out, int out_stride) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == 0) nrm_sorted[g.n] = make_float4(1.f, 0.f, 0.f, 0.f);  // length bound: unit normals
   if (k >= g.n) return;
   uint64_t keys[KMAX];
   int pos[KMAX];

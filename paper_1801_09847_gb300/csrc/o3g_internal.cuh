@@ -89,7 +89,7 @@ int32_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* tmp_k, uint32
 // (z fastest), and cell_start[c] = number of points whose cell index is < c.
 struct GridView {
   const float4* pts;         // sorted points; .w holds the original index (int bits)
-  const float4* nrm;         // sorted normals (.w = 0), or null
+  const float4* nrm;         // sorted normals (.w = 0), or null; nrm[n].x bounds their length
   const uint32_t* cell_start;  // cells + 1 entries
   const uint32_t* col_z;     // per (x, y) column: lowest | highest occupied z cell << 16 (empty: 0xffff)
   int lo_x, lo_y, lo_z;      // smallest occupied cell coordinate per axis
@@ -174,9 +174,11 @@ struct o3g_grid {
   float cell = 0.f, inv_cell = 0.f;
   int lo[3] = {0, 0, 0};
   int span[3] = {1, 1, 1};
+  float box_lo[3] = {0.f, 0.f, 0.f};  // coordinate bounding box of the points
+  float box_hi[3] = {0.f, 0.f, 0.f};
   int64_t cells = 1;
   float4* pts = nullptr;
-  float4* nrm = nullptr;
+  float4* nrm = nullptr;  // n + 1 entries: the sorted normals, then (length bound, 0, 0, 0)
   uint32_t* cell_start = nullptr;
   uint32_t* col_z = nullptr;  // per column: lowest | highest occupied z cell << 16
   int32_t* pos_of = nullptr;  // original index -> sorted position

@@ -73,6 +73,7 @@ _SIGNATURES = {
     "o3g_icp_point_to_plane_batch": ([_i32, _vp, _vp, _vp, _vp, _f64p, _f64p, _i32, _f64, _f64p, _f64p, _f64p, _i32p,
                                       _i32p, _vp], _i32),
     "o3g_server_create": ([_i32, _i64, _vp, ctypes.POINTER(_vp)], _i32),
+    "o3g_server_request_bytes": ([_i64, _i64], _i64),
     "o3g_server_destroy": ([_vp], _i32),
     "o3g_server_submit": ([_vp, _vp, _i64, _vp, _i64, _vp, _f32, _i32, _f64p, _f64, _i32, _f64,
                            ctypes.POINTER(_i64)], _i32),
@@ -461,6 +462,14 @@ def icp_point_to_plane_batch(grids, srcs, init_Ts, max_corr_dists, max_iter: int
 
 class Server:
     """Continuous-batching registration server (o3g_server_*): submit, step, poll."""
+
+    @staticmethod
+    def request_bytes(ns: int, nt: int) -> int:
+        """Device-memory estimate a request of ns source / nt target points is admitted against."""
+        v = int(lib().o3g_server_request_bytes(int(ns), int(nt)))
+        if v < 0:
+            raise O3GError(ERR_ARG, "o3g_server_request_bytes", "negative or oversized cloud size")
+        return v
 
     def __init__(self, max_active: int = 64, hbm_budget_bytes: int = 8 << 30, stream=None):
         h = _vp()

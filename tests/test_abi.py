@@ -86,3 +86,16 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(o3g, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         o3g.lib()
+
+
+def test_server_request_bytes_is_host_only_and_monotone(L):
+    """The server's admission estimate needs no device: positive, growing with either cloud, -1 for bad sizes."""
+    from paper_1801_09847_gb300 import o3g
+    L.o3g_server_request_bytes.restype = ctypes.c_int64
+    L.o3g_server_request_bytes.argtypes = [ctypes.c_int64, ctypes.c_int64]
+    base = L.o3g_server_request_bytes(1000, 2000)
+    assert base > 0
+    assert L.o3g_server_request_bytes(5000, 2000) > base and L.o3g_server_request_bytes(1000, 9000) > base
+    assert L.o3g_server_request_bytes(0, 0) > 0
+    assert L.o3g_server_request_bytes(-1, 10) == -1 and L.o3g_server_request_bytes(10, -1) == -1
+    assert o3g.Server.request_bytes(1000, 2000) == base

@@ -321,6 +321,45 @@ def test_normal_equations_sign_invariance(o3g):
     assert np.array_equal(A1, A2) and np.array_equal(b1, b2)
 
 
+@pytest.mark.parametrize("scale,offset", [(7.3, 0.0), (1e-3, 0.0), (1.0, 1000.0), (2.5, -40000.0)])
+def test_normal_equations_scaled_normals_and_far_clouds(o3g, scale, offset):
+    """The sums are accumulated in fixed point scaled by the target's coordinate box and the normals'
+    length bound: normals that are not unit vectors and clouds far from the origin meet the oracle at
+    the same bars (a bound taken too small would report non-finite sums)."""
+    pr = synth.sphere_plane_pair(n=4000)
+    tgt = (pr.tgt.astype(np.float64) + offset).astype(np.float32)
+    src = (pr.src.astype(np.float64) + offset).astype(np.float32)
+    nrm = (pr.tgt_nrm.astype(np.float64) * scale).astype(np.float32)
+    r = pr.max_corr_dist
+    grid = o3g.build_grid(cuda(tgt), r)
+    grid.set_normals(cuda(nrm))
+    shift = synth.make_T(np.eye(3), [0.004, -0.003, 0.002])
+    for T in [np.eye(4), shift]:
+        A, b, stats = o3g.normal_equations(grid, cuda(src), T, r)
+        A_ref, b_ref, st_ref, scale_b = oracle_equations(src, tgt, nrm, T, r)
+        assert st_ref[2] > 100
+        ea, eb = rel_errors(A, b, A_ref, b_ref, scale_b)
+        assert ea <= 1e-5 and eb <= 1e-5, (ea, eb)
+        assert stats[2] == st_ref[2]
+        assert stats[1] == pytest.approx(st_ref[1], rel=1e-5)
+
+
+def test_nonfinite_normal_reported(o3g):
+    """A NaN target normal that a correspondence uses makes the sums non-finite: both the normal
+    equations and ICP report O3G_ERR_NONFINITE instead of returning a result."""
+    pr = synth.sphere_plane_pair(n=2000)
+    nrm = pr.tgt_nrm.copy()
+    nrm[::50] = np.nan
+    grid = o3g.build_grid(cuda(pr.tgt), pr.max_corr_dist)
+    grid.set_normals(cuda(nrm))
+    with pytest.raises(o3g.O3GError) as e:
+        o3g.normal_equations(grid, cuda(pr.src), np.eye(4), pr.max_corr_dist)
+    assert e.value.status == o3g.ERR_NONFINITE
+    with pytest.raises(o3g.O3GError) as e:
+        o3g.icp_point_to_plane_grid(grid, cuda(pr.src), np.eye(4), pr.max_corr_dist, 5)
+    assert e.value.status == o3g.ERR_NONFINITE
+
+
 # ------------------------------------------------------------------- ICP
 
 

