@@ -446,14 +446,27 @@ __device__ void block_reduce_rows(const float* __restrict__ rows, int kind, floa
   const uchar4 ix = *reinterpret_cast<const uchar4*>(kTerm[kind][k]);
   float s = 0.f, c = 0.f;
   const float* r = rows + quarter * 32 * kRow;
+  if (kind == kPointToPlane) {
+    // no low parts (their slots hold zeros): the same sums without reading them
 #pragma unroll 4
-  for (int j = 0; j < 32; ++j, r += kRow) {
-    const float x = r[ix.x], y = r[ix.y], xl = r[ix.z], yl = r[ix.w];
-    const float hi = __fmul_rn(x, y);
-    const float lo = fmaf(x, y, -hi) + fmaf(x, yl, xl * y);
-    float e;
-    two_sum(s, hi, s, e);
-    c += lo + e;
+    for (int j = 0; j < 32; ++j, r += kRow) {
+      const float x = r[ix.x], y = r[ix.y];
+      const float hi = __fmul_rn(x, y);
+      const float lo = fmaf(x, y, -hi);
+      float e;
+      two_sum(s, hi, s, e);
+      c += lo + e;
+    }
+  } else {
+#pragma unroll 4
+    for (int j = 0; j < 32; ++j, r += kRow) {
+      const float x = r[ix.x], y = r[ix.y], xl = r[ix.z], yl = r[ix.w];
+      const float hi = __fmul_rn(x, y);
+      const float lo = fmaf(x, y, -hi) + fmaf(x, yl, xl * y);
+      float e;
+      two_sum(s, hi, s, e);
+      c += lo + e;
+    }
   }
   qs[quarter][k] = s;
   qc[quarter][k] = c;
