@@ -667,51 +667,16 @@ __device__ void solve_update(const double* sums, IcpState* __restrict__ st, doub
   }
 }
 
-// Largest root of x^4 + c2 x^2 + c1 x + c0 (the characteristic polynomial of a
-// trace-free symmetric 4x4 scaled so that every eigenvalue lies in [-1, 1]),
-// by Newton's method from x = 1.  To the right of its largest root the quartic
-// is increasing and convex (the roots of its derivatives interlace its own), so
-// the iterates fall monotonically onto the root: float32 steps first, then
-// float64 steps until the step is below 1e-15 (at most 64 of each).
-__device__ double quartic_top_root(double c2, double c1, double c0) {
-  const float f2 = static_cast<float>(c2), f1 = static_cast<float>(c1), f0 = static_cast<float>(c0);
-  float xf = 1.0f;
-  for (int k = 0; k < 64; ++k) {
-    const float x2 = xf * xf;
-    const float f = (x2 + f2) * x2 + (f1 * xf + f0);
-    const float d = (4.0f * x2 + 2.0f * f2) * xf + f1;
-    if (!(f > 0.0f) || !(d > 0.0f)) break;
-    const float nx = xf - f / d;
-    if (!(nx < xf)) break;
-    xf = nx;
-  }
-  double x = xf;
-  for (int k = 0; k < 64; ++k) {
-    const double x2 = x * x;
-    const double f = fma(x2 + c2, x2, fma(c1, x, c0));
-    const double d = fma(fma(4.0, x2, 2.0 * c2), x, c1);
-    if (!(d > 1e-300)) break;
-    const double step = f * recip(d);
-    x -= step;
-    if (!(fabs(step) > 1e-15)) break;
-  }
-  return x;
+// Helpers of the serial float64 code: 2^k (|k| < 1023), the biased exponent of
+// a double, and a float32 reciprocal (rcp.approx) of a double.
+__device__ __forceinline__ double pow2(int k) { return __longlong_as_double(static_cast<long long>(1023 + k) << 52); }
+__device__ __forceinline__ int bexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+__device__ __forceinline__ float rcp_f(double d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(__double2float_rn(d)));
+  return r;
 }
 
-// Largest root of x^3 + a2 x^2 + a1 x + a0 below x0 (the quartic above with
-// its top root x0 divided out), by the same Newton iteration from x0.
-__device__ double cubic_top_root(double a2, double a1, double a0, double x0) {
-  double x = x0;
-  for (int k = 0; k < 64; ++k) {
-    const double f = fma(fma(x + a2, x, a1), x, a0);
-    const double d = fma(fma(3.0, x, 2.0 * a2), x, a1);
-    if (!(d > 1e-300)) break;
-    const double step = f * recip(d);
-    x -= step;
-    if (!(fabs(step) > 1e-15)) break;
-  }
-  return x;
-}
 
 // Point-to-point update on one warp in float64 (TransformationEstimationPointToPoint,
 // Sec. 3.3): the rigid motion minimising sum |R p + t - q|^2 over the matched
@@ -719,75 +684,79 @@ __device__ double cubic_top_root(double a2, double a1, double a0, double x0) {
 // moments of a = p - c and b = q - c for a fixed reference point c near the
 // clouds (sums 0-2: a, 3-5: b, 6-14: a b^T row-major, 15: |a|^2, 16: |b|^2),
 // from which the centred cross-covariance S and E0 = (sum|a - mean a|^2 +
-// sum|b - mean b|^2) / 2 follow.  Horn's trace-free symmetric N (built from S)
-// is scaled by 1 / |N|_F, which puts every eigenvalue in [-1, 1]; its largest
-// eigenvalue comes from the characteristic quartic (Newton, as in the QCP method
-// of Theobald, Acta Cryst. A 61, 2005), the second largest from the deflated
-// cubic.  A gap below 1e-6 E0 (E0 bounds every eigenvalue's magnitude) leaves
-// the rotation undetermined: R = I, the degenerate flag is set.  (Newton on a
+// sum|b - mean b|^2) / 2 follow.  Horn's trace-free symmetric N (built from S,
+// one entry per lane) is scaled by 2^-e with 2^e >= |N|_F, which puts every
+// eigenvalue in [-1, 1] and is exact; its largest eigenvalue comes from the
+// characteristic quartic x^4 + c2 x^2 + c1 x + c0 (c2 = -tr(N^2)/2,
+// c1 = -tr(N^3)/3, c0 = det N) by Newton's method from x = 1, as in the QCP
+// method of Theobald (Acta Cryst. A 61, 2005): to the right of its largest
+// root the quartic is increasing and convex (the roots of its derivatives
+// interlace its own), so the iterates fall monotonically onto the root; float32
+// steps first, then float64 steps with a float32 reciprocal of the slope
+// (each contracts the error by about 2^-22) until the step is below 2^-50 of the
+// root.  The second largest eigenvalue comes from the deflated cubic the same
+// way.  A gap below 1e-6 E0 (E0 bounds every eigenvalue's magnitude) leaves the
+// rotation undetermined: R = I, the degenerate flag is set.  (Newton on a
 // double root stops about 1e-8 from it, so a threshold near the float64
 // rounding level would miss exact degeneracy; float32 inputs cannot fix a
-// rotation with a smaller gap anyway.)  Otherwise the
-// quaternion is the column of adj(N - lambda I) whose diagonal entry has the
-// largest magnitude (for a simple eigenvalue adj is a multiple of v v^T),
-// normalised with w >= 0.
-// t = mean q - R mean p;  T <- [R t; 0 1] T;  done when max(angle, |t|) < eps.
-__device__ void solve_update_p2p(const double* sums, IcpState* __restrict__ st, double eps, float cx, float cy,
-                                 float cz) {
-  // the 3x3 and 4x4 matrices live in shared memory and each lane handles one
-  // entry, which keeps the register footprint of the kernel that runs this low
+// rotation with a smaller gap anyway.)  Otherwise the quaternion q is the
+// column of adj(N - lambda I) whose diagonal entry has the largest magnitude
+// (for a simple eigenvalue adj is a multiple of v v^T), and dR is the rotation
+// of q / |q| formed directly from q and 1 / |q|^2 (the same for q and -q).
+// t = mean q - dR mean p;  T <- [dR t; 0 1] T;  done when the rotation angle
+// and |t| are below eps, the angle tested as |q_xyz|^2 < tan^2(eps/2) q_w^2.
+// Few float64 instructions: comparisons on integer bit patterns, exact
+// power-of-two scalings, no division or square root.
+__device__ void solve_update_p2p(const double* sums, IcpState* __restrict__ st, double eps, double eps_tan2,
+                                 float cx, float cy, float cz) {
   __shared__ double sS[9], sN[16], sM[16];
+  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  const double Tpre = lane < 12 ? st->T[lane] : 0.0;
   const double n = sums[29];
   const double inv_n = recip(n);
-  if (lane < 9) {
-    const int i = lane / 3, j = lane % 3;
-    sS[lane] = fma(-n * (sums[i] * inv_n), sums[3 + j] * inv_n, sums[6 + lane]);
-  }
-  __syncwarp();
-  double gp = sums[15], gq = sums[16];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    gp = fma(-n * (sums[k] * inv_n), sums[k] * inv_n, gp);
-    gq = fma(-n * (sums[3 + k] * inv_n), sums[3 + k] * inv_n, gq);
-  }
-  const double E0 = 0.5 * (gp + gq);
-  if (lane < 16) {
-    // Horn's N from S (rows x, y, z of S index the source, columns the target)
-    const double Sxx = sS[0], Sxy = sS[1], Sxz = sS[2], Syx = sS[3], Syy = sS[4], Syz = sS[5], Szx = sS[6],
-                 Szy = sS[7], Szz = sS[8];
-    double v;
-    switch (lane) {
-      case 0: v = Sxx + Syy + Szz; break;
-      case 1: case 4: v = Syz - Szy; break;
-      case 2: case 8: v = Szx - Sxz; break;
-      case 3: case 12: v = Sxy - Syx; break;
-      case 5: v = Sxx - Syy - Szz; break;
-      case 6: case 9: v = Sxy + Syx; break;
-      case 7: case 13: v = Szx + Sxz; break;
-      case 10: v = -Sxx + Syy - Szz; break;
-      case 11: case 14: v = Syz + Szy; break;
-      default: v = -Sxx - Syy + Szz; break;
-    }
-    sN[lane] = v;
-  }
-  __syncwarp();
-  double w = 1.0, x = 0.0, y = 0.0, z = 0.0;
-  bool degenerate = true;
+  // means of a (lanes 0..2) and b (lanes 3..5), and n times them
+  const double mk = lane < 6 ? sums[lane] * inv_n : 0.0;
+  const double nm = n * mk;
   {
-    // characteristic polynomial x^4 + c2 x^2 + c1 x + c0 of the trace-free N
-    // scaled by 1 / |N|_F (so every eigenvalue lies in [-1, 1]):
-    // c2 = -tr(N^2) / 2, c1 = -tr(N^3) / 3, c0 = det N (Laplace expansion along
-    // rows 0, 1: lane k < 6 takes column pair k), each times the scale's power
-    double t2 = 0.0, t3 = 0.0, dt = 0.0;
-    if (lane < 16) {
-      const int i = lane >> 2, j = lane & 3;
-      double n2 = 0.0;
+    const int i = lane < 9 ? lane / 3 : 0, j = lane < 9 ? lane % 3 : 0;
+    const double s = fma(-shfl_d(nm, i), shfl_d(mk, 3 + j), sums[6 + (lane < 9 ? lane : 0)]);
+    if (lane < 9) sS[lane] = s;
+  }
+  // E0 = (sum |a - mean a|^2 + sum |b - mean b|^2) / 2
+  double e0;
+  {
+    double q = lane < 6 ? nm * mk : 0.0;
+    q += __shfl_xor_sync(full, q, 1);
+    q += __shfl_xor_sync(full, q, 2);
+    q += __shfl_xor_sync(full, q, 4);
+    e0 = 0.5 * ((sums[15] + sums[16]) - shfl_d(q, 0));
+  }
+  __syncwarp();
+  if (lane < 16) {
+    // Horn's N, entry (i, j) on lane 4 i + j as (s1 S[k1] + s2 S[k2]) + s3 S[k3], S index 3 row + col
+    const int k1 = static_cast<int>((0x0561501661051650ULL >> (4 * lane)) & 15);
+    const int k2 = static_cast<int>((0x4723743223473274ULL >> (4 * lane)) & 15);
+    const unsigned neg1 = 0x8400u, neg2 = 0x913Eu, neg3 = 0x0420u, has3 = 0x8421u;
+    const int k3 = 8;
+    double a = sS[k1], b = sS[k2], c = sS[k3];
+    if ((neg1 >> lane) & 1u) a = -a;
+    if ((neg2 >> lane) & 1u) b = -b;
+    if ((neg3 >> lane) & 1u) c = -c;
+    const double ab = a + b;
+    const double v = ab + c;
+    sN[lane] = ((has3 >> lane) & 1u) ? v : ab;
+  }
+  __syncwarp();
+  // tr(N^2) on lanes 0..15 and tr(N^3) on lanes 16..31 of one register; det N (Laplace along rows 0, 1,
+  // lane k < 6 takes column pair k) on another
+  double r1, r2 = 0.0;
+  {
+    const int h = lane & 15, i = h >> 2, j = h & 3;
+    double n2 = 0.0;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) n2 = fma(sN[4 * i + k], sN[4 * k + j], n2);
-      t2 = sN[lane] * sN[lane];
-      t3 = n2 * sN[4 * j + i];
-    }
+    for (int k = 0; k < 4; ++k) n2 = fma(sN[4 * i + k], sN[4 * k + j], n2);
+    r1 = (lane < 16 ? sN[h] : n2) * sN[lane < 16 ? h : 4 * j + i];
     if (lane < 6) {
       const int a = lane < 3 ? 0 : (lane < 5 ? 1 : 2);
       const int b = lane < 3 ? lane + 1 : (lane < 5 ? lane - 1 : 3);
@@ -795,104 +764,149 @@ __device__ void solve_update_p2p(const double* sums, IcpState* __restrict__ st, 
       const int d = 6 - a - b - c;
       const double top = sN[a] * sN[4 + b] - sN[b] * sN[4 + a];
       const double bot = sN[8 + c] * sN[12 + d] - sN[8 + d] * sN[12 + c];
-      dt = ((1 + a + b) & 1) ? -top * bot : top * bot;
+      r2 = ((1 + a + b) & 1) ? -top * bot : top * bot;
     }
+  }
 #pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-      t2 += __shfl_xor_sync(0xffffffffu, t2, off);
-      t3 += __shfl_xor_sync(0xffffffffu, t3, off);
-      dt += __shfl_xor_sync(0xffffffffu, dt, off);
+  for (int off = 8; off >= 1; off >>= 1) r1 += __shfl_xor_sync(full, r1, off);
+#pragma unroll
+  for (int off = 4; off >= 1; off >>= 1) r2 += __shfl_xor_sync(full, r2, off);
+  const double t2 = shfl_d(r1, 0), t3 = shfl_d(r1, 16), dt = shfl_d(r2, 0);
+  double w = 1.0, x = 0.0, y = 0.0, z = 0.0;
+  bool degenerate = true;
+  const int et = bexp(t2);
+  if (et > 0 && et < 0x7ff && order_key(e0) > 0) {
+    // scale N by 2^-e with 2^e >= |N|_F: every eigenvalue in [-1, 1], and the scaling is exact
+    const int e = (et - 1022 + 1) >> 1;
+    const double c2 = t2 * -pow2(-2 * e - 1);
+    const double c1 = (t3 * (-pow2(-2 * e) * (1.0 / 3.0))) * pow2(-e);  // = -t3 2^-3e / 3, no division
+    const double c0 = (dt * pow2(-2 * e)) * pow2(-2 * e);
+    // largest root of x^4 + c2 x^2 + c1 x + c0 by Newton from 1: float32 to convergence, then float64
+    // steps with the float32 reciprocal of the slope (each contracts the error by 2^-22 or better)
+    float xf = 1.0f;
+    {
+      const float f2 = static_cast<float>(c2), f1 = static_cast<float>(c1), f0 = static_cast<float>(c0);
+      for (int k = 0; k < 64; ++k) {
+        const float x2 = xf * xf;
+        const float f = (x2 + f2) * x2 + (f1 * xf + f0);
+        const float d = (4.0f * x2 + 2.0f * f2) * xf + f1;
+        if (!(f > 0.0f) || !(d > 0.0f)) break;
+        const float nx = xf - f / d;
+        if (!(nx < xf)) break;
+        xf = nx;
+      }
     }
-    // every lane now holds the same bits (each butterfly step adds the same two
-    // partial sums in swapped order, and addition commutes), so the root
-    // iterations and the branches below are warp-uniform
-    const double nf = sqrt(t2);
-    if (nf > 0.0 && E0 > 0.0) {
-      const double sc = 1.0 / nf, sc2 = sc * sc;
-      const double c2 = -0.5, c1 = -t3 / 3.0 * (sc2 * sc), c0 = dt * (sc2 * sc2);
-      const double l1 = quartic_top_root(c2, c1, c0);
-      const double a1 = fma(l1, l1, c2);
-      const double l2 = cubic_top_root(l1, a1, fma(l1, a1, c1), l1);
-      degenerate = !(l1 - l2 > 1e-6 * E0 * sc);
-      if (!degenerate && lane < 16) sM[lane] = sN[lane] * sc - ((lane % 5 == 0) ? l1 : 0.0);
+    double l1 = xf;
+    const double two_c2 = c2 + c2;
+    for (int k = 0; k < 8; ++k) {
+      const double x2 = l1 * l1;
+      const double f = fma(x2 + c2, x2, fma(c1, l1, c0));
+      const double d = fma(fma(4.0, x2, two_c2), l1, c1);
+      const float rd = rcp_f(d);
+      if (!(rd > 0.0f && rd < 3.0e38f)) break;
+      const double step = f * static_cast<double>(rd);
+      l1 -= step;
+      if (step == 0.0 || bexp(step) + 50 < max(bexp(l1), 1023 - 20)) break;
     }
+    // second root from the deflated cubic x^3 + l1 x^2 + a1 x + a0: float32 Newton from l1, one float64 step
+    const double a1 = fma(l1, l1, c2), a0 = fma(l1, a1, c1);
+    float yf = static_cast<float>(l1);
+    {
+      const float g2 = yf, g1 = static_cast<float>(a1), g0 = static_cast<float>(a0);
+      for (int k = 0; k < 64; ++k) {
+        const float f = ((yf + g2) * yf + g1) * yf + g0;
+        const float d = (3.0f * yf + 2.0f * g2) * yf + g1;
+        if (!(f > 0.0f) || !(d > 0.0f)) break;
+        const float ny = yf - f / d;
+        if (!(ny < yf)) break;
+        yf = ny;
+      }
+    }
+    double l2 = yf;
+    {
+      const double f = fma(fma(l2 + l1, l2, a1), l2, a0);
+      const double d = fma(fma(3.0, l2, l1 + l1), l2, a1);
+      const float rd = rcp_f(d);
+      if (rd > 0.0f && rd < 3.0e38f) l2 -= f * static_cast<double>(rd);
+    }
+    degenerate = !(order_key(l1 - l2) > order_key(1e-6 * e0 * pow2(-e)));
     if (!degenerate) {
+      if (lane < 16) sM[lane] = fma(sN[lane], pow2(-e), (lane % 5 == 0) ? -l1 : 0.0);
       __syncwarp();
-      // cofactor (i, j) of M = N - l1 I on lane 4 i + j
+      // cofactor (i, j) of M = N / 2^e - l1 I on lane 4 i + j
       double cof = 0.0;
       if (lane < 16) {
         const int i = lane >> 2, j = lane & 3;
-        const int r0 = i == 0 ? 1 : 0, r1 = i <= 1 ? 2 : 1, r2 = i <= 2 ? 3 : 2;
+        const int r0 = i == 0 ? 1 : 0, r1i = i <= 1 ? 2 : 1, r2i = i <= 2 ? 3 : 2;
         const int q0 = j == 0 ? 1 : 0, q1 = j <= 1 ? 2 : 1, q2 = j <= 2 ? 3 : 2;
-        const double d3 = sM[4 * r0 + q0] * (sM[4 * r1 + q1] * sM[4 * r2 + q2] - sM[4 * r1 + q2] * sM[4 * r2 + q1]) -
-                          sM[4 * r0 + q1] * (sM[4 * r1 + q0] * sM[4 * r2 + q2] - sM[4 * r1 + q2] * sM[4 * r2 + q0]) +
-                          sM[4 * r0 + q2] * (sM[4 * r1 + q0] * sM[4 * r2 + q1] - sM[4 * r1 + q1] * sM[4 * r2 + q0]);
+        const double m0 = fma(-sM[4 * r1i + q2], sM[4 * r2i + q1], sM[4 * r1i + q1] * sM[4 * r2i + q2]);
+        const double m1 = fma(-sM[4 * r1i + q2], sM[4 * r2i + q0], sM[4 * r1i + q0] * sM[4 * r2i + q2]);
+        const double m2 = fma(-sM[4 * r1i + q1], sM[4 * r2i + q0], sM[4 * r1i + q0] * sM[4 * r2i + q1]);
+        const double d3 = fma(sM[4 * r0 + q2], m2, fma(-sM[4 * r0 + q1], m1, sM[4 * r0 + q0] * m0));
         cof = ((i + j) & 1) ? -d3 : d3;
       }
-      // adj(M) = (l2 - l1)(l3 - l1)(l4 - l1) v v^T: its diagonal is <= 0, and the
-      // entry of largest magnitude marks the best-conditioned column
-      const double e0 = fabs(shfl_d(cof, 0)), e1 = fabs(shfl_d(cof, 5)), e2 = fabs(shfl_d(cof, 10)),
-                   e3 = fabs(shfl_d(cof, 15));
+      // adj(M) is a multiple of v v^T: take the column whose diagonal entry is largest in magnitude
+      const long long k0 = __double_as_longlong(shfl_d(cof, 0)) & 0x7fffffffffffffffLL;
+      const long long k1 = __double_as_longlong(shfl_d(cof, 5)) & 0x7fffffffffffffffLL;
+      const long long k2 = __double_as_longlong(shfl_d(cof, 10)) & 0x7fffffffffffffffLL;
+      const long long k3 = __double_as_longlong(shfl_d(cof, 15)) & 0x7fffffffffffffffLL;
       int jb = 0;
-      double best = e0;
-      if (e1 > best) { best = e1; jb = 1; }
-      if (e2 > best) { best = e2; jb = 2; }
-      if (e3 > best) { best = e3; jb = 3; }
+      long long best = k0;
+      if (k1 > best) { best = k1; jb = 1; }
+      if (k2 > best) { best = k2; jb = 2; }
+      if (k3 > best) { best = k3; jb = 3; }
       w = shfl_d(cof, jb);
       x = shfl_d(cof, 4 + jb);
       y = shfl_d(cof, 8 + jb);
       z = shfl_d(cof, 12 + jb);
-      double len = sqrt(w * w + x * x + y * y + z * z);
-      if (!(len > 0.0)) {  // no usable column: treat as undetermined
-        degenerate = true;
-        len = 1.0;
-      }
-      if (w < 0.0) len = -len;
-      const double il = 1.0 / len;
-      w *= il;
-      x *= il;
-      y *= il;
-      z *= il;
+      if (best == 0 || best >= 0x7ff0000000000000LL) degenerate = true;  // no usable column
     }
   }
   if (degenerate) w = 1.0, x = y = z = 0.0;
-  // lane 4 r + c: entry (r, c) of [dR t] T, r < 3
-  const int r = (lane >> 2) < 3 ? (lane >> 2) : 0, c = lane & 3;
-  double d0, d1, d2;
-  if (r == 0) {
-    d0 = w * w + x * x - y * y - z * z;
-    d1 = 2.0 * (x * y - w * z);
-    d2 = 2.0 * (x * z + w * y);
-  } else if (r == 1) {
-    d0 = 2.0 * (x * y + w * z);
-    d1 = w * w - x * x + y * y - z * z;
-    d2 = 2.0 * (y * z - w * x);
+  // dR from q = (w, x, y, z) of any length: entry e = 3 row + col on lane e as (A B + C D) 2 / |q|^2 + K
+  const double s2 = fma(z, z, fma(y, y, fma(x, x, w * w)));
+  const double two_inv = 2.0 * recip(s2);
+  const int e = lane < 9 ? lane : 8;
+  double A, B, C, D, K = 0.0;
+  // diagonal: 2 (w^2 + q_i^2) / |q|^2 - 1;  off-diagonal: 2 (q_a q_b +- w q_c) / |q|^2
+  const int ri = e / 3, ci = e % 3;
+  auto qsel = [&](int k) { return k == 0 ? x : (k == 1 ? y : z); };
+  if (ri == ci) {
+    A = w; B = w; C = qsel(ri); D = C; K = -1.0;
   } else {
-    d0 = 2.0 * (x * z - w * y);
-    d1 = 2.0 * (y * z + w * x);
-    d2 = w * w - x * x - y * y + z * z;
+    const int oth = 3 - ri - ci;
+    A = qsel(ri < ci ? ri : ci); B = qsel(ri < ci ? ci : ri); D = qsel(oth);
+    // sign of w q_c: + for (1,0), (0,2), (2,1); - for (0,1), (2,0), (1,2)
+    const bool plus = (ri == 1 && ci == 0) || (ri == 0 && ci == 2) || (ri == 2 && ci == 1);
+    C = plus ? w : -w;
   }
-  // translation row r: mean q - dR mean p (means of a and b shifted back by c)
-  const double mpx = fma(sums[0], inv_n, static_cast<double>(cx)), mpy = fma(sums[1], inv_n, static_cast<double>(cy)),
-               mpz = fma(sums[2], inv_n, static_cast<double>(cz));
-  const double mq_r = fma(sums[3 + r], inv_n, static_cast<double>(r == 0 ? cx : (r == 1 ? cy : cz)));
-  const double tr = mq_r - (d0 * mpx + d1 * mpy + d2 * mpz);
-  const double Tpre = lane < 12 ? st->T[lane] : 0.0;
-  const double t0 = shfl_d(Tpre, c), t1 = shfl_d(Tpre, 4 + c), t2 = shfl_d(Tpre, 8 + c);
-  double tn = d0 * t0 + d1 * t1 + d2 * t2;
-  if (c == 3) tn += tr;
-  const double tx = shfl_d(tr, 0), ty = shfl_d(tr, 4), tz = shfl_d(tr, 8);
+  const double dR = fma(fma(A, B, C * D), two_inv, K);
+  // translation t_r = mean q_r - (dR mean p)_r, mean p = mean a + c, mean q = mean b + c, on lanes 4 r + c
+  const double cc = lane < 6 ? static_cast<double>((lane % 3) == 0 ? cx : ((lane % 3) == 1 ? cy : cz)) : 0.0;
+  const double mpq = lane < 6 ? fma(sums[lane], inv_n, cc) : 0.0;  // lanes 0..2: mean p, 3..5: mean q
+  const int r = (lane >> 2) < 3 ? (lane >> 2) : 0, c = lane & 3;
+  const double d0 = shfl_d(dR, 3 * r), d1 = shfl_d(dR, 3 * r + 1), d2 = shfl_d(dR, 3 * r + 2);
+  const double tr = shfl_d(mpq, 3 + r) - fma(d2, shfl_d(mpq, 2), fma(d1, shfl_d(mpq, 1), d0 * shfl_d(mpq, 0)));
+  const double t0 = shfl_d(Tpre, c), t1 = shfl_d(Tpre, 4 + c), tt2 = shfl_d(Tpre, 8 + c);
+  const double tn = fma(d2, tt2, fma(d1, t1, fma(d0, t0, c == 3 ? tr : 0.0)));
   if (lane < 12) {
     st->T[lane] = tn;
     if (c < 3) st->R[3 * r + c] = __double2float_rn(tn);
     else st->t[r] = __double2float_rn(tn);
   }
+  bool done = false;
+  if (order_key(eps) > 0) {
+    // angle < eps  <=>  |(x, y, z)|^2 < tan^2(eps / 2) w^2;  |t| < eps
+    const double v2 = fma(z, z, fma(y, y, x * x));
+    const bool rot_ok = degenerate || order_key(v2) < order_key((w * w) * eps_tan2);
+    const double tx = shfl_d(tr, 0), ty = shfl_d(tr, 4), tz = shfl_d(tr, 8);
+    const double tl2 = fma(tz, tz, fma(ty, ty, tx * tx));
+    done = rot_ok && order_key(tl2) < order_key(eps * eps);
+  }
   if (lane == 0) {
     if (degenerate) st->degenerate = 1;
     st->iters += 1;
-    const double angle = degenerate ? 0.0 : 2.0 * atan2(sqrt(x * x + y * y + z * z), w);
-    const double tl = sqrt(tx * tx + ty * ty + tz * tz);
-    if (eps > 0.0 && fmax(angle, tl) < eps) st->done = 1;
+    if (done) st->done = 1;
   }
 }
 
@@ -900,11 +914,20 @@ __device__ void solve_update_p2p(const double* sums, IcpState* __restrict__ st, 
 // (never; also for NaN), so that the device tests it on its bit pattern.
 inline double stop_eps(double eps) { return eps > 0.0 ? eps : 0.0; }
 
+// tan^2(eps / 2), the point-to-point rotation threshold (see solve_update_p2p).
+inline double stop_tan2(double eps) {
+  if (!(eps > 0.0)) return 0.0;
+  if (eps >= 3.141592653589793) return 1e300;
+  const double t = std::tan(0.5 * eps);
+  return t * t;
+}
+
 // Everything one registration problem brings to an iteration launch.
 struct PairDesc {
   GridView g;
   float cell, r;
   double eps;          // convergence threshold of this pair (0: never; see stop_eps)
+  double eps_tan2;     // tan^2(eps / 2) (see stop_tan2)
   int kind;            // kPointToPlane or kPointToPoint
   float ctr[3];        // point-to-point: reference point subtracted before the moments
   const float4* src4;  // cell-sorted source, .w = original index bits
@@ -1049,7 +1072,7 @@ __device__ void finish(const PairDesc& P, int mode, float nlen) {
     }
     return;
   }
-  if (P.kind == kPointToPoint) solve_update_p2p(sums, st, P.eps, P.ctr[0], P.ctr[1], P.ctr[2]);
+  if (P.kind == kPointToPoint) solve_update_p2p(sums, st, P.eps, P.eps_tan2, P.ctr[0], P.ctr[1], P.ctr[2]);
   else solve_update(sums, st, P.eps);
 }
 
@@ -1424,6 +1447,7 @@ struct Work {
     P.cell = g->cell;
     P.r = r;
     P.eps = stop_eps(eps);
+    P.eps_tan2 = stop_tan2(eps);
     P.kind = kind;
     // the centre of the grid's box: near every point that can find a partner
     for (int k = 0; k < 3; ++k)
@@ -1735,6 +1759,7 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const 
     P.cell = g->cell;
     P.r = r;
     P.eps = stop_eps(eps);
+    P.eps_tan2 = stop_tan2(eps);
     P.kind = kPointToPlane;
     P.ctr[0] = P.ctr[1] = P.ctr[2] = 0.f;
     P.src4 = src4;
@@ -1906,6 +1931,7 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
     P.cell = tgts[p]->cell;
     P.r = static_cast<float>(max_corr_dist[p]);
     P.eps = stop_eps(eps);
+    P.eps_tan2 = stop_tan2(eps);
     P.kind = kPointToPlane;
     P.ctr[0] = P.ctr[1] = P.ctr[2] = 0.f;
     P.src4 = d_src4.as<float4>() + off[p];
@@ -2089,6 +2115,7 @@ PairDesc slot_desc(o3g_server* sv, int k, int tile0) {
   P.cell = sl.grid->cell;
   P.r = sl.r;
   P.eps = stop_eps(sl.eps);
+  P.eps_tan2 = stop_tan2(sl.eps);
   P.kind = kPointToPlane;
   P.ctr[0] = P.ctr[1] = P.ctr[2] = 0.f;
   P.src4 = sl.src4;
