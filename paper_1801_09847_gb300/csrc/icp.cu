@@ -572,10 +572,10 @@ __device__ __forceinline__ double sym6(const double* sums, int i, int j) {
 // three angles on lanes 0..5 (as many Taylor terms as the largest angle needs
 // for a truncation error below 2^-60; the library call from 0.25 rad), dR =
 // Rz(gamma) Ry(beta) Rx(alpha) one entry per lane, and T <- [dR, t] T on lanes
-// 4 r + c.
-__device__ void solve_update(const double* sums, IcpState* __restrict__ st, double eps) {
+// 4 r + c (Tpre: pose entry `lane` for lanes 0..11, and iters0 the iteration
+// count, both fetched by the caller).
+__device__ void solve_update(const double* sums, double Tpre, int iters0, IcpState* __restrict__ st, double eps) {
   const int lane = threadIdx.x & 31;
-  const double Tpre = lane < 12 ? st->T[lane] : 0.0;  // pose rows 0..2, fetched early
   // this lane's entry; lanes 28..31 hold a copy of entry (0, 0) that nothing reads
   const int tl = lane < 28 ? lane : 0;
   const int i = (tl >= 1) + (tl >= 3) + (tl >= 6) + (tl >= 10) + (tl >= 15) + (tl >= 21);
@@ -662,7 +662,7 @@ __device__ void solve_update(const double* sums, IcpState* __restrict__ st, doub
   }
   if (lane == 0) {
     if (frozen) st->degenerate = 1;
-    st->iters += 1;
+    st->iters = iters0 + 1;
     if (done) st->done = 1;
   }
 }
@@ -707,12 +707,11 @@ __device__ __forceinline__ float rcp_f(double d) {
 // and |t| are below eps, the angle tested as |q_xyz|^2 < tan^2(eps/2) q_w^2.
 // Few float64 instructions: comparisons on integer bit patterns, exact
 // power-of-two scalings, no division or square root.
-__device__ void solve_update_p2p(const double* sums, IcpState* __restrict__ st, double eps, double eps_tan2,
-                                 float cx, float cy, float cz) {
+__device__ void solve_update_p2p(const double* sums, double Tpre, int iters0, IcpState* __restrict__ st,
+                                 double eps, double eps_tan2, float cx, float cy, float cz) {
   __shared__ double sS[9], sN[16], sM[16];
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const double Tpre = lane < 12 ? st->T[lane] : 0.0;
   const double n = sums[29];
   const double inv_n = recip(n);
   // means of a (lanes 0..2) and b (lanes 3..5), and n times them
@@ -905,7 +904,7 @@ __device__ void solve_update_p2p(const double* sums, IcpState* __restrict__ st, 
   }
   if (lane == 0) {
     if (degenerate) st->degenerate = 1;
-    st->iters += 1;
+    st->iters = iters0 + 1;
     if (done) st->done = 1;
   }
 }
@@ -1022,6 +1021,10 @@ __device__ void finish(const PairDesc& P, int mode, float nlen) {
   __shared__ double sums[kPartial];
   __shared__ bool bad;
   const int col = threadIdx.x & 31, q = threadIdx.x >> 5;
+  IcpState* const st = P.st;
+  // the pose rows the update multiplies and the iteration count, fetched with the accumulators
+  const double Tpre = threadIdx.x < 12 ? st->T[threadIdx.x] : 0.0;
+  const int iters0 = st->iters;
   unsigned long long v[kAccRows / 4];
 #pragma unroll
   for (int j = 0; j < kAccRows / 4; ++j) {
@@ -1036,7 +1039,6 @@ __device__ void finish(const PairDesc& P, int mode, float nlen) {
     if (row < P.nacc) P.acc[static_cast<size_t>(row) * kPartial + col] = 0ull;
   }
   sub[q][col] = static_cast<long long>(t);
-  IcpState* const st = P.st;
   if (threadIdx.x == 0) st->arrived = 0u;  // ready for the next launch
   __syncthreads();
   if (threadIdx.x < kPartial) {
@@ -1072,8 +1074,9 @@ __device__ void finish(const PairDesc& P, int mode, float nlen) {
     }
     return;
   }
-  if (P.kind == kPointToPoint) solve_update_p2p(sums, st, P.eps, P.eps_tan2, P.ctr[0], P.ctr[1], P.ctr[2]);
-  else solve_update(sums, st, P.eps);
+  if (P.kind == kPointToPoint)
+    solve_update_p2p(sums, Tpre, iters0, st, P.eps, P.eps_tan2, P.ctr[0], P.ctr[1], P.ctr[2]);
+  else solve_update(sums, Tpre, iters0, st, P.eps);
 }
 
 
@@ -1107,20 +1110,23 @@ __device__ __forceinline__ void p2p_terms(const PairDesc& P, float3 p, float4 q,
 // performs the pair's solve and update (see finish).  Block-uniform control flow.
 template <bool F64, class St>
 __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
-  if (mode == kIterate && P.st->done) return;
+  // every load the tile starts with (the stop flag, the pose, the source point
+  // and its hint) is issued before any of them is used: one memory round trip
+  const int done = P.st->done;
   float R[9], t[3];
 #pragma unroll
   for (int k = 0; k < 9; ++k) R[k] = P.st->R[k];
 #pragma unroll
   for (int k = 0; k < 3; ++k) t[k] = P.st->t[k];
-  const float r2 = __fmul_rn(P.r, P.r);
   const int i = j * kThreads + threadIdx.x;
   // every lane runs the search (lanes past the end on a far-away dummy point) so
   // that the warp-wide exchange of first candidates is convergent
   const bool live = i < P.ns;
   const float4 s = live ? P.src4[i] : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
-  const float3 p = live ? xform_rn(R, t, s.x, s.y, s.z) : make_float3(3.0e38f, 3.0e38f, 3.0e38f);
   const int hint = (P.hints && live) ? P.hints[i] : -1;
+  if (mode == kIterate && done) return;
+  const float r2 = __fmul_rn(P.r, P.r);
+  const float3 p = live ? xform_rn(R, t, s.x, s.y, s.z) : make_float3(3.0e38f, 3.0e38f, 3.0e38f);
   Nearest nb{r2, 0x7fffffff, -1};
   first_bound(P.g, p.x, p.y, p.z, hint, nb);
   if (!staged_search(P.g, P.cell, p.x, p.y, p.z, P.r, live, nb, stage) && live)
