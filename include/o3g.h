@@ -250,12 +250,34 @@ O3G_API int32_t o3g_icp_point_to_plane(const float* d_src, int64_t ns, int32_t s
                                double* out_fitness, double* out_rmse);
 
 /*
+ * The whole pairwise refinement from DEVICE buffers (Sec. 3.3: estimate_normals
+ * on the target, then registration_icp with TransformationEstimationPointToPlane()):
+ * builds the target grid (cell = 1.002 x max_corr_dist), attaches d_tgt_nrm
+ * (nt normals, nrm_stride floats per row) or, if it is NULL, estimates target
+ * normals (normal_radius, normal_max_nn, viewpoint = origin), runs ICP (as
+ * o3g_icp_point_to_plane_grid with eps) and frees the grid.  d_src / d_tgt are
+ * device xyz rows of src_stride / tgt_stride floats (>= 3), read only.  The
+ * source's spatial sort runs on a library-owned stream beside `stream` while the
+ * grid is built and the normals are computed (events order it after the work
+ * already on `stream` and the iterations after it), so the result equals the
+ * separate calls bit for bit.  Results in host memory; synchronous; status codes
+ * as o3g_icp_point_to_plane_grid, plus those of o3g_build_grid and the normals.
+ */
+O3G_API int32_t o3g_register_point_to_plane(const float* d_src, int64_t ns, int32_t src_stride, const float* d_tgt,
+                                            int64_t nt, int32_t tgt_stride, const float* d_tgt_nrm,
+                                            int32_t nrm_stride, float normal_radius, int32_t normal_max_nn,
+                                            const double* init_T, double max_corr_dist, int32_t max_iter, double eps,
+                                            double* out_T, double* out_fitness, double* out_rmse, int32_t* out_iters,
+                                            void* stream);
+
+/*
  * The whole pairwise refinement from HOST buffers (the call a user with data in
  * host memory makes): copies source and target to the device, builds the
  * target grid (cell = 1.002 x max_corr_dist), attaches h_tgt_nrm or, if it is NULL,
  * estimates target normals (normal_radius, normal_max_nn, viewpoint = origin),
- * runs ICP and returns the results in host memory.  h_src, h_tgt and h_tgt_nrm
- * are packed xyz (stride 3); page-locked buffers make the copies asynchronous.
+ * runs ICP and returns the results in host memory (o3g_register_point_to_plane
+ * on the copies).  h_src, h_tgt and h_tgt_nrm are packed xyz (stride 3);
+ * page-locked buffers make the copies asynchronous.
  */
 O3G_API int32_t o3g_register_point_to_plane_host(const float* h_src, int64_t ns, const float* h_tgt, int64_t nt,
                                          const float* h_tgt_nrm, float normal_radius, int32_t normal_max_nn,

@@ -1423,7 +1423,9 @@ void set_sums(PairDesc& P, const o3g_grid* g, unsigned long long* acc) {
 // Everything one ICP-style call needs on the device: the cell-sorted source,
 // the iteration state and the fixed-point accumulators.
 struct Work {
-  SortedCloud src;
+  SortedCloud src;         // the cell-sorted source when this Work sorts it
+  const float4* pts = nullptr;  // the sorted source in use (own, or sorted by the caller)
+  const int* aux = nullptr;     // its flags (aux[6]: a non-finite coordinate)
   DevBuf state;
   DevBuf acc;    // accum_rows(nblk) x kPartial fixed-point sums
   DevBuf hints;  // per source point: sorted target position of its last match, or -1
@@ -1431,8 +1433,16 @@ struct Work {
   int nblk = 1;
   int launches = 0;  // launches so far (the queue parity)
   explicit Work(cudaStream_t s) : src(s), state(s), acc(s), hints(s), queue(s) {}
-  int32_t prepare(const float* d_src, int64_t ns, int32_t stride, float cell, const double* T, cudaStream_t s) {
-    O3G_TRY_STATUS(sort_cloud(d_src, ns, stride, s, &src));
+  int32_t prepare(const float* d_src, int64_t ns, int32_t stride, float cell, const double* T, cudaStream_t s,
+                  const SortedCloud* pre = nullptr) {
+    if (pre) {
+      pts = pre->pts;
+      aux = pre->aux.as<int>();
+    } else {
+      O3G_TRY_STATUS(sort_cloud(d_src, ns, stride, s, &src));
+      pts = src.pts;
+      aux = src.aux.as<int>();
+    }
     nblk = iter_blocks(ns);
     O3G_TRY(state.alloc(sizeof(IcpState)));
     const size_t acc_bytes = sizeof(unsigned long long) * kPartial * accum_rows(nblk);
@@ -1459,7 +1469,7 @@ struct Work {
     for (int k = 0; k < 3; ++k)
       P.ctr[k] = kind == kPointToPoint ? (static_cast<float>(g->lo[k]) + 0.5f * static_cast<float>(g->span[k])) * g->cell
                                        : 0.f;
-    P.src4 = src.pts;
+    P.src4 = pts;
     P.ns = ns;
     P.ntiles = nblk;
     P.tile0 = 0;
@@ -1480,7 +1490,8 @@ struct Work {
 
 int32_t icp_run(const o3g_grid* g, const float* d_src, int64_t ns, int32_t stride, const double* init_T,
                 double max_corr_dist, int32_t max_iter, double eps, double* out_T, double* out_fitness,
-                double* out_rmse, int32_t* out_iters, cudaStream_t s, int32_t precision, bool point_to_point) {
+                double* out_rmse, int32_t* out_iters, cudaStream_t s, int32_t precision, bool point_to_point,
+                const SortedCloud* pre) {
   const char* fn = point_to_point ? "o3g_icp_point_to_point_grid" : "o3g_icp_point_to_plane_grid";
   const int kind = point_to_point ? kPointToPoint : kPointToPlane;
   if (precision != O3G_PREC_F32_COMPENSATED && precision != O3G_PREC_F64) {
@@ -1504,7 +1515,7 @@ int32_t icp_run(const o3g_grid* g, const float* d_src, int64_t ns, int32_t strid
   }
   const float r = static_cast<float>(max_corr_dist);
   Work w(s);
-  O3G_TRY_STATUS(w.prepare(d_src, ns, stride, g->cell, init_T, s));
+  O3G_TRY_STATUS(w.prepare(d_src, ns, stride, g->cell, init_T, s, pre));
   const int n = static_cast<int>(ns);
   for (int it = 0; it < max_iter; ++it) {
     TimedRegion tr(O3G_KERNEL_ICP_CORR, s);
@@ -1515,7 +1526,7 @@ int32_t icp_run(const o3g_grid* g, const float* d_src, int64_t ns, int32_t strid
   IcpState h;
   int aux[8];
   O3G_TRY(cudaMemcpyAsync(&h, w.state.p, sizeof(IcpState), cudaMemcpyDeviceToHost, s));
-  O3G_TRY(cudaMemcpyAsync(aux, w.src.aux.p, sizeof(aux), cudaMemcpyDeviceToHost, s));
+  O3G_TRY(cudaMemcpyAsync(aux, w.aux, sizeof(aux), cudaMemcpyDeviceToHost, s));
   O3G_TRY(cudaStreamSynchronize(s));
   if (aux[6]) {
     set_error("%s: non-finite source coordinate", fn);
@@ -1587,7 +1598,7 @@ extern "C" int32_t o3g_normal_equations_ex(const o3g_grid* g, const float* d_src
   IcpState h;
   int aux[8];
   O3G_TRY(cudaMemcpyAsync(&h, w.state.p, sizeof(IcpState), cudaMemcpyDeviceToHost, s));
-  O3G_TRY(cudaMemcpyAsync(aux, w.src.aux.p, sizeof(aux), cudaMemcpyDeviceToHost, s));
+  O3G_TRY(cudaMemcpyAsync(aux, w.aux, sizeof(aux), cudaMemcpyDeviceToHost, s));
   O3G_TRY(cudaStreamSynchronize(s));
   if (aux[6]) {
     set_error("%s: non-finite source coordinate", fn);
@@ -1813,6 +1824,7 @@ namespace {
 
 std::mutex g_graph_mutex;
 cudaStream_t g_graph_stream[kNaMaxDevices] = {};
+cudaStream_t g_side_stream[kNaMaxDevices] = {};
 
 // A non-blocking stream of the library per device, used to capture graphs
 // (the legacy default stream cannot be captured).
@@ -1871,6 +1883,22 @@ int32_t run_iterations(const PairDesc* descs, const int* tile_pair, const int* d
 }
 
 }  // namespace
+
+// A library-owned non-blocking stream per device for work that runs beside the
+// caller's stream (the source sort of the combined registration entry points).
+cudaError_t side_stream(cudaStream_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_graph_mutex);
+  if (!g_side_stream[dev]) {
+    e = cudaStreamCreateWithFlags(&g_side_stream[dev], cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  *out = g_side_stream[dev];
+  return cudaSuccess;
+}
 }  // namespace o3g
 
 extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid* const* tgts, const float* const* d_src,

@@ -160,10 +160,14 @@ __device__ __forceinline__ float3 xform_rn(const float* R, const float* t, float
 struct o3g_grid;
 
 namespace o3g {
+// ICP on a target grid (point-to-plane, or point-to-point); `pre`, when given,
+// is the source already sorted (sort_cloud of d_src, complete before work on s).
 int32_t icp_run(const o3g_grid* g, const float* d_src, int64_t ns, int32_t stride, const double* init_T,
                 double max_corr_dist, int32_t max_iter, double eps, double* out_T, double* out_fitness,
                 double* out_rmse, int32_t* out_iters, cudaStream_t s, int32_t precision = O3G_PREC_F32_COMPENSATED,
-                bool point_to_point = false);
+                bool point_to_point = false, const SortedCloud* pre = nullptr);
+// A library-owned non-blocking stream per device for work beside the caller's stream.
+cudaError_t side_stream(cudaStream_t* out);
 int32_t estimate_normals_impl(o3g_grid* g, float radius, int32_t max_nn, const float* viewpoint, float* d_out,
                               int32_t out_stride, cudaStream_t s);
 }  // namespace o3g

@@ -68,6 +68,8 @@ _SIGNATURES = {
                                     _i32),
     "o3g_icp_point_to_plane": ([_vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64, _i32, _f64p, _f64, _i32, _f64p, _f64p,
                                 _f64p], _i32),
+    "o3g_register_point_to_plane": ([_vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _f32, _i32, _f64p, _f64, _i32, _f64,
+                                     _f64p, _f64p, _f64p, ctypes.POINTER(_i32), _vp], _i32),
     "o3g_register_point_to_plane_host": ([_vp, _i64, _vp, _i64, _vp, _f32, _i32, _f64p, _f64, _i32, _f64, _f64p,
                                           _f64p, _f64p, _i32p, _vp], _i32),
     "o3g_icp_point_to_plane_batch": ([_i32, _vp, _vp, _vp, _vp, _f64p, _f64p, _i32, _f64, _f64p, _f64p, _f64p, _i32p,
@@ -551,6 +553,30 @@ def icp_point_to_plane(src, tgt, tgt_nrm, init_T, max_corr_dist: float, max_iter
                                              int(max_iter), _pp(T), ctypes.byref(fit), ctypes.byref(rmse)),
                 "o3g_icp_point_to_plane")
     return _result(st, T, fit, rmse, None)
+
+
+def register_point_to_plane(src, tgt, tgt_nrm, init_T, max_corr_dist: float, max_iter: int, eps: float = 0.0,
+                            normal_radius: float = 0.1, normal_max_nn: int = 30, stream=None) -> dict:
+    """Whole refinement from device clouds (o3g_register_point_to_plane): target grid, target normals
+    (attached `tgt_nrm`, or estimated with (normal_radius, normal_max_nn) when None), ICP; the source's
+    sort runs beside the grid build and the normals.  Returns dict(status, T, fitness, rmse, iters)."""
+    ps, ns, ss = _cloud(src, "src")
+    pt, nt, st_ = _cloud(tgt, "tgt")
+    if tgt_nrm is not None:
+        pn, nn, sn = _cloud(tgt_nrm, "tgt_nrm")
+        if nn != nt:
+            raise O3GError(ERR_ARG, "register_point_to_plane", "normals must match the target points one to one")
+    else:
+        pn, sn = _vp(0), 3
+    T0 = _pose(init_T)
+    T = np.zeros(16)
+    fit, rmse, iters = _f64(), _f64(), _i32()
+    st = _check(lib().o3g_register_point_to_plane(ps, ns, ss, pt, nt, st_, pn, sn, float(normal_radius),
+                                                  int(normal_max_nn), _pp(T0), float(max_corr_dist), int(max_iter),
+                                                  float(eps), _pp(T), ctypes.byref(fit), ctypes.byref(rmse),
+                                                  ctypes.byref(iters), _stream(stream)),
+                "o3g_register_point_to_plane")
+    return _result(st, T, fit, rmse, iters)
 
 
 def register_point_to_plane_host(src, tgt, tgt_nrm, init_T, max_corr_dist: float, max_iter: int, eps: float = 0.0,

@@ -543,6 +543,48 @@ def test_one_shot_and_host_entry_points_agree(o3g):
         o3g.icp_point_to_plane(cuda(pr.src), cuda(pr.tgt), cuda(pr.tgt_nrm[:-1]), np.eye(4), 0.05, 3)
 
 
+def _same_result(a, b):
+    assert a["status"] == b["status"] and a["iters"] == b["iters"]
+    assert np.array_equal(a["T"], b["T"])
+    assert a["fitness"] == b["fitness"] and a["rmse"] == b["rmse"]
+
+
+def test_combined_entry_equals_separate_calls(o3g, room):
+    """o3g_register_point_to_plane sorts the source on a side stream while the grid and normals are built; its
+    result is the separate calls' (grid at 1.002 r, normals, ICP) bit for bit, with estimated or attached
+    normals, with strided rows, and through the host-buffer entry that runs on it."""
+    import torch
+    r = room.max_corr_dist
+    grid = o3g.build_grid(cuda(room.tgt), r * 1.002)
+    grid.estimate_normals(0.05, 30, out=False)
+    sep = o3g.icp_point_to_plane_grid(grid, cuda(room.src), np.eye(4), r, room.max_iter)
+    comb = o3g.register_point_to_plane(cuda(room.src), cuda(room.tgt), None, np.eye(4), r, room.max_iter,
+                                       normal_radius=0.05, normal_max_nn=30)
+    _same_result(sep, comb)
+    host = o3g.register_point_to_plane_host(room.src, room.tgt, None, np.eye(4), r, room.max_iter,
+                                            normal_radius=0.05, normal_max_nn=30)
+    _same_result(sep, host)
+    # attached normals, 4-float rows, a pose and eps
+    pr = synth.sphere_plane_pair(n=6000, seed=7)
+    wide = lambda a: torch.from_numpy(np.hstack([a, np.ones((len(a), 1), np.float32)])).cuda()
+    g2 = o3g.build_grid(cuda(pr.tgt), pr.max_corr_dist * 1.002)
+    g2.set_normals(cuda(pr.tgt_nrm))
+    T0 = synth.perturbation(synth.rng(8), 1.0, 0.01)
+    sep2 = o3g.icp_point_to_plane_grid(g2, cuda(pr.src), T0, pr.max_corr_dist, 40, eps=1e-8)
+    comb2 = o3g.register_point_to_plane(wide(pr.src), wide(pr.tgt), wide(pr.tgt_nrm), T0, pr.max_corr_dist, 40,
+                                        eps=1e-8)
+    _same_result(sep2, comb2)
+    # empty source, non-finite source
+    empty = o3g.register_point_to_plane(torch.zeros((0, 3), device="cuda"), cuda(pr.tgt), cuda(pr.tgt_nrm),
+                                        np.eye(4), 0.05, 5)
+    assert empty["status"] == o3g.WARN_FEW_CORR
+    bad = pr.src.copy()
+    bad[7, 2] = np.nan
+    with pytest.raises(o3g.O3GError) as e:
+        o3g.register_point_to_plane(cuda(bad), cuda(pr.tgt), cuda(pr.tgt_nrm), np.eye(4), 0.05, 5)
+    assert e.value.status == o3g.ERR_NONFINITE
+
+
 def test_host_entry_with_gpu_normals_matches_oracle_pipeline(o3g, room):
     """register_point_to_plane_host on the RGB-D-frame pair (GPU normals) against the oracle's pipeline."""
     res = o3g.register_point_to_plane_host(room.src, room.tgt, None, np.eye(4), room.max_corr_dist, room.max_iter,
