@@ -64,34 +64,36 @@ __global__ void __launch_bounds__(kThreads) k_bbox(const float* __restrict__ xyz
     fx[1] = max(fx[1], ky);
     fx[2] = max(fx[2], kz);
   }
+  // warp, then block reduction; one atomic per value per block
   const unsigned full = 0xffffffffu;
-  mn0 = __reduce_min_sync(full, mn0);
-  mn1 = __reduce_min_sync(full, mn1);
-  mn2 = __reduce_min_sync(full, mn2);
-  mx0 = __reduce_max_sync(full, mx0);
-  mx1 = __reduce_max_sync(full, mx1);
-  mx2 = __reduce_max_sync(full, mx2);
-  bad = __reduce_or_sync(full, bad);
+  int v[13] = {mn0, mn1, mn2, mx0, mx1, mx2, bad, fn[0], fn[1], fn[2], fx[0], fx[1], fx[2]};
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    fn[a] = __reduce_min_sync(full, fn[a]);
-    fx[a] = __reduce_max_sync(full, fx[a]);
+  for (int k = 0; k < 13; ++k) {
+    if (k < 3 || (k >= 7 && k < 10)) v[k] = __reduce_min_sync(full, v[k]);
+    else if (k == 6) v[k] = __reduce_or_sync(full, v[k]);
+    else v[k] = __reduce_max_sync(full, v[k]);
   }
-  if ((threadIdx.x & 31) == 0) {
-    if (mn0 != INT_MAX) {
-      atomicMin(bb + 0, mn0);
-      atomicMin(bb + 1, mn1);
-      atomicMin(bb + 2, mn2);
-      atomicMax(bb + 3, mx0);
-      atomicMax(bb + 4, mx1);
-      atomicMax(bb + 5, mx2);
+  __shared__ int part[kThreads / 32][13];
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        atomicMin(bb + 7 + a, fn[a]);
-        atomicMax(bb + 10 + a, fx[a]);
-      }
+    for (int k = 0; k < 13; ++k) part[warp][k] = v[k];
+  __syncthreads();
+  const int k = threadIdx.x;
+  if (k < 13) {
+    int r = part[0][k];
+    for (int w = 1; w < kThreads / 32; ++w) {
+      const int x = part[w][k];
+      r = (k < 3 || (k >= 7 && k < 10)) ? min(r, x) : (k == 6 ? (r | x) : max(r, x));
     }
-    if (bad) atomicOr(bb + 6, 1);
+    // an empty block (all of its points non-finite or none) leaves the extremes untouched
+    if (k == 6) {
+      if (r) atomicOr(bb + 6, 1);
+    } else if (k < 3 || (k >= 7 && k < 10)) {
+      if (r != INT_MAX) atomicMin(bb + k, r);
+    } else if (r != INT_MIN) {
+      atomicMax(bb + k, r);
+    }
   }
 }
 
@@ -381,19 +383,31 @@ __global__ void __launch_bounds__(kThreads) k_fbox(const float* __restrict__ xyz
       mx[a] = max(mx[a], ordered_int(v[a]));
     }
   }
+  // warp, then block reduction; one atomic per value per block
+  int v[7] = {mn[0], mn[1], mn[2], mx[0], mx[1], mx[2], bad};
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    mn[a] = __reduce_min_sync(0xffffffffu, mn[a]);
-    mx[a] = __reduce_max_sync(0xffffffffu, mx[a]);
-  }
-  bad = __reduce_or_sync(0xffffffffu, bad);
-  if ((threadIdx.x & 31) == 0) {
+  for (int k = 0; k < 7; ++k)
+    v[k] = k < 3 ? __reduce_min_sync(0xffffffffu, v[k])
+                 : (k < 6 ? __reduce_max_sync(0xffffffffu, v[k]) : __reduce_or_sync(0xffffffffu, v[k]));
+  __shared__ int part[kThreads / 32][7];
+  if ((threadIdx.x & 31) == 0)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (mn[a] != INT_MAX) atomicMin(aux + a, mn[a]);
-      if (mx[a] != INT_MIN) atomicMax(aux + 3 + a, mx[a]);
+    for (int k = 0; k < 7; ++k) part[threadIdx.x >> 5][k] = v[k];
+  __syncthreads();
+  const int k = threadIdx.x;
+  if (k < 7) {
+    int r = part[0][k];
+    for (int w = 1; w < kThreads / 32; ++w) {
+      const int x = part[w][k];
+      r = k < 3 ? min(r, x) : (k < 6 ? max(r, x) : (r | x));
     }
-    if (bad) atomicOr(aux + 6, 1);
+    if (k < 3) {
+      if (r != INT_MAX) atomicMin(aux + k, r);
+    } else if (k < 6) {
+      if (r != INT_MIN) atomicMax(aux + k, r);
+    } else if (r) {
+      atomicOr(aux + 6, 1);
+    }
   }
 }
 
@@ -604,7 +618,7 @@ int32_t sort_cloud(const float* d_xyz, int64_t n64, int32_t stride, cudaStream_t
   count_launch();
   if (n == 0) return O3G_OK;
   int nb = blocks_for(n, kThreads);
-  if (nb > kNumSMs * 8) nb = kNumSMs * 8;
+  if (nb > kNumSMs * 2) nb = kNumSMs * 2;
   k_fbox<<<nb, kThreads, 0, s>>>(d_xyz, n, stride, out->aux.as<int>());
   DevBuf keys(s), vals(s), tk(s), tv(s);
   O3G_TRY(keys.alloc(sizeof(uint32_t) * n));
@@ -716,7 +730,7 @@ static int32_t build_impl(const float* d_xyz, int64_t n64, int stride, float cel
     }
     k_bbox_init<<<1, 32, 0, s>>>(bb.as<int>());
     int nb = blocks_for(n, kThreads);
-    if (nb > kNumSMs * 8) nb = kNumSMs * 8;
+    if (nb > kNumSMs * 2) nb = kNumSMs * 2;
     k_bbox<<<nb, kThreads, 0, s>>>(d_xyz, n, stride, inv, bb.as<int>());
     count_launch(2);
     O3G_TRY(cudaGetLastError());
