@@ -24,6 +24,12 @@
  *  - The library allocates device memory from a private stream-ordered pool.
  *    Handles (o3g_grid) are library-owned and released with o3g_free_grid.
  *  - Non-finite input coordinates are rejected with O3G_ERR_NONFINITE.
+ *  - The ICP sums over all correspondences are accumulated exactly as 64-bit
+ *    fixed-point integers scaled by a-priori bounds (the number of source
+ *    points, the radius, the target's coordinate box and the largest length of
+ *    its normals), so they do not depend on the order of accumulation.  A term
+ *    outside its bound (a NaN normal, say) makes the sums unusable and the call
+ *    returns O3G_ERR_NONFINITE.
  *  - Thread safety: calls on different handles may run concurrently from
  *    different host threads; a handle must not be used by two calls at once.
  */
@@ -49,7 +55,7 @@ typedef enum {
   O3G_ERR_ARG = -1,        /* invalid argument (null pointer, negative size, bad stride, ...) */
   O3G_ERR_OOM = -2,        /* device allocation failed */
   O3G_ERR_CUDA = -3,       /* a CUDA runtime call failed; see o3g_last_error() */
-  O3G_ERR_NONFINITE = -4,  /* a point coordinate or the pose is NaN or infinite */
+  O3G_ERR_NONFINITE = -4,  /* a coordinate, a normal or the pose is NaN or infinite */
   O3G_ERR_TIMEOUT = -5     /* a bounded device-side wait gave up */
 } o3g_status;
 
@@ -89,7 +95,9 @@ O3G_API int32_t o3g_grid_info(const o3g_grid* grid, int64_t* n, float* cell_size
 /*
  * Attaches normals to a grid's points (Sec. 3.1: normals are valid only when
  * they have as many records as the points -> n != grid's n gives O3G_ERR_ARG).
- * d_nrm is read in the caller's point order and copied into the grid.
+ * d_nrm is read in the caller's point order and copied into the grid, and the
+ * largest normal length is recorded (it bounds the ICP sums; normals need not
+ * be unit length).  Asynchronous.
  */
 O3G_API int32_t o3g_grid_set_normals(o3g_grid* grid, const float* d_nrm, int64_t n, int32_t stride, void* stream);
 
@@ -160,8 +168,10 @@ O3G_API int32_t o3g_correspondences(const o3g_grid* tgt, const float* d_src, int
  * J_i = [p_i x n_i ; n_i] (target normals), and
  *   out_A [36] = sum J J^T (row-major, symmetric),  out_b [6] = sum J r,
  *   out_stats [3] = (sum r^2, sum d2, |C|).
- * Per-correspondence arithmetic is float32 with compensated block sums; the
- * cross-block sum is float64.  Requires normals on the target grid.  Synchronous.
+ * Per-correspondence arithmetic is float32 with compensated block sums, which
+ * are added across blocks as exact 64-bit fixed point and converted to float64
+ * once.  Requires normals on the target grid.  A non-finite source coordinate
+ * or a sum left unusable by a non-finite normal: O3G_ERR_NONFINITE.  Synchronous.
  */
 O3G_API int32_t o3g_normal_equations(const o3g_grid* tgt, const float* d_src, int64_t ns, int32_t stride, const double* T,
                              float max_corr_dist, double* out_A, double* out_b, double* out_stats, void* stream);
@@ -169,12 +179,14 @@ O3G_API int32_t o3g_normal_equations(const o3g_grid* tgt, const float* d_src, in
 /*
  * Arithmetic of the per-correspondence terms and of the block sums.
  *   O3G_PREC_F32_COMPENSATED  J, r and the 27 products in float32, block sums
- *                             compensated (TwoSum pairs), cross-block sums and
- *                             the solve in float64 (the default everywhere).
+ *                             compensated (TwoSum pairs), cross-block sums exact
+ *                             in 64-bit fixed point, the solve in float64 (the
+ *                             default everywhere).
  *   O3G_PREC_F64              J, r and the products in float64 from the float32
  *                             points and normals, each operation rounded once in
  *                             the order r = ((dx nx + dy ny) + dz nz), block sums
- *                             in plain float64 (the precision study's all-FP64
+ *                             in plain float64, then the same fixed-point
+ *                             cross-block sums (the precision study's all-FP64
  *                             variant).
  * Correspondences and the float32 transform are the same under both.
  */
@@ -192,8 +204,9 @@ O3G_API int32_t o3g_normal_equations_ex(const o3g_grid* tgt, const float* d_src,
  * Point-to-plane ICP against a resident target grid that carries normals
  * (registration_icp(source, target, max_correspondence_distance, init,
  * TransformationEstimationPointToPlane()), Sec. 3.3).  Each iteration: the
- * correspondence step, the normal equations, the LDL^T solve of
- * (J^T J) xi = -J^T r (Eq. 2) with xi = (alpha, beta, gamma, tx, ty, tz), and
+ * correspondence step, the normal equations, the solve of
+ * (J^T J) xi = -J^T r (Eq. 2; pivots those of LDL^T) with
+ * xi = (alpha, beta, gamma, tx, ty, tz), and
  * T <- [Rz(gamma) Ry(beta) Rx(alpha), t; 0 1] T.  A pivot D_kk <= 1e-12 max_j A_jj
  * freezes its unknown (status O3G_WARN_DEGENERATE).  Iteration stops after
  * max_iter updates, when fewer than 6 correspondences remain
