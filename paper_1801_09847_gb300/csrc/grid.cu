@@ -334,10 +334,11 @@ __global__ void __launch_bounds__(kThreads) k_set_normals(const float* __restric
     const float* q = nrm + static_cast<int64_t>(o) * stride;
     out[k] = make_float4(q[0], q[1], q[2], 0.f);
     len = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+    if (!isfinite(len)) len = 0.f;  // such a normal, where a correspondence uses it, makes its terms non-finite
   }
-  // out[n].x (zeroed before the launch): the largest normal length, the bound
-  // the ICP sums are scaled by.  Non-negative floats order like their bits as
-  // ints; a NaN length (sqrtf's NaN is positive) orders above every number.
+  // out[n].x (zeroed before the launch): the largest finite normal length, the
+  // bound the ICP sums are scaled by (non-negative floats order like their bits
+  // as ints).
   const int bits = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned>(__float_as_int(len))));
   if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(&out[n].x), bits);
 }

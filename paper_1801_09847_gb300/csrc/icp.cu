@@ -982,8 +982,12 @@ __device__ __forceinline__ int sum_exponent(const PairDesc& P, int k, float nlen
   const float R = P.r * 1.01f, L = nlen * 1.01f, a = P.bnd_a * 1.01f, b = P.bnd_b * 1.01f;
   const float B = slot_bound(P.kind, ix.x, a, b, L, R) * slot_bound(P.kind, ix.y, a, b, L, R) *
                   (static_cast<float>(max(P.ns, 1)) * 1.01f);
-  if (!(B > 0.f)) return 0;  // an empty column (or a NaN bound: the values are then flagged)
+  if (B != B) return -126;    // a NaN bound: report every nonzero term
+  if (!(B > 0.f)) return 0;  // an empty column
   const int e = ((__float_as_int(B) >> 23) & 0xff) - 127;
+  // a bound beyond float range (absurd coordinates): the smallest unit, so that
+  // every nonzero term of the column is reported rather than rounded away
+  if (e == 128) return -126;
   return min(max(e + 1 - 62, -126), 126);
 }
 

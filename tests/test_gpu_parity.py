@@ -358,6 +358,17 @@ def test_nonfinite_normal_reported(o3g):
     with pytest.raises(o3g.O3GError) as e:
         o3g.icp_point_to_plane_grid(grid, cuda(pr.src), np.eye(4), pr.max_corr_dist, 5)
     assert e.value.status == o3g.ERR_NONFINITE
+    # a non-finite normal that no correspondence uses changes nothing: the fixed-point scale takes the
+    # largest finite normal length, and the result meets the oracle's
+    tgt = np.vstack([pr.tgt, np.array([[50.0, 50.0, 50.0], [-50.0, 0.0, 0.0]], np.float32)])
+    nrm2 = np.vstack([pr.tgt_nrm, np.array([[np.nan, 0.0, 1.0], [np.inf, 0.0, 0.0]], np.float32)])
+    g2 = o3g.build_grid(cuda(tgt), pr.max_corr_dist)
+    g2.set_normals(cuda(nrm2))
+    res = o3g.icp_point_to_plane_grid(g2, cuda(pr.src), np.eye(4), pr.max_corr_dist, pr.max_iter)
+    ref = oracle.icp_point_to_plane(pr.src, tgt, nrm2, np.eye(4), pr.max_corr_dist, pr.max_iter)
+    assert res["status"] == ref["status"] and res["iters"] == ref["iters"]
+    ang, dt = synth.pose_error(res["T"], ref["T"])
+    assert ang <= 1e-6 and dt <= 1e-6, (ang, dt)
 
 
 # ------------------------------------------------------------------- ICP
