@@ -2,13 +2,15 @@
 // estimate_normals(pc, KDTreeSearchParamHybrid(radius, max_nn)) of the Open3D
 // paper (Fig. 1, Sec. 3.3), parallel across data samples (Sec. 4).
 //
-// Per point: the at most max_nn grid points with float32 d2 <= fl(radius)^2 in
-// (d2, original index) order; the covariance of the neighbourhood about its mean
-// (float32, offsets taken from the query point first); its smallest-eigenvalue
-// eigenvector by cyclic Jacobi rotations; orientation toward the viewpoint.
-// max_nn <= 32 (the paper's 30 included) runs one warp per point (coalesced
-// candidate loads, bitonic top-k across the lanes); larger max_nn runs one
-// thread per point with an insertion-sorted list in local memory.
+// Per point: the at most max_nn grid points with float32 d2 <= fl(radius)^2,
+// smallest first in (d2, original index) order; the covariance of that
+// neighbourhood about its mean (float32, offsets taken from the query point
+// first); its smallest-eigenvalue eigenvector; orientation toward the
+// viewpoint.  max_nn <= 32 (the paper's 30 included) runs one warp per point:
+// coalesced candidate loads, the box's column runs found by all lanes at once,
+// an exact selection through a histogram of d2, and a closed-form eigenvector.
+// Larger max_nn runs one thread per point with an insertion-sorted list in
+// local memory and cyclic Jacobi rotations.
 #include <cmath>
 
 #include <vector>
@@ -161,13 +163,24 @@ __device__ float3 smallest_eigvec_closed(const float a[3][3]) {
 
 // ---------------------------------------------------------------------------
 // Warp-cooperative hybrid search (max_nn <= 32): one warp per query.  Lanes
-// load consecutive points of a cell column (coalesced), keep those within the
-// radius and below the current k-th key, compact them into a 64-entry staging
-// buffer in shared memory, and whenever 32 are staged sort them with a bitonic
-// network across the lanes and merge them into the running list (lane j holds
-// the j-th smallest key).  Keys are (d2 bits << 32 | original index), so the
-// order is (d2, index) and the result is the exact set the definition gives.
+// load consecutive points of a cell column (coalesced) and append the keys of
+// those within the radius to the warp's buffer in shared memory; keys are
+// (d2 bits << 32 | original index), so their order is (d2, index) and the
+// result is the exact set the definition gives.  The max_nn smallest are then
+// selected in two steps: a histogram of d2 finds the bin that holds the
+// max_nn-th smallest key, and only the keys up to that bin (typically max_nn to
+// max_nn + 2) are kept.  kNN queries sort them (one bitonic network across the
+// lanes); normals need only the set, so they rank just the few keys of that
+// last bin.  A buffer that fills up is cut down to its max_nn smallest keys the
+// same way, and from then on only keys below the max_nn-th are appended.
 constexpr uint64_t kNoKey = ~0ull;
+constexpr int kStageCap = 256;  // keys buffered per warp
+constexpr int kBins = 128;      // histogram bins of the selection, four per lane
+
+struct alignas(16) WarpStage {
+  uint64_t key[kStageCap];
+  uint32_t hist[kBins];
+};
 
 __device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
   return __shfl_xor_sync(0xffffffffu, v, m);
@@ -200,8 +213,104 @@ __device__ __forceinline__ uint64_t warp_merge32(uint64_t list, uint64_t batch, 
   return v;
 }
 
-// Returns lane `lane`'s entry of the sorted list of the <= max_nn nearest keys.
-__device__ uint64_t warp_knn(const GridView& g, float qx, float qy, float qz, float r, int max_nn, uint64_t* stage) {
+__device__ __forceinline__ float key_d2(uint64_t key) {
+  return __uint_as_float(static_cast<uint32_t>(key >> 32));
+}
+
+// Histogram bin of a key: non-decreasing in the key (a correctly rounded
+// product of non-negative floats, truncated and clamped, keeps their order).
+__device__ __forceinline__ int key_bin(uint64_t key, float scale) {
+  return min(static_cast<int>(__fmul_rn(key_d2(key), scale)), kBins - 1);
+}
+
+// The k (<= 32) smallest of the m keys s.key[0, m), ascending, lane j holding
+// the j-th (kNoKey past the end); every key has d2 <= hi.  With more than 32
+// keys, a histogram of d2 over [0, hi] gives the bin b of the k-th smallest;
+// since bins follow the key order, the k smallest are among the keys of bins
+// <= b, which are moved to the front of the buffer.  While more than 32 remain,
+// the same is repeated over the range of those bins (a few rounds at most),
+// then the rest is sorted.  Should more than 32 keys still be left (ties), they
+// are sorted and merged 32 at a time.  Any scale gives non-decreasing bins, so
+// the range only decides how fast the keys thin out.  With ordered false the
+// result may instead be the same set unsorted: lanes below m hold the selected
+// keys or kNoKey, in buffer order.  All lanes must call this.
+__device__ uint64_t warp_select(WarpStage& s, int m, int k, float hi, int lane, bool ordered = true) {
+  const unsigned full = 0xffffffffu;
+  __syncwarp();
+  float scale = __fdiv_rn(static_cast<float>(kBins), hi);
+  int last_b = -1;
+  uint32_t last_nb = 0;
+  float last_scale = 0.f;
+  for (int round = 0; m > 32 && round < 3 && scale <= 3.0e38f; ++round) {  // hi = 0: no histogram
+    reinterpret_cast<uint4*>(s.hist)[lane] = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+    for (int i = lane; i < m; i += 32) atomicAdd(&s.hist[key_bin(s.key[i], scale)], 1u);
+    __syncwarp();
+    const uint4 c = reinterpret_cast<const uint4*>(s.hist)[lane];
+    const uint32_t own = c.x + c.y + c.z + c.w;
+    uint32_t incl = own;  // keys in the bins of lanes 0..lane
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(full, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const uint32_t uk = static_cast<uint32_t>(k);
+    const int src = __ffs(__ballot_sync(full, incl >= uk)) - 1;  // incl of lane 31 is m > k
+    const uint32_t e0 = incl - own + c.x, e1 = e0 + c.y, e2 = e1 + c.z;
+    const int sub = e0 >= uk ? 0 : e1 >= uk ? 1 : e2 >= uk ? 2 : 3;
+    const int b = 4 * src + __shfl_sync(full, sub, src);
+    last_nb = __shfl_sync(full, sub == 0 ? c.x : sub == 1 ? c.y : sub == 2 ? c.z : c.w, src);
+    last_b = b;
+    last_scale = scale;
+    int w = 0;
+    for (int base = 0; base < m; base += 32) {  // in place: writes stay below base + 32
+      const int i = base + lane;
+      const uint64_t key = i < m ? s.key[i] : kNoKey;
+      const bool sel = i < m && key_bin(key, scale) <= b;
+      const uint32_t mask = __ballot_sync(full, sel);
+      if (sel) s.key[w + __popc(mask & ((1u << lane) - 1u))] = key;
+      w += __popc(mask);
+    }
+    __syncwarp();
+    m = w;
+    if (b == kBins - 1) break;  // nothing was dropped, and the range would not narrow
+    scale = __fmul_rn(scale, __fdiv_rn(static_cast<float>(kBins), static_cast<float>(b + 1)));
+  }
+  if (!ordered && last_b >= 0 && m <= 32) {
+    // the keys of bins below last_b are all in; of the last_nb keys in bin
+    // last_b, the (k - those below) smallest, by their rank within the bin
+    const uint64_t v = lane < m ? s.key[lane] : kNoKey;
+    const bool inb = lane < m && key_bin(v, last_scale) == last_b;
+    const uint32_t need = static_cast<uint32_t>(k) - (static_cast<uint32_t>(m) - last_nb);
+    bool keep = lane < m;
+    if (last_nb > need) {
+      uint32_t mb = __ballot_sync(full, inb), rank = 0;
+      while (mb) {
+        const int j = __ffs(mb) - 1;
+        mb &= mb - 1u;
+        const uint64_t o = __shfl_sync(full, v, j);
+        rank += o < v ? 1u : 0u;
+      }
+      keep = keep && (!inb || rank < need);
+    }
+    return keep ? v : kNoKey;
+  }
+  if (m <= 32) {
+    const uint64_t v = warp_sort32(lane < m ? s.key[lane] : kNoKey, lane);
+    return lane < k ? v : kNoKey;
+  }
+  uint64_t list = kNoKey;
+  for (int base = 0; base < m; base += 32) {
+    const uint64_t v = warp_sort32(base + lane < m ? s.key[base + lane] : kNoKey, lane);
+    list = warp_merge32(list, v, lane);
+  }
+  return lane < k ? list : kNoKey;
+}
+
+// Returns lane `lane`'s entry of the <= max_nn nearest keys: lane j holds the
+// j-th when ordered, otherwise the set sits on some lanes (kNoKey on the rest).
+__device__ uint64_t warp_knn(const GridView& g, float qx, float qy, float qz, float r, int max_nn, WarpStage& s,
+                             bool ordered = true) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   const float r2 = __fmul_rn(r, r);
@@ -209,16 +318,31 @@ __device__ uint64_t warp_knn(const GridView& g, float qx, float qy, float qz, fl
   axis_range(qx, r, g.inv_cell, g.lo_x, g.sx, ax, bx);
   axis_range(qy, r, g.inv_cell, g.lo_y, g.sy, ay, by);
   axis_range(qz, r, g.inv_cell, g.lo_z, g.sz, az, bz);
-  uint64_t list = kNoKey;
-  uint64_t thr = kNoKey;  // current max_nn-th key (keys must be < thr to matter)
-  int staged = 0;
-  if (ax > bx || ay > by || az > bz) return list;
-  for (int x = ax; x <= bx; ++x) {
-    for (int y = ay; y <= by; ++y) {
+  if (ax > bx || ay > by || az > bz) return kNoKey;
+  uint64_t thr = kNoKey;  // once the buffer was cut down: its max_nn-th key (keys must be < thr to matter)
+  float hi = r2;          // every buffered key has d2 <= hi
+  int m = 0;              // keys in the buffer
+  // The box's (x, y) columns, 32 at a time: lane c finds the run of sorted
+  // points of column c over the box's z-range (two loads, all columns at once),
+  // then the warp scans the runs one after another.
+  const uint32_t ny = by - ay + 1, ncols = (bx - ax + 1) * ny;  // <= the grid's cells < 2^31
+  for (uint32_t c0 = 0; c0 < ncols; c0 += 32) {
+    uint32_t rb = 0, re = 0;
+    const uint32_t c = c0 + lane;
+    if (c < ncols) {
+      const int x = ax + static_cast<int>(c / ny), y = ay + static_cast<int>(c % ny);
       int zl = az, zh = bz;
-      if (!column_z(g, x * g.sy + y, zl, zh)) continue;
-      const int col = (x * g.sy + y) * g.sz;
-      const uint32_t beg = g.cell_start[col + zl], end = g.cell_start[col + zh + 1];
+      if (column_z(g, x * g.sy + y, zl, zh)) {
+        const int col = (x * g.sy + y) * g.sz;
+        rb = g.cell_start[col + zl];
+        re = g.cell_start[col + zh + 1];
+      }
+    }
+    uint32_t runs = __ballot_sync(0xffffffffu, rb < re);
+    while (runs) {
+      const int src = __ffs(runs) - 1;
+      runs &= runs - 1u;
+      const uint32_t beg = __shfl_sync(0xffffffffu, rb, src), end = __shfl_sync(0xffffffffu, re, src);
       for (uint32_t k0 = beg; k0 < end; k0 += 32) {
         const uint32_t k = k0 + lane;
         uint64_t key = kNoKey;
@@ -228,33 +352,25 @@ __device__ uint64_t warp_knn(const GridView& g, float qx, float qy, float qz, fl
           if (d2 <= r2)
             key = (static_cast<uint64_t>(__float_as_uint(d2)) << 32) | static_cast<uint32_t>(__float_as_int(q.w));
         }
-        const bool keep = key < thr;
-        const uint32_t mask = __ballot_sync(0xffffffffu, keep);
+        bool keep = key < thr;
+        uint32_t mask = __ballot_sync(0xffffffffu, keep);
         if (mask == 0u) continue;
-        if (keep) stage[staged + __popc(mask & lt)] = key;
-        staged += __popc(mask);
-        __syncwarp();
-        if (staged >= 32) {
-          const uint64_t batch = warp_sort32(stage[lane], lane);
-          list = warp_merge32(list, batch, lane);
-          thr = __shfl_sync(0xffffffffu, list, max_nn - 1);
+        if (m + __popc(mask) > kStageCap) {  // m > kStageCap - 32 >= max_nn: the cut keeps max_nn keys
+          const uint64_t v = warp_select(s, m, max_nn, hi, lane);
           __syncwarp();
-          const int rest = staged - 32;
-          const uint64_t carry = lane < rest ? stage[32 + lane] : kNoKey;
-          __syncwarp();
-          if (lane < rest) stage[lane] = carry;
-          staged = rest;
-          __syncwarp();
+          if (lane < max_nn) s.key[lane] = v;
+          m = max_nn;
+          thr = __shfl_sync(0xffffffffu, v, max_nn - 1);
+          hi = key_d2(thr);
+          keep = key < thr;
+          mask = __ballot_sync(0xffffffffu, keep);
         }
+        if (keep) s.key[m + __popc(mask & lt)] = key;
+        m += __popc(mask);
       }
     }
   }
-  if (staged > 0) {
-    const uint64_t batch = warp_sort32(lane < staged ? stage[lane] : kNoKey, lane);
-    list = warp_merge32(list, batch, lane);
-    __syncwarp();
-  }
-  return lane < max_nn ? list : kNoKey;
+  return warp_select(s, m, max_nn, hi, lane, ordered);
 }
 
 constexpr int kWarpsPerBlock = kThreads / 32;
@@ -267,13 +383,14 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // Normal of sorted point k of grid g, computed by one whole warp (stage: that
-// warp's 64 staging slots).  Lane 0 stores it.
+// warp's key buffer).  The sums run over the lanes in a fixed order, so the
+// result depends only on the grid and the point.  Lane 0 stores it.
 __device__ void warp_normal(const GridView& g, const int32_t* __restrict__ pos_of, int k, float radius, int max_nn,
                             float vx, float vy, float vz, float4* __restrict__ nrm_sorted, float* __restrict__ out,
-                            int out_stride, uint64_t* stage) {
+                            int out_stride, WarpStage& stage) {
   const int lane = threadIdx.x & 31;
   const float4 q = g.pts[k];
-  const uint64_t key = warp_knn(g, q.x, q.y, q.z, radius, max_nn, stage);
+  const uint64_t key = warp_knn(g, q.x, q.y, q.z, radius, max_nn, stage, false);
   const bool have = key != kNoKey;
   const int m = __popc(__ballot_sync(0xffffffffu, have));
   float3 n = make_float3(0.f, 0.f, 1.f);
@@ -315,11 +432,11 @@ __device__ void warp_normal(const GridView& g, const int32_t* __restrict__ pos_o
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_normals_warp(GridView g, const int32_t* __restrict__ pos_of,
+__global__ void __launch_bounds__(kThreads, 10) k_normals_warp(GridView g, const int32_t* __restrict__ pos_of,
                                                            float radius, int max_nn, float vx, float vy, float vz,
                                                            float4* __restrict__ nrm_sorted, float* __restrict__ out,
                                                            int out_stride) {
-  __shared__ uint64_t stage_all[kWarpsPerBlock][64];
+  __shared__ WarpStage stage_all[kWarpsPerBlock];
   const int warp = threadIdx.x >> 5;
   const int k = blockIdx.x * kWarpsPerBlock + warp;
   if (k == 0 && threadIdx.x == 0) nrm_sorted[g.n] = make_float4(1.f, 0.f, 0.f, 0.f);  // length bound: unit normals
@@ -356,10 +473,10 @@ __device__ __forceinline__ int job_of(const int64_t* __restrict__ first, int njo
 
 // Normals of many clouds in one launch: warp w takes point w - first[j] of
 // job j, so every point gets exactly the computation the one-cloud launch gives it.
-__global__ void __launch_bounds__(kThreads) k_normals_batch(const NormalsJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kThreads, 9) k_normals_batch(const NormalsJob* __restrict__ jobs,
                                                             const int64_t* __restrict__ first, int njobs,
                                                             int64_t total, int max_nn) {
-  __shared__ uint64_t stage_all[kWarpsPerBlock][64];
+  __shared__ WarpStage stage_all[kWarpsPerBlock];
   const int warp = threadIdx.x >> 5;
   const int64_t w = static_cast<int64_t>(blockIdx.x) * kWarpsPerBlock + warp;
   if (w >= total) return;
@@ -375,7 +492,7 @@ __global__ void __launch_bounds__(kThreads) k_normals_batch(const NormalsJob* __
 // Hybrid kNN of query i, computed by one whole warp.
 __device__ void warp_query(const GridView& g, const float* __restrict__ qry, int i, int stride, float radius,
                            int max_nn, int32_t* __restrict__ idx, float* __restrict__ dd, int32_t* __restrict__ cnt,
-                           uint64_t* stage) {
+                           WarpStage& stage) {
   const int lane = threadIdx.x & 31;
   const float* q = qry + static_cast<int64_t>(i) * stride;
   const uint64_t key = warp_knn(g, q[0], q[1], q[2], radius, max_nn, stage);
@@ -391,7 +508,7 @@ __device__ void warp_query(const GridView& g, const float* __restrict__ qry, int
 __global__ void __launch_bounds__(kThreads) k_knn_warp(GridView g, const float* __restrict__ qry, int nq, int stride,
                                                        float radius, int max_nn, int32_t* __restrict__ idx,
                                                        float* __restrict__ dd, int32_t* __restrict__ cnt) {
-  __shared__ uint64_t stage_all[kWarpsPerBlock][64];
+  __shared__ WarpStage stage_all[kWarpsPerBlock];
   const int warp = threadIdx.x >> 5;
   const int i = blockIdx.x * kWarpsPerBlock + warp;
   if (i >= nq) return;
@@ -403,7 +520,7 @@ __global__ void __launch_bounds__(kThreads) k_knn_warp(GridView g, const float* 
 __global__ void __launch_bounds__(kThreads) k_knn_batch(const NormalsJob* __restrict__ jobs,
                                                         const int64_t* __restrict__ first, int njobs, int64_t total,
                                                         int max_nn) {
-  __shared__ uint64_t stage_all[kWarpsPerBlock][64];
+  __shared__ WarpStage stage_all[kWarpsPerBlock];
   const int warp = threadIdx.x >> 5;
   const int64_t w = static_cast<int64_t>(blockIdx.x) * kWarpsPerBlock + warp;
   if (w >= total) return;

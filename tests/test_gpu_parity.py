@@ -195,6 +195,34 @@ def test_knn_room_frame_sampled(o3g, room):
     assert np.array_equal(d2.cpu().numpy(), d_ref)
 
 
+def crowded_cloud(g):
+    """A dense cube (thousands of points within the radius of every query, far more than a warp
+    buffers), 700 copies of one point (keys that differ only by index, all at d2 = 0) and a
+    cluster around that point."""
+    cube = g.uniform(-0.05, 0.05, (3000, 3))
+    copies = np.tile([[0.31, 0.32, 0.33]], (700, 1))
+    near = np.array([0.31, 0.32, 0.33]) + g.uniform(-0.01, 0.01, (500, 3))
+    pts = np.vstack([cube, near[:250], copies, near[250:]]).astype(np.float32)
+    qry = np.vstack([pts[::13], pts[3250:3260], g.uniform(-0.06, 0.06, (100, 3)),
+                     np.array([0.31, 0.32, 0.33]) + g.uniform(-0.012, 0.012, (100, 3))]).astype(np.float32)
+    return pts, qry
+
+
+@pytest.mark.parametrize("radius,max_nn", [(0.2, 30), (0.2, 32), (0.2, 1), (0.03, 30), (0.012, 7), (0.0, 30)])
+def test_knn_crowded_neighbourhoods_bitexact(o3g, radius, max_nn):
+    """More keys within the radius than the warp buffers (the buffer is cut to its max_nn smallest
+    and later keys are filtered), hundreds of exactly tied distances (the selection's distance
+    histogram puts them all in one bin), and radius 0 (only exact copies of the query qualify)."""
+    pts, qry = crowded_cloud(synth.rng(41))
+    grid = o3g.build_grid(cuda(pts), 0.1)
+    idx, d2, cnt = o3g.knn_hybrid(grid, cuda(qry), radius, max_nn)
+    i_ref, d_ref, c_ref = oracle.knn_hybrid(pts, qry, radius, max_nn)
+    assert np.array_equal(cnt.cpu().numpy(), c_ref)
+    assert np.array_equal(idx.cpu().numpy(), i_ref)
+    assert np.array_equal(d2.cpu().numpy(), d_ref)
+    assert c_ref.max() == max_nn or radius == 0.0
+
+
 # --------------------------------------------------------------- normals
 
 
@@ -250,6 +278,15 @@ def test_normals_room_frame_sampled(o3g, room):
     n_ora_s = None  # the oracle computes all normals; sample the comparison only
     check_normals(room.tgt, n_gpu, 0.05, 30, (0.0, 0.0, 0.0), sample=sample)
     del n_ora_s
+
+
+def test_normals_dense_cube(o3g):
+    """Thousands of points within the radius of every point: the warp's key buffer is cut down to
+    its 30 nearest several times before the neighbourhood is known."""
+    pts = synth.rng(43).uniform(-0.05, 0.05, (3000, 3)).astype(np.float32)
+    grid = o3g.build_grid(cuda(pts), 0.1)
+    n_gpu = grid.estimate_normals(0.2, 30, viewpoint=(1.0, 0.0, 0.0)).cpu().numpy()
+    check_normals(pts, n_gpu, 0.2, 30, (1.0, 0.0, 0.0))
 
 
 def test_normals_degenerate_neighbourhoods(o3g):
