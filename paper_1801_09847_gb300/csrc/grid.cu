@@ -99,17 +99,14 @@ __global__ void __launch_bounds__(kThreads) k_bbox(const float* __restrict__ xyz
 
 // ---------------------------------------------------------------- keys
 
-__global__ void __launch_bounds__(kThreads) k_keys(const float* __restrict__ xyz, int n, int stride, float inv, int lx,
-                                                   int ly, int lz, uint32_t sy, uint32_t sz, uint32_t* __restrict__ keys,
-                                                   uint32_t* __restrict__ vals) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// Linear cell key of point i.
+__device__ __forceinline__ uint32_t cell_key(const float* __restrict__ xyz, int i, int stride, float inv, int lx, int ly,
+                                             int lz, uint32_t sy, uint32_t sz) {
   const float* p = xyz + static_cast<int64_t>(i) * stride;
   uint32_t cx = static_cast<uint32_t>(cell_coord(p[0], inv) - lx);
   uint32_t cy = static_cast<uint32_t>(cell_coord(p[1], inv) - ly);
   uint32_t cz = static_cast<uint32_t>(cell_coord(p[2], inv) - lz);
-  keys[i] = (cx * sy + cy) * sz + cz;
-  vals[i] = static_cast<uint32_t>(i);
+  return (cx * sy + cy) * sz + cz;
 }
 
 // -------------------------------------------------------- exclusive scan
@@ -202,7 +199,21 @@ __global__ void __launch_bounds__(kThreads) k_scan_down(const uint32_t* __restri
 constexpr int kRsRounds = 8;
 constexpr int kRsTile = kThreads * kRsRounds;
 constexpr int kWarps = kThreads / 32;
+// Sorts of at most this many tiles skip the separate scan of the per-tile digit
+// counts: each scatter block sums the counts it needs itself (every block reads
+// all nblk x 256 counts once, which beats three more launches while nblk is small).
+constexpr int kRsInlineBlocks = 160;
 
+// Per-tile digit counts: digit-major (count of digit d in tile b at d * nblk +
+// b, the order whose exclusive scan gives every tile's offsets) or, with
+// kTileMajor, at b * 256 + d for the scatter to sum itself.
+template <bool kTileMajor>
+__device__ __forceinline__ void store_hist(uint32_t* __restrict__ hist, int nblk, uint32_t count) {
+  if (kTileMajor) hist[static_cast<size_t>(blockIdx.x) * 256 + threadIdx.x] = count;
+  else hist[static_cast<size_t>(threadIdx.x) * nblk + blockIdx.x] = count;
+}
+
+template <bool kTileMajor>
 __global__ void __launch_bounds__(kThreads) k_rs_hist(const uint32_t* __restrict__ keys, int n, int shift,
                                                       uint32_t* __restrict__ hist, int nblk) {
   __shared__ uint32_t h[256];
@@ -215,12 +226,41 @@ __global__ void __launch_bounds__(kThreads) k_rs_hist(const uint32_t* __restrict
     if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
   }
   __syncthreads();
-  hist[static_cast<size_t>(threadIdx.x) * nblk + blockIdx.x] = h[threadIdx.x];
+  store_hist<kTileMajor>(hist, nblk, h[threadIdx.x]);
+}
+
+// The grid build's first step: cell keys (and identity values) of tile b, with
+// the tile's counts of the first sort digit.
+template <bool kTileMajor>
+__global__ void __launch_bounds__(kThreads) k_keys_hist(const float* __restrict__ xyz, int n, int stride, float inv,
+                                                        int lx, int ly, int lz, uint32_t sy, uint32_t sz,
+                                                        uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                        uint32_t* __restrict__ hist, int nblk) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  int base = blockIdx.x * kRsTile;
+#pragma unroll
+  for (int r = 0; r < kRsRounds; ++r) {
+    int i = base + r * kThreads + threadIdx.x;
+    if (i < n) {
+      const uint32_t k = cell_key(xyz, i, stride, inv, lx, ly, lz, sy, sz);
+      keys[i] = k;
+      vals[i] = static_cast<uint32_t>(i);
+      atomicAdd(&h[k & 255u], 1u);
+    }
+  }
+  __syncthreads();
+  store_hist<kTileMajor>(hist, nblk, h[threadIdx.x]);
 }
 
 // Stable scatter of one tile: elements keep their input order within a digit.
 // Rounds walk the tile in order; inside a round, warps in order; inside a warp,
-// lanes in order (rank among equal digits via __match_any_sync).
+// lanes in order (rank among equal digits via __match_any_sync).  The tile's
+// first output position for each digit comes from the scanned digit-major
+// counts or, with kInline, from the tile-major counts: all tiles' counts of
+// smaller digits plus the earlier tiles' counts of the same digit.
+template <bool kInline>
 __global__ void __launch_bounds__(kThreads) k_rs_scatter(const uint32_t* __restrict__ kin,
                                                          const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
                                                          uint32_t* __restrict__ vout, int n, int shift,
@@ -230,7 +270,18 @@ __global__ void __launch_bounds__(kThreads) k_rs_scatter(const uint32_t* __restr
   __shared__ uint32_t total[256];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt = (1u << lane) - 1u;
-  base[tid] = offs[static_cast<size_t>(tid) * nblk + blockIdx.x];
+  if (kInline) {
+    uint32_t all = 0, before = 0;
+    for (int b = 0; b < nblk; ++b) {
+      const uint32_t c = offs[static_cast<size_t>(b) * 256 + tid];
+      all += c;
+      before += b < static_cast<int>(blockIdx.x) ? c : 0u;
+    }
+    uint32_t sum;
+    base[tid] = block_exclusive_scan(all, &sum) + before;
+  } else {
+    base[tid] = offs[static_cast<size_t>(tid) * nblk + blockIdx.x];
+  }
   const int tile0 = blockIdx.x * kRsTile;
   for (int r = 0; r < kRsRounds; ++r) {
 #pragma unroll
@@ -284,39 +335,52 @@ __global__ void __launch_bounds__(kThreads) k_cell_start(const uint32_t* __restr
 // Per (x, y) column: the lowest and highest occupied z-cell, from cell_start by
 // binary search (cell_start is non-decreasing along the column).  Empty columns
 // get lowest = 0xffff, highest = 0, an empty range.
-__global__ void __launch_bounds__(kThreads) k_col_extent(const uint32_t* __restrict__ cell_start, int ncol, int sz,
-                                                         uint32_t* __restrict__ col_z) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncol; c += gridDim.x * blockDim.x) {
-    const uint32_t* cs = cell_start + static_cast<int64_t>(c) * sz;
-    const uint32_t first = cs[0], last = cs[sz];
-    if (first == last) {
-      col_z[c] = 0xffffu;
-      continue;
-    }
-    int lo = 0, hi = sz - 1;  // lowest z with cs[z + 1] > first
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (cs[mid + 1] > first) hi = mid;
-      else lo = mid + 1;
-    }
-    const int zmin = lo;
-    lo = 0;
-    hi = sz - 1;  // highest z with cs[z] < last
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (cs[mid] < last) lo = mid;
-      else hi = mid - 1;
-    }
-    col_z[c] = static_cast<uint32_t>(zmin) | (static_cast<uint32_t>(lo) << 16);
+__device__ __forceinline__ void col_extent(const uint32_t* __restrict__ cell_start, int c, int sz,
+                                           uint32_t* __restrict__ col_z) {
+  const uint32_t* cs = cell_start + static_cast<int64_t>(c) * sz;
+  const uint32_t first = cs[0], last = cs[sz];
+  if (first == last) {
+    col_z[c] = 0xffffu;
+    return;
   }
+  int lo = 0, hi = sz - 1;  // lowest z with cs[z + 1] > first
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (cs[mid + 1] > first) hi = mid;
+    else lo = mid + 1;
+  }
+  const int zmin = lo;
+  lo = 0;
+  hi = sz - 1;  // highest z with cs[z] < last
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cs[mid] < last) lo = mid;
+    else hi = mid - 1;
+  }
+  col_z[c] = static_cast<uint32_t>(zmin) | (static_cast<uint32_t>(lo) << 16);
 }
 
 __global__ void k_empty_col(uint32_t* col_z) { col_z[0] = 0xffffu; }
 
-__global__ void __launch_bounds__(kThreads) k_gather(const float* __restrict__ xyz, int n, int stride,
-                                                     const uint32_t* __restrict__ perm, float4* __restrict__ pts,
-                                                     int32_t* __restrict__ pos_of) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
+// The grid's last step, two independent parts in one launch: blocks below nbz
+// find the occupied z-range of every (x, y) column (grid-stride), the others
+// copy the points into cell order (point k of the sorted order is input point
+// perm[k]), record where each input point went and zero the normals' length
+// bound (no normals yet).
+__global__ void __launch_bounds__(kThreads) k_col_extent_gather(const uint32_t* __restrict__ cell_start, int ncol,
+                                                                int sz, uint32_t* __restrict__ col_z, int nbz,
+                                                                const float* __restrict__ xyz, int n, int stride,
+                                                                const uint32_t* __restrict__ perm,
+                                                                float4* __restrict__ pts,
+                                                                int32_t* __restrict__ pos_of,
+                                                                float4* __restrict__ nrm) {
+  if (static_cast<int>(blockIdx.x) < nbz) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncol; c += nbz * blockDim.x)
+      col_extent(cell_start, c, sz, col_z);
+    return;
+  }
+  int k = (blockIdx.x - nbz) * blockDim.x + threadIdx.x;
+  if (k == 0) nrm[n] = make_float4(0.f, 0.f, 0.f, 0.f);
   if (k >= n) return;
   uint32_t o = perm[k];
   const float* p = xyz + static_cast<int64_t>(o) * stride;
@@ -652,22 +716,41 @@ int32_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t m, cudaStr
   return O3G_OK;
 }
 
+int rs_tiles(int n) { return blocks_for(n, kRsTile); }
+bool rs_inline(int nblk) { return nblk <= kRsInlineBlocks; }
+
 // Stable sort of (keys, vals) by the low `bits` bits of the keys.  The sorted
-// pairs end in (keys, vals); tmp_k/tmp_v are scratch of the same size.
+// pairs end in (keys, vals); tmp_k/tmp_v are scratch of the same size.  With
+// hist0 non-null, the first pass's per-tile digit counts are already there
+// (256 x rs_tiles(n) entries, tile-major when rs_inline, digit-major
+// otherwise) and the buffer serves all passes.
 int32_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* tmp_k, uint32_t* tmp_v, int n, int bits,
-                         cudaStream_t s) {
+                         cudaStream_t s, uint32_t* hist0) {
   if (n <= 1 || bits <= 0) return O3G_OK;
-  int nblk = blocks_for(n, kRsTile);
-  DevBuf hist(s);
-  O3G_TRY(hist.alloc(sizeof(uint32_t) * 256 * static_cast<size_t>(nblk)));
+  const int nblk = rs_tiles(n);
+  const bool inl = rs_inline(nblk);
+  DevBuf own(s);
+  uint32_t* hist = hist0;
+  if (!hist) {
+    O3G_TRY(own.alloc(sizeof(uint32_t) * 256 * static_cast<size_t>(nblk)));
+    hist = own.as<uint32_t>();
+  }
   uint32_t *ka = keys, *va = vals, *kb = tmp_k, *vb = tmp_v;
   int passes = (bits + 7) / 8;
   for (int p = 0; p < passes; ++p) {
     int shift = 8 * p;
-    k_rs_hist<<<nblk, kThreads, 0, s>>>(ka, n, shift, hist.as<uint32_t>(), nblk);
-    O3G_TRY_STATUS(exclusive_scan_u32(hist.as<uint32_t>(), hist.as<uint32_t>(), 256LL * nblk, s));
-    k_rs_scatter<<<nblk, kThreads, 0, s>>>(ka, va, kb, vb, n, shift, hist.as<uint32_t>(), nblk);
-    count_launch(2);
+    if (p > 0 || !hist0) {
+      if (inl) k_rs_hist<true><<<nblk, kThreads, 0, s>>>(ka, n, shift, hist, nblk);
+      else k_rs_hist<false><<<nblk, kThreads, 0, s>>>(ka, n, shift, hist, nblk);
+      count_launch();
+    }
+    if (inl) {
+      k_rs_scatter<true><<<nblk, kThreads, 0, s>>>(ka, va, kb, vb, n, shift, hist, nblk);
+    } else {
+      O3G_TRY_STATUS(exclusive_scan_u32(hist, hist, 256LL * nblk, s));
+      k_rs_scatter<false><<<nblk, kThreads, 0, s>>>(ka, va, kb, vb, n, shift, hist, nblk);
+    }
+    count_launch();
     O3G_TRY(cudaGetLastError());
     uint32_t* t = ka;
     ka = kb;
@@ -770,21 +853,27 @@ static int32_t build_impl(const float* d_xyz, int64_t n64, int stride, float cel
   O3G_TRY(vals.alloc(sizeof(uint32_t) * n));
   O3G_TRY(tk.alloc(sizeof(uint32_t) * n));
   O3G_TRY(tv.alloc(sizeof(uint32_t) * n));
-  k_keys<<<blocks_for(n, kThreads), kThreads, 0, s>>>(d_xyz, n, stride, inv, h[0], h[1], h[2],
-                                                      static_cast<uint32_t>(span[1]), static_cast<uint32_t>(span[2]),
-                                                      keys.as<uint32_t>(), vals.as<uint32_t>());
+  const int nblk = rs_tiles(n);
+  DevBuf hist(s);
+  O3G_TRY(hist.alloc(sizeof(uint32_t) * 256 * static_cast<size_t>(nblk)));
+  const uint32_t sy = static_cast<uint32_t>(span[1]), sz = static_cast<uint32_t>(span[2]);
+  if (rs_inline(nblk))
+    k_keys_hist<true><<<nblk, kThreads, 0, s>>>(d_xyz, n, stride, inv, h[0], h[1], h[2], sy, sz, keys.as<uint32_t>(),
+                                                vals.as<uint32_t>(), hist.as<uint32_t>(), nblk);
+  else
+    k_keys_hist<false><<<nblk, kThreads, 0, s>>>(d_xyz, n, stride, inv, h[0], h[1], h[2], sy, sz, keys.as<uint32_t>(),
+                                                 vals.as<uint32_t>(), hist.as<uint32_t>(), nblk);
   count_launch();
   O3G_TRY(cudaGetLastError());
   int bits = 0;
   while (bits < 32 && (static_cast<uint64_t>(cells - 1) >> bits) != 0) ++bits;
   O3G_TRY_STATUS(radix_sort_pairs(keys.as<uint32_t>(), vals.as<uint32_t>(), tk.as<uint32_t>(), tv.as<uint32_t>(), n,
-                                  bits, s));
+                                  bits, s, hist.as<uint32_t>()));
 
   // 4-5. cell table and sorted points
   O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->cell_start), sizeof(uint32_t) * (cells + 1), s));
   O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->pts), sizeof(float4) * n, s));
   O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->nrm), sizeof(float4) * (n + 1), s));
-  O3G_TRY(cudaMemsetAsync(g->nrm + n, 0, sizeof(float4), s));
   O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->pos_of), sizeof(int32_t) * n, s));
   int nbc = blocks_for(cells + 1, kThreads);
   if (nbc > kNumSMs * 16) nbc = kNumSMs * 16;
@@ -793,9 +882,9 @@ static int32_t build_impl(const float* d_xyz, int64_t n64, int stride, float cel
   O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->col_z), sizeof(uint32_t) * ncol, s));
   int nbz = blocks_for(ncol, kThreads);
   if (nbz > kNumSMs * 16) nbz = kNumSMs * 16;
-  k_col_extent<<<nbz, kThreads, 0, s>>>(g->cell_start, ncol, g->span[2], g->col_z);
-  count_launch();
-  k_gather<<<blocks_for(n, kThreads), kThreads, 0, s>>>(d_xyz, n, stride, vals.as<uint32_t>(), g->pts, g->pos_of);
+  k_col_extent_gather<<<nbz + blocks_for(n, kThreads), kThreads, 0, s>>>(
+      g->cell_start, ncol, g->span[2], g->col_z, nbz, d_xyz, n, stride, vals.as<uint32_t>(), g->pts, g->pos_of,
+      g->nrm);
   count_launch(2);
   O3G_TRY(cudaGetLastError());
   return O3G_OK;

@@ -81,7 +81,7 @@ int32_t sort_cloud(const float* d_xyz, int64_t n, int32_t stride, cudaStream_t s
 int32_t sort_clouds_batch(const float* const* d_ptrs, const int32_t* d_strides, const int64_t* d_offsets,
                           int n_pairs, int64_t total, cudaStream_t s, float4* out, int* aux);
 int32_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* tmp_k, uint32_t* tmp_v, int n, int bits,
-                         cudaStream_t s);
+                         cudaStream_t s, uint32_t* hist0 = nullptr);
 
 // ------------------------------------------------------------ the grid
 
