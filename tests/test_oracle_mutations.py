@@ -38,6 +38,7 @@ VOX = [("test_voxel_downsample_matches_numpy_bitexact", (20000, 0.1, 1.0)), ("te
 GRID = [("test_grid_nn_partners_at_the_radius_anywhere_in_a_cell", ()), ("test_grid_nn_on_a_lattice_at_the_radius", ()),
         ("test_grid_nn_equals_bruteforce_bitexact", (3000, 3000, 0.05, 1.0))]
 EVAL = [("test_evaluate_poses_matches_independent_bruteforce", ())]
+KNN = [("test_knn_matches_numpy_bruteforce", ()), ("test_knn_radius_boundary_and_ties", ())]
 
 MUTATIONS = [
     ("nn tie keeps the last index", "if (best < 0 || d2 < best_d2) {", "if (best < 0 || d2 <= best_d2) {", NN),
@@ -68,6 +69,13 @@ MUTATIONS = [
     ("grid cell narrower than r", "g->inv_h = 1.0 / (1.01 * (double)r_max);",
      "g->inv_h = 1.0 / (0.999 * (double)r_max);", GRID),
     ("grid drops a neighbour layer", "for (int dz = -1; dz <= 1; ++dz)", "for (int dz = -1; dz <= 0; ++dz)", GRID),
+    ("knn ties to the higher index", "  if (x->d2 > y->d2) return 1;\n  return (x->j > y->j) - (x->j < y->j);",
+     "  if (x->d2 > y->d2) return 1;\n  return (x->j < y->j) - (x->j > y->j);", KNN),
+    ("knn ordered by index only", "  if (x->d2 < y->d2) return -1;\n  if (x->d2 > y->d2) return 1;\n", "", KNN),
+    ("knn radius strict", "      if (d2 <= c->r2) {\n        buf[m].d2 = d2;", "      if (d2 < c->r2) {\n        buf[m].d2 = d2;",
+     KNN),
+    ("knn keeps one too few", "int64_t keep = m < c->max_nn ? m : c->max_nn;",
+     "int64_t keep = m < c->max_nn ? m : c->max_nn - 1;", KNN),
     ("evaluation counts unmatched", "    if (corr[i] >= 0) {\n        sum_d2 += (double)d2[i];\n        ++count;\n      }\n    out_count",
      "    if (corr[i] >= -1) {\n        sum_d2 += (double)d2[i];\n        ++count;\n      }\n    out_count", EVAL),
 ]

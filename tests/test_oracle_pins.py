@@ -449,6 +449,33 @@ def test_knn_matches_numpy_bruteforce(ora):
             assert np.all(idx[i, cnt[i]:] == -1)
 
 
+def test_knn_radius_boundary_and_ties(ora):
+    """Hybrid kNN on an exact binary lattice (spacing 0.25, shuffled, with duplicates at higher indices):
+    the radius is inclusive, equal distances go to the lower index, and the count within radius 0.5 of a
+    lattice point is the closed form: integer triples with i^2 + j^2 + k^2 <= 4 number 1 + 6 + 12 + 8 + 6 = 33."""
+    g = synth.rng(31)
+    ax = np.arange(-4, 5) * 0.25
+    lat = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), -1).reshape(-1, 3)
+    lat = lat[g.permutation(len(lat))]
+    pts = np.vstack([lat, lat[:40]]).astype(np.float32)  # 40 exact copies after all originals
+    q = np.array([[0, 0, 0], [0.125, 0.125, 0.125], [0.25, -0.5, 0.75]], np.float32)
+    for radius, k in [(0.5, 64), (0.5, 7), (0.25, 27), (0.5, 1)]:
+        idx, dd, cnt = ora.knn_hybrid(pts, q, radius, k)
+        for i in range(len(q)):
+            ri, rd = ind.knn_bruteforce_f32(pts, q[i], radius, k)
+            assert cnt[i] == len(ri)
+            assert np.array_equal(idx[i, : cnt[i]], ri) and np.array_equal(dd[i, : cnt[i]], rd)
+        # at the origin: the 33 lattice points within 0.5, plus whichever of them were copied
+        near = np.flatnonzero(np.sum(lat.astype(np.float64) ** 2, 1) <= radius * radius)
+        copies = np.count_nonzero(np.isin(np.arange(40), near))
+        assert cnt[0] == min(k, len(near) + copies)
+        if radius == 0.5:
+            assert len(near) == 33
+        # ties go to the lower index: among equal d2, indices ascend
+        for a in range(cnt[0] - 1):
+            assert dd[0, a] < dd[0, a + 1] or idx[0, a] < idx[0, a + 1]
+
+
 def test_jacobi_matches_numpy_eigh(ora):
     g = synth.rng(27)
     for _ in range(200):
