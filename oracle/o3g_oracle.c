@@ -629,7 +629,7 @@ void ora_jacobi_eig3(const double C[9], double evals[3], double V[9]) {
 
 /* Normal of one neighbourhood: FP64 centred covariance / m, smallest-eigenvalue
  * eigenvector, oriented toward the viewpoint.  Also returns the three
- * eigenvalues in ascending order (used by tests to judge conditioning). */
+ * eigenvalues in ascending order (used by tests to assess conditioning). */
 void ora_normal_from_neighbours(const float* pts, const int32_t* idx, int32_t m, const float q[3],
                                 const double viewpoint[3], float out_n[3], double out_evals[3]) {
   if (m < 3) {
