@@ -416,10 +416,11 @@ def assert_pose_close(T, T_ref, tol=POSE_TOL):
     assert ang <= tol and dt <= tol, (ang, dt)
 
 
-def oracle_step(src, tgt, nrm, T, r):
-    """One Gauss-Newton update of the oracle from pose T (Eq. 2), as a 4x4 FP64 pose."""
+def oracle_step(src, tgt, nrm, T, r, method="brute"):
+    """One Gauss-Newton update of the oracle from pose T (Eq. 2), as a 4x4 FP64 pose.  method "grid" answers the
+    correspondence step through the oracle's exact uniform grid, pinned bit-exact to the brute-force scan."""
     p = oracle.transform(src, T)
-    corr, d2 = oracle.nn(p, tgt, r)
+    corr, d2 = oracle.nn(p, tgt, r, method=method)
     A, b, _, _, cnt = oracle.normal_equations(p, tgt, nrm, corr, d2)
     xi, _ = oracle.ldlt_solve(A, b)
     return oracle.delta_T(xi) @ T, cnt
@@ -436,12 +437,14 @@ def gpu_trajectory(o3g, grid, src, r, K):
 SHADOW_TOL = 1e-7
 
 
-def assert_shadows_oracle(o3g, grid, src_np, tgt, nrm, r, K):
-    """Every GPU iterate T_{k+1} is the oracle's Gauss-Newton step from the GPU's own T_k (within 1e-7)."""
-    traj = gpu_trajectory(o3g, grid, cuda(src_np), r, K)
+def assert_shadows_oracle(o3g, grid, src_np, tgt, nrm, r, K, method="brute", traj=None):
+    """Every GPU iterate T_{k+1} is the oracle's Gauss-Newton step from the GPU's own T_k (within 1e-7).
+    traj: the GPU's T_0 .. T_K when the caller already has them (else run on `grid`)."""
+    if traj is None:
+        traj = gpu_trajectory(o3g, grid, cuda(src_np), r, K)
     worst = 0.0
     for k in range(K):
-        T_next, cnt = oracle_step(src_np, tgt, nrm, traj[k], r)
+        T_next, cnt = oracle_step(src_np, tgt, nrm, traj[k], r, method)
         ang, dt = synth.pose_error(traj[k + 1], T_next)
         worst = max(worst, ang, dt)
         assert ang <= SHADOW_TOL and dt <= SHADOW_TOL, (k, ang, dt)
@@ -474,12 +477,12 @@ def test_icp_sphere_plane_matches_oracle(o3g):
 
 
 def test_icp_room_frame_shadows_oracle(o3g, room):
-    """RGB-D-frame pair at full size (both sides use the oracle's target normals): the first 8 GPU iterates
-    are each the oracle's Gauss-Newton step from the previous GPU iterate."""
+    """RGB-D-frame pair at full size (both sides use the oracle's target normals): every one of the 30 GPU
+    iterates the bench runs is the oracle's Gauss-Newton step from the previous GPU iterate."""
     nrm = oracle.estimate_normals(room.tgt, 0.05, 30)
     grid = o3g.build_grid(cuda(room.tgt), room.max_corr_dist)
     grid.set_normals(cuda(nrm))
-    assert_shadows_oracle(o3g, grid, room.src, room.tgt, nrm, room.max_corr_dist, 8)
+    assert_shadows_oracle(o3g, grid, room.src, room.tgt, nrm, room.max_corr_dist, room.max_iter, method="grid")
     res = o3g.icp_point_to_plane_grid(grid, cuda(room.src), np.eye(4), room.max_corr_dist, room.max_iter)
     assert res["status"] == o3g.OK and res["iters"] == room.max_iter and res["fitness"] > 0.9
     ev = oracle.icp_point_to_plane(room.src, room.tgt, nrm, res["T"], room.max_corr_dist, 0)
@@ -644,6 +647,25 @@ def test_host_entry_with_gpu_normals_matches_oracle_pipeline(o3g, room):
     ang, dt = synth.pose_error(res["T"], ref["T"])
     assert ang < 1e-3 and dt < 1e-3, (ang, dt)
     assert res["fitness"] == pytest.approx(ref["fitness"], abs=1e-3)
+
+
+def test_combined_call_with_gpu_normals_shadows_oracle(o3g, room):
+    """The call the bench times on the RGB-D-frame pair (o3g_register_point_to_plane: grid, GPU normals, ICP):
+    the normals it uses are the separate calls' (bit for bit, tested above), downloaded here; with them, every
+    one of its 30 iterates is the oracle's Gauss-Newton step from the previous iterate, and fitness / rmse are
+    the oracle's evaluation at its final pose."""
+    r = room.max_corr_dist
+    grid = o3g.build_grid(cuda(room.tgt), r * 1.002)
+    nrm = grid.estimate_normals(0.05, 30).cpu().numpy()
+    src, tgt = cuda(room.src), cuda(room.tgt)
+    traj, last = [np.eye(4)], None
+    for k in range(1, room.max_iter + 1):
+        last = o3g.register_point_to_plane(src, tgt, None, np.eye(4), r, k, normal_radius=0.05, normal_max_nn=30)
+        traj.append(last["T"])
+    assert_shadows_oracle(o3g, None, room.src, room.tgt, nrm, r, room.max_iter, method="grid", traj=traj)
+    ev = oracle.icp_point_to_plane(room.src, room.tgt, nrm, last["T"], r, 0, nn_method="grid")
+    assert last["fitness"] == ev["fitness"]
+    assert last["rmse"] == pytest.approx(ev["rmse"], rel=1e-6)
 
 
 def test_launch_forms_give_identical_results(o3g):

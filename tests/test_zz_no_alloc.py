@@ -3,11 +3,14 @@
 o3g_icp_point_to_plane_grid_noalloc is for callers that cannot allocate device
 memory once running (a per-frame tracking loop under a fixed memory budget, a
 host that gives all device memory to its own allocator).  It keeps its working
-memory in one static device array shared by every call, so this test calls it
-twice in a row and checks both results against o3g_icp_point_to_plane_grid on a
-well-conditioned problem run to convergence, within the 1e-6 pose tolerance the
-other ICP parity tests use for such problems.  The file name sorts last so that
-a run stopping at the first failure has already run every other test.
+memory in one static device array shared by every call, so these tests call it
+twice in a row and check both results against o3g_icp_point_to_plane_grid and
+against the CPU oracle on well-conditioned problems run to convergence, within
+the 1e-6 pose tolerance the other ICP parity tests use for such problems; one
+test runs a larger source and then a smaller, different one, so that state left
+in the shared array by the first call would show in the second.  The file name
+sorts last so that a run stopping at the first failure has already run every
+other test.
 """
 from __future__ import annotations
 
@@ -16,6 +19,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_1801_09847_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -23,7 +27,7 @@ pytestmark = pytest.mark.gpu
 POSE_TOL = 1e-6
 
 
-def _corner_scene(g, spacing=0.01):
+def _corner_scene(g=None, spacing=0.01):
     u = np.arange(0.0, 1.0, spacing)
     a, b = np.meshgrid(u, u)
     a, b = a.ravel(), b.ravel()
@@ -87,3 +91,30 @@ def test_noalloc_rejects_sizes_beyond_its_fixed_memory(o3g):
     st, *_ = _call_noalloc(o3g, grid, big, np.eye(4), 0.1, 1, 0.0)
     assert st == o3g.ERR_ARG
     assert "exceed" in o3g.last_error()
+
+
+def _problem(seed, spacing, deg, trans):
+    g = synth.rng(seed)
+    tgt, nrm = _corner_scene(g, spacing)
+    T_gt = synth.perturbation(g, deg, trans)
+    src = (synth.apply_T(synth.inv_T(T_gt), tgt) + g.normal(0, 0.002, tgt.shape)).astype(np.float32)
+    return src, tgt.astype(np.float32), nrm.astype(np.float32)
+
+
+def test_noalloc_larger_then_smaller_source_matches_oracle(o3g):
+    """A 120,000-point source and then a different 30,000-point one through the shared array: each result
+    within 1e-6 rad / m of the oracle (same iteration count, fitness exact, rmse 1e-6 relative)."""
+    import torch
+    oracle.build()
+    for seed, spacing in ((91, 0.005), (92, 0.01)):
+        src, tgt, nrm = _problem(seed, spacing, 2.5, 0.025)
+        grid = o3g.build_grid(torch.from_numpy(tgt).cuda(), 0.05)
+        grid.set_normals(torch.from_numpy(nrm).cuda())
+        st, T, fit, rmse, iters = _call_noalloc(o3g, grid, torch.from_numpy(src).cuda(), np.eye(4), 0.05, 100, 1e-7)
+        ref = oracle.icp_point_to_plane(src, tgt, nrm, np.eye(4), 0.05, 100, eps=1e-7, nn_method="grid")
+        assert ref["iters"] < 100
+        assert st == ref["status"] and iters == ref["iters"], (st, iters, ref["iters"])
+        ang, dt = synth.pose_error(T, ref["T"])
+        assert ang <= POSE_TOL and dt <= POSE_TOL, (spacing, ang, dt)
+        assert fit == ref["fitness"]
+        assert rmse == pytest.approx(ref["rmse"], rel=1e-6)
