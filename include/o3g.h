@@ -231,6 +231,21 @@ O3G_API int32_t o3g_icp_point_to_plane_grid_ex(const o3g_grid* tgt, const float*
                                                double* out_rmse, int32_t* out_iters, void* stream);
 
 /*
+ * o3g_icp_point_to_plane_grid_ex that also returns the correspondence set at
+ * the final pose (the correspondence_set of Open3D's RegistrationResult,
+ * Sec. 3.3): d_corr [ns] int32 = the original target index matched to source
+ * point i (in the caller's order), or -1; d_d2 [ns] float32 = its squared
+ * distance (0 if none).  Both device, caller-owned; null with ns > 0 is
+ * O3G_ERR_ARG.  The set is the one fitness and rmse are computed from, found by
+ * the same warm-started search as the iterations.  Synchronous.
+ */
+O3G_API int32_t o3g_icp_point_to_plane_grid_corr(const o3g_grid* tgt, const float* d_src, int64_t ns, int32_t stride,
+                                                 const double* init_T, double max_corr_dist, int32_t max_iter,
+                                                 double eps, int32_t precision, double* out_T, double* out_fitness,
+                                                 double* out_rmse, int32_t* out_iters, int32_t* d_corr, float* d_d2,
+                                                 void* stream);
+
+/*
  * Point-to-point ICP against a resident target grid (registration_icp with
  * TransformationEstimationPointToPoint, Sec. 3.3; target normals not needed).
  * Each iteration: the correspondence step of o3g_correspondences at the current

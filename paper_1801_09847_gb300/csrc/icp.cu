@@ -3,11 +3,14 @@
 // of the Open3D paper (Sec. 3.3), as the Gauss-Newton iteration of Sec. 4,
 // Eq. (1)-(2).  One kernel launch per iteration, k_icp_iter:
 //   1. transform the (cell-sorted) source point, float32, fixed rounding order;
-//   2. fixed-radius nearest neighbour over the target grid: the home cell first,
-//      then every cell column whose slab can still hold a point at or below the
-//      best squared distance so far, over the z-range that bound allows (exact:
-//      every pruning bound carries a margin for float32 rounding, and ties are
-//      kept, so the result is the minimum of (d2, original index));
+//   2. fixed-radius nearest neighbour over the target grid (exact: every
+//      pruning bound carries a margin for float32 rounding, and ties are kept,
+//      so the result is the minimum of (d2, original index)).  A point's
+//      candidate list from an earlier iteration decides it alone while the list
+//      still covers it (see ListSink); otherwise the search starts from the
+//      last matches of the point and its warp neighbours and scans every cell
+//      column whose slab can still hold a point within the bound, over the
+//      z-range that bound allows, staged block-wide in shared memory;
 //   3. r = (p - q) . n, J = [p x n ; n]; the 21 upper entries of J^T J, J^T r,
 //      r^2, d2 and |C| as exact (value, error) pairs, summed over the tile's
 //      rows in a fixed order into one compensated float32 pair per sum, which
@@ -53,7 +56,10 @@ struct IcpState {
   int degenerate;  // some pivot was frozen
   int few_corr;    // stopped with < 6 correspondences
   int nonfinite;   // the normal equations were not finite
+  int lists_on;    // candidate lists are kept (the updates have become small; see ListSink)
   unsigned arrived;  // tiles of the current launch whose sums are added
+  unsigned pending;  // queries of the current launch left to the fallback pass (see k_icp_fallback)
+  int E[32];         // fixed-point exponent of each sum column (see sum_exponent), written by the tiles
   double A[36];
   double b[6];
   double stats[3];  // sum r^2, sum d2, |C|
@@ -77,17 +83,13 @@ __global__ void k_init_state(IcpState* st, Pose T) {
   st->degenerate = 0;
   st->few_corr = 0;
   st->nonfinite = 0;
+  st->lists_on = 0;
   st->arrived = 0u;
+  st->pending = 0u;
   st->fitness = 0.0;
   st->rmse = 0.0;
 }
 
-// sqrt(x) for x >= 0 from the hardware reciprocal square root (a few ulp): the
-// search bounds add a relative margin far larger than that error.
-__device__ __forceinline__ float fast_sqrt(float x) {
-  const float y = fmaxf(x, 1e-30f);
-  return y * rsqrtf(y);
-}
 
 // Pose j of poses (n x 16 float64) into state j, as k_init_state.
 __global__ void k_init_states(IcpState* st, const double* __restrict__ poses, int n) {
@@ -104,28 +106,14 @@ __global__ void k_init_states(IcpState* st, const double* __restrict__ poses, in
     S.degenerate = 0;
     S.few_corr = 0;
     S.nonfinite = 0;
+    S.lists_on = 0;
     S.arrived = 0u;
+    S.pending = 0u;
     S.fitness = 0.0;
     S.rmse = 0.0;
   }
 }
 
-
-// Scans sorted target positions [beg, end) and keeps the minimum of (d2, original index).
-__device__ __forceinline__ void scan_run(const float4* __restrict__ pts, uint32_t beg, uint32_t end, float px,
-                                         float py, float pz, float& best_d2, int& best_orig, int& best) {
-#pragma unroll 4
-  for (uint32_t k = beg; k < end; ++k) {
-    const float4 q = pts[k];
-    const float d2 = dist2_rn(px, py, pz, q);
-    const int o = __float_as_int(q.w);
-    if (d2 < best_d2 || (d2 == best_d2 && o < best_orig)) {
-      best_d2 = d2;
-      best_orig = o;
-      best = static_cast<int>(k);
-    }
-  }
-}
 
 // Running fixed-radius nearest neighbour of one query: the minimum of
 // (d2, original index) among the candidates seen so far with d2 <= r2.
@@ -135,13 +123,170 @@ struct Nearest {
   int pos;  // sorted target position, -1 if none
 };
 
-__device__ __forceinline__ void consider(Nearest& nb, float4 q, int pos, float px, float py, float pz) {
-  const float d2 = dist2_rn(px, py, pz, q);
-  const int o = __float_as_int(q.w);
-  if (d2 < nb.d2 || (d2 == nb.d2 && o < nb.orig)) {
+__device__ __forceinline__ void consider_d2(Nearest& nb, float d2, int orig, int pos) {
+  if (d2 < nb.d2 || (d2 == nb.d2 && orig < nb.orig)) {
     nb.d2 = d2;
-    nb.orig = o;
+    nb.orig = orig;
     nb.pos = pos;
+  }
+}
+
+__device__ __forceinline__ void consider(Nearest& nb, float4 q, int pos, float px, float py, float pz) {
+  consider_d2(nb, dist2_rn(px, py, pz, q), __float_as_int(q.w), pos);
+}
+
+// Where the exact searches put their candidates.  NnSink keeps the nearest
+// neighbour; its pruning bound is the best d2 so far.
+struct NnSink {
+  Nearest nb;
+  __device__ __forceinline__ float bound() const { return nb.d2; }
+  __device__ __forceinline__ bool seeded() const { return nb.pos >= 0; }
+  __device__ __forceinline__ void offer(float4 q, int pos, float px, float py, float pz) {
+    consider(nb, q, pos, px, py, pz);
+  }
+};
+
+// Candidate lists.  While ICP iterates, each source point keeps a list of the
+// targets near the place p_b where the list was built: every target within
+// d1 + sigma of p_b (d1: the distance to its nearest target within r, or r
+// when there is none; sigma = kSkin r), at most kList of them (the nearest),
+// with a bound rho2 such that every target at dist2_rn(p_b, q) < rho2 is
+// listed (a Verlet neighbour list with skin sigma, as molecular dynamics keeps
+// them).  At a later position p with d = |p - p_b|: a target at d2 <= D from p
+// lies within sqrt(D) + d of p_b, so when (sqrt(D) + d)^2, with margins for the
+// float32 rounding of the three distances, is below rho2, every candidate of
+// the exact search is listed and the list alone decides the correspondence
+// (D = the best listed d2 within r2, or r2 when none is, which proves that no
+// target is within r).  A list stays valid while its point moves less than
+// about sigma; a point whose list no longer covers it searches the grid and
+// rebuilds its list.
+constexpr int kList = 8;
+constexpr float kSkin = 0.1f;
+
+// The bound a list rebuilt at p takes its candidates within: (sqrt(D) + sigma)^2,
+// rounded up, for the best d2 D known when the rebuild starts (the nearest
+// listed target of the old list within r2, else r2).
+__device__ __forceinline__ float list_lim(float D, float sigma) {
+  const float s = __fadd_rn(fast_sqrt(__fmul_rn(D, 1.0001f)), sigma);
+  return __fmul_rn(__fmul_rn(s, s), 1.0001f);
+}
+
+// A list being rebuilt at p, with the nearest neighbour within r2 beside it:
+// the kList nearest candidates by (d2, position) among those at d2 <= lim.
+// While fewer are held every candidate within lim is taken; once kList are
+// held, a nearer one replaces the farthest (and the pruning bound becomes the
+// farthest held d2).  Every target left out is then at d2 >= the farthest held
+// d2, so every target at d2 < rho2() is held.  The list depends only on the
+// targets, p and lim, not on the order the search offers candidates in.
+// Entries sit in shared-memory columns (entry k of thread t at [k][t]).
+struct ListSink {
+  Nearest nb;
+  float (*d)[kThreads];
+  int (*p)[kThreads];
+  float lim;
+  int m;       // entries held
+  float maxv;  // m == kList: the farthest held (d2, position) is (maxv, p[maxk])
+  int maxk;
+  __device__ __forceinline__ float bound() const { return m < kList ? lim : maxv; }
+  __device__ __forceinline__ bool seeded() const { return nb.pos >= 0; }
+  __device__ __forceinline__ void rescan() {
+    const int t = threadIdx.x;
+    maxv = d[0][t];
+    maxk = 0;
+#pragma unroll
+    for (int k = 1; k < kList; ++k)
+      if (d[k][t] > maxv || (d[k][t] == maxv && p[k][t] > p[maxk][t])) {
+        maxv = d[k][t];
+        maxk = k;
+      }
+  }
+  __device__ __forceinline__ void offer(float4 q, int pos, float px, float py, float pz) {
+    const float v = dist2_rn(px, py, pz, q);
+    consider_d2(nb, v, __float_as_int(q.w), pos);
+    if (!(v <= lim)) return;
+    const int t = threadIdx.x;
+    if (m < kList) {
+      d[m][t] = v;
+      p[m][t] = pos;
+      if (++m == kList) rescan();
+    } else if (v < maxv || (v == maxv && pos < p[maxk][t])) {
+      d[maxk][t] = v;
+      p[maxk][t] = pos;
+      rescan();
+    }
+  }
+  // every target at d2 < rho2 from the build position is held
+  __device__ __forceinline__ float rho2() const { return m < kList ? lim : maxv; }
+};
+
+// The state of one source point's list: (p_b, rho2) and kList sorted target
+// positions (-1: empty).  rho2 NaN (the initial all-ones bytes): no list.
+struct ListRef {
+  float4* pb;  // per source point
+  int4* idx;   // 2 per source point
+  int* hint;   // per source point: sorted target position of its last match, or -1
+};
+constexpr size_t kListBytes = 64;  // per source point (a multiple of 16: buffers of many pairs stay aligned)
+
+// Candidate lists pay where an iteration launch is bound by throughput rather
+// than by the latency of one wave of tiles: a pair keeps them when it has at
+// least kListMinPoints source points, once an update moves its points by less
+// than a quarter of the skin.
+constexpr int64_t kListMinPoints = 1 << 17;
+inline float list_motion(int64_t ns, float r) { return ns >= kListMinPoints ? 0.25f * kSkin * r : -1.f; }
+
+// The lists of n source points in one buffer of kListBytes * n bytes (all
+// bytes 0xff at the start: no lists, no matches).
+inline ListRef list_ref(void* base, int64_t n) {
+  float4* pb = static_cast<float4*>(base);
+  int4* idx = reinterpret_cast<int4*>(pb + n);
+  return ListRef{pb, idx, reinterpret_cast<int*>(idx + 2 * n)};
+}
+
+// Scans a query's list at its position p: the nearest listed target within r2
+// goes into nb (a first bound for a rebuild), and the result says whether the
+// list covers the query (see above).
+__device__ __forceinline__ bool list_scan(const GridView& g, float4 pb, int4 l0, int4 l1, float px, float py,
+                                          float pz, Nearest& nb) {
+  const int e[kList] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+  float4 q[kList];
+#pragma unroll
+  for (int k = 0; k < kList; ++k) q[k] = e[k] >= 0 ? g.pts[e[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < kList; ++k)
+    if (e[k] >= 0) consider(nb, q[k], e[k], px, py, pz);
+  const float moved = dist2_rn(px, py, pz, pb);  // NaN without a list
+  const float s = __fadd_rn(fast_sqrt(__fmul_rn(nb.d2, 1.0001f)), fast_sqrt(__fmul_rn(moved, 1.0001f)));
+  return __fadd_rn(__fmul_rn(__fmul_rn(s, s), 1.0001f), 1e-30f) < pb.w;
+}
+
+// Stores a rebuilt list of thread threadIdx.x for source point i.
+__device__ __forceinline__ void list_store(const ListRef& L, int i, const ListSink& ls, float px, float py,
+                                           float pz) {
+  int e[kList];
+#pragma unroll
+  for (int k = 0; k < kList; ++k) e[k] = k < ls.m ? ls.p[k][threadIdx.x] : -1;
+  L.pb[i] = make_float4(px, py, pz, ls.rho2());
+  L.idx[2 * i] = make_int4(e[0], e[1], e[2], e[3]);
+  L.idx[2 * i + 1] = make_int4(e[4], e[5], e[6], e[7]);
+}
+
+// Offers the sorted target positions [beg, end) to a sink, loading them
+// kRunGroup at a time (the loads of a group are independent, so they overlap;
+// offering one candidate at a time would expose a full memory latency per
+// candidate).
+constexpr int kRunGroup = 4;
+
+template <class Sink>
+__device__ __forceinline__ void offer_run(const GridView& g, uint32_t beg, uint32_t end, float px, float py, float pz,
+                                          Sink& sk) {
+  for (uint32_t j = beg; j < end; j += kRunGroup) {
+    float4 q[kRunGroup];
+#pragma unroll
+    for (int k = 0; k < kRunGroup; ++k) q[k] = j + k < end ? g.pts[j + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < kRunGroup; ++k)
+      if (j + k < end) sk.offer(q[k], static_cast<int>(j + k), px, py, pz);
   }
 }
 
@@ -161,27 +306,27 @@ __device__ __forceinline__ void first_bound(const GridView& g, float px, float p
     if (h[k] >= 0) consider(nb, q[k], h[k], px, py, pz);
 }
 
-
-// The rest of the exact search from global memory, given the first bound: the
-// home cell first when there is no bound yet, then every cell that can still
-// hold d2 <= best (box sized from the bound; each column over the z-range the
-// bound allows, clipped to the column's occupied cells).  Every bound carries a
-// margin for float32 rounding and ties are kept, so the result is exactly the
-// brute-force minimum.
-__device__ void box_search_global(const GridView& g, float cell, float px, float py, float pz, float r,
-                                  Nearest& nb) {
-  const float margin = search_margin(cell, r, px, py, pz);
+// The exact search from global memory: the home cell first when the sink has no
+// bound yet, then every cell that can still hold a candidate within the sink's
+// bound (box sized from the bound; each column over the z-range the bound
+// allows, clipped to the column's occupied cells).  Every bound carries a
+// margin for float32 rounding and ties are kept, so the nearest neighbour is
+// exactly the brute-force minimum and a list holds exactly the nearest.
+// R: the largest radius the sink asks for (its margins are sized by it).
+template <class Sink>
+__device__ void box_search_global(const GridView& g, float cell, float px, float py, float pz, float R, Sink& sk) {
+  const float margin = search_margin(cell, R, px, py, pz);
   const int hx = cell_coord(px, g.inv_cell) - g.lo_x;
   const int hy = cell_coord(py, g.inv_cell) - g.lo_y;
   const int hz = cell_coord(pz, g.inv_cell) - g.lo_z;
   const bool home_in = hx >= 0 && hx < g.sx && hy >= 0 && hy < g.sy && hz >= 0 && hz < g.sz;
   bool home_done = false;
-  if (nb.pos < 0 && home_in) {
+  if (!sk.seeded() && home_in) {
     const int c = (hx * g.sy + hy) * g.sz + hz;
-    scan_run(g.pts, g.cell_start[c], g.cell_start[c + 1], px, py, pz, nb.d2, nb.orig, nb.pos);
+    offer_run(g, g.cell_start[c], g.cell_start[c + 1], px, py, pz, sk);
     home_done = true;
   }
-  const float reach = __fadd_rn(fast_sqrt(__fmul_rn(nb.d2, 1.0001f)), margin);
+  const float reach = __fadd_rn(fast_sqrt(__fmul_rn(sk.bound(), 1.0001f)), margin);
   int ax, bx, ay, by, az, bz;
   axis_range(px, reach, g.inv_cell, g.lo_x, g.sx, ax, bx);
   axis_range(py, reach, g.inv_cell, g.lo_y, g.sy, ay, by);
@@ -191,19 +336,19 @@ __device__ void box_search_global(const GridView& g, float cell, float px, float
     const float gx = slab_gap(px, x + g.lo_x, cell, margin);
     for (int y = ay; y <= by; ++y) {
       const float gy = slab_gap(py, y + g.lo_y, cell, margin);
-      const float lim = __fmul_rn(nb.d2, 1.0001f) - (gx * gx + gy * gy);
+      const float lim = __fmul_rn(sk.bound(), 1.0001f) - (gx * gx + gy * gy);
       if (lim < 0.f) continue;
       const float rz = __fadd_rn(fast_sqrt(lim), margin);
       int zl = max(az, cell_coord(__fsub_rn(pz, rz), g.inv_cell) - g.lo_z);
       int zh = min(bz, cell_coord(__fadd_rn(pz, rz), g.inv_cell) - g.lo_z);
       if (zl > zh || !column_z(g, x * g.sy + y, zl, zh)) continue;
       const int col = (x * g.sy + y) * g.sz;
+      const uint32_t b0 = g.cell_start[col + zl], e1 = g.cell_start[col + zh + 1];
       if (home_done && x == hx && y == hy && zl <= hz && hz <= zh) {
-        scan_run(g.pts, g.cell_start[col + zl], g.cell_start[col + hz], px, py, pz, nb.d2, nb.orig, nb.pos);
-        scan_run(g.pts, g.cell_start[col + hz + 1], g.cell_start[col + zh + 1], px, py, pz, nb.d2, nb.orig,
-                 nb.pos);
+        offer_run(g, b0, g.cell_start[col + hz], px, py, pz, sk);
+        offer_run(g, g.cell_start[col + hz + 1], e1, px, py, pz, sk);
       } else {
-        scan_run(g.pts, g.cell_start[col + zl], g.cell_start[col + zh + 1], px, py, pz, nb.d2, nb.orig, nb.pos);
+        offer_run(g, b0, e1, px, py, pz, sk);
       }
     }
   }
@@ -221,6 +366,9 @@ __device__ void box_search_global(const GridView& g, float cell, float px, float
 // nothing changed, when the staged set does not fit: the caller then searches
 // from global memory.  All threads of the block must call this.
 constexpr int kStageZ = 15;  // z-cells per column
+// A tile stages its search when more than this many of its queries are left
+// after the neighbour records.
+constexpr int kStagedMin = 0;
 
 // Two stage sizes, one per launch configuration.  Latency: every tile of a
 // launch is resident at once (5 blocks per SM), so a large stage keeps blocks
@@ -232,6 +380,10 @@ struct CfgLatency {
 struct CfgThroughput {
   static constexpr int kPts = 1024, kCols = 64, kMinBlocks = 7;
 };
+
+// The lists being rebuilt in a tile (see ListSink) take the last kListPts
+// points of the stage, which then holds kListPts fewer candidates.
+constexpr int kListPts = kList * kThreads * 2 * 4 / 16;
 
 template <class Cfg>
 struct Stage {
@@ -264,12 +416,53 @@ __device__ __forceinline__ void column_range(const GridView& g, float cell, floa
   zh = min(bz, cell_coord(__fadd_rn(pz, rz), g.inv_cell) - g.lo_z);
 }
 
-template <class St>
+// The exact search of one query from global memory with its memory accesses
+// batched: the columns of the box its bound allows are taken kBatchCols at a
+// time, each column's z-range from its slab gaps, the run bounds of the whole
+// batch are loaded together (independent loads), then the runs are scanned.
+// Every planned run is scanned, so the result is exact; a batch is planned with
+// the bound of the moment, which the scan can only tighten.  For queries
+// searched one per thread (the fallback pass), where a chain of dependent
+// per-column loads would set the time.
+constexpr int kBatchCols = 8;
+
+template <class Sink>
+__device__ void box_search_batched(const GridView& g, float cell, float px, float py, float pz, float R, Sink& sk) {
+  const float margin = search_margin(cell, R, px, py, pz);
+  const float reach = __fadd_rn(fast_sqrt(__fmul_rn(sk.bound(), 1.0001f)), margin);
+  int ax, bx, ay, by, az, bz;
+  axis_range(px, reach, g.inv_cell, g.lo_x, g.sx, ax, bx);
+  axis_range(py, reach, g.inv_cell, g.lo_y, g.sy, ay, by);
+  axis_range(pz, reach, g.inv_cell, g.lo_z, g.sz, az, bz);
+  if (ax > bx || ay > by || az > bz) return;
+  const int ny = by - ay + 1, ncol = (bx - ax + 1) * ny;
+  for (int c0 = 0; c0 < ncol; c0 += kBatchCols) {
+    const float bound = sk.bound();
+    uint32_t beg[kBatchCols], end[kBatchCols];
+#pragma unroll
+    for (int k = 0; k < kBatchCols; ++k) {
+      beg[k] = end[k] = 0u;
+      const int c = c0 + k;
+      if (c >= ncol) continue;
+      const int x = ax + c / ny, y = ay + c % ny;
+      int zl, zh;
+      column_range(g, cell, px, py, pz, margin, bound, x, y, az, bz, zl, zh);
+      if (zl > zh) continue;
+      const int col = (x * g.sy + y) * g.sz;
+      beg[k] = g.cell_start[col + zl];
+      end[k] = g.cell_start[col + zh + 1];
+    }
+#pragma unroll
+    for (int k = 0; k < kBatchCols; ++k) offer_run(g, beg[k], end[k], px, py, pz, sk);
+  }
+}
+
+template <class St, class Sink>
 __device__ bool staged_search(const GridView& g, float cell, float px, float py, float pz, float r, bool live,
-                              Nearest& nb, St& S) {
-  constexpr int kStageCols = St::kStageCols, kStagePts = St::kStagePts;
+                              Sink& sk, St& S, int cap = St::kStagePts) {
+  constexpr int kStageCols = St::kStageCols;
   const float margin = search_margin(cell, r, px, py, pz);
-  const float reach = __fadd_rn(fast_sqrt(__fmul_rn(nb.d2, 1.0001f)), margin);
+  const float reach = __fadd_rn(fast_sqrt(__fmul_rn(sk.bound(), 1.0001f)), margin);
   int ax = 0, bx = -1, ay = 0, by = -1, az = 0, bz = -1;
   if (live) {
     axis_range(px, reach, g.inv_cell, g.lo_x, g.sx, ax, bx);
@@ -311,7 +504,7 @@ __device__ bool staged_search(const GridView& g, float cell, float px, float py,
     for (int x = ax; x <= bx; ++x)
       for (int y = ay; y <= by; ++y) {
         int zl, zh;
-        column_range(g, cell, px, py, pz, margin, nb.d2, x, y, az, bz, zl, zh);
+        column_range(g, cell, px, py, pz, margin, sk.bound(), x, y, az, bz, zl, zh);
         if (zl > zh) continue;
         const int t = (x - AX) * NCY + (y - AY);
         atomicMin(&S.zlo[t], zl - AZ);
@@ -354,7 +547,7 @@ __device__ bool staged_search(const GridView& g, float cell, float px, float py,
   }
   __syncthreads();
   const int M = S.total;
-  if (M > kStagePts) return false;
+  if (M > cap) return false;
   {  // copy: one warp per column, lanes over its points
     const int lane = threadIdx.x & 31;
     for (int t = threadIdx.x >> 5; t < ncol; t += blockDim.x >> 5) {
@@ -370,7 +563,7 @@ __device__ bool staged_search(const GridView& g, float cell, float px, float py,
   for (int x = ax; x <= bx; ++x) {
     for (int y = ay; y <= by; ++y) {
       int zl, zh;
-      column_range(g, cell, px, py, pz, margin, nb.d2, x, y, az, bz, zl, zh);
+      column_range(g, cell, px, py, pz, margin, sk.bound(), x, y, az, bz, zl, zh);
       const int t = (x - AX) * NCY + (y - AY);
       // Clamp to the planned range: only its offsets were loaded.  The bound
       // has only shrunk since planning, but x * rsqrt(x) is not monotone to
@@ -382,7 +575,7 @@ __device__ bool staged_search(const GridView& g, float cell, float px, float py,
       if (zl > zh) continue;
       const int shift = static_cast<int>(S.base[t]) - static_cast<int>(S.off[t][S.zlo[t]]);
       const uint32_t gb = S.off[t][zl - AZ], ge = S.off[t][zh + 1 - AZ];
-      for (uint32_t k = gb; k < ge; ++k) consider(nb, S.pts[static_cast<int>(k) + shift], static_cast<int>(k), px, py, pz);
+      for (uint32_t k = gb; k < ge; ++k) sk.offer(S.pts[static_cast<int>(k) + shift], static_cast<int>(k), px, py, pz);
     }
   }
   return true;
@@ -574,7 +767,8 @@ __device__ __forceinline__ double sym6(const double* sums, int i, int j) {
 // Rz(gamma) Ry(beta) Rx(alpha) one entry per lane, and T <- [dR, t] T on lanes
 // 4 r + c (Tpre: pose entry `lane` for lanes 0..11, and iters0 the iteration
 // count, both fetched by the caller).
-__device__ void solve_update(const double* sums, double Tpre, int iters0, IcpState* __restrict__ st, double eps) {
+__device__ void solve_update(const double* sums, double Tpre, int iters0, IcpState* __restrict__ st, double eps,
+                             float a, float mlim) {
   const int lane = threadIdx.x & 31;
   // this lane's entry; lanes 28..31 hold a copy of entry (0, 0) that nothing reads
   const int tl = lane < 28 ? lane : 0;
@@ -651,6 +845,19 @@ __device__ void solve_update(const double* sums, double Tpre, int iters0, IcpSta
     st->T[lane] = tn;
     if (c < 3) st->R[3 * r + c] = __double2float_rn(tn);
     else st->t[r] = __double2float_rn(tn);
+  }
+  // candidate lists pay once the updates are small: the update moves every
+  // point p by at most |(alpha, beta, gamma)| |p| + |t| (to first order), with
+  // |p| <= a; below mlim the pair keeps lists from the next launch on (float32:
+  // only the speed depends on this)
+  {
+    const float xf = static_cast<float>(xv);
+    const float q = xf * xf;
+    const float w2 = (__shfl_sync(0xffffffffu, q, 21) + __shfl_sync(0xffffffffu, q, 22)) +
+                     __shfl_sync(0xffffffffu, q, 23);
+    const float t2 = (__shfl_sync(0xffffffffu, q, 24) + __shfl_sync(0xffffffffu, q, 25)) +
+                     __shfl_sync(0xffffffffu, q, 26);
+    if (lane == 0 && sqrtf(w2) * a + sqrtf(t2) < mlim) st->lists_on = 1;
   }
   // converged when |(alpha, beta, gamma)|^2 < eps^2 and |t|^2 < eps^2 (eps > 0)
   bool done = false;
@@ -937,8 +1144,9 @@ struct PairDesc {
   unsigned long long* acc;  // nacc x kPartial fixed-point sums (see add_fixed), zero between launches
   int nacc;                 // accumulator rows: min(kAccRows, ntiles)
   float bnd_a, bnd_b;       // per-correspondence bounds the sums are scaled by (see set_sums)
-  int32_t* hints;      // per source point: sorted target position of its last match, or -1; may be null
-  int32_t* corr_out;   // kCorrOnly outputs (by original source index)
+  ListRef lists;       // per source point last matches and candidate lists (see ListSink); pb null: none kept
+  float list_motion;   // the pair keeps candidate lists once an update moves points by less (< 0: never)
+  int32_t* corr_out;   // kCorrOnly / kEvaluate outputs (by original source index), or null
   float* d2_out;
 };
 
@@ -1043,7 +1251,6 @@ __device__ void finish(const PairDesc& P, int mode, float nlen) {
     if (row < P.nacc) P.acc[static_cast<size_t>(row) * kPartial + col] = 0ull;
   }
   sub[q][col] = static_cast<long long>(t);
-  if (threadIdx.x == 0) st->arrived = 0u;  // ready for the next launch
   __syncthreads();
   if (threadIdx.x < kPartial) {
     const long long tot = sub[0][col] + sub[1][col] + sub[2][col] + sub[3][col];
@@ -1080,7 +1287,7 @@ __device__ void finish(const PairDesc& P, int mode, float nlen) {
   }
   if (P.kind == kPointToPoint)
     solve_update_p2p(sums, Tpre, iters0, st, P.eps, P.eps_tan2, P.ctr[0], P.ctr[1], P.ctr[2]);
-  else solve_update(sums, Tpre, iters0, st, P.eps);
+  else solve_update(sums, Tpre, iters0, st, P.eps, P.bnd_a, P.list_motion);
 }
 
 
@@ -1108,140 +1315,252 @@ __device__ __forceinline__ void p2p_terms(const PairDesc& P, float3 p, float4 q,
   v[29] = 1.0;
 }
 
-// One tile (kThreads cell-sorted source points, tile j of pair P) of one ICP step.
-// mode kIterate: skipped once the pair is done; the other modes always run.
-// kCorrOnly writes corr/d2 and no sums.  The last tile of the pair to finish
-// performs the pair's solve and update (see finish).  Block-uniform control flow.
+// The all-float64 terms of one correspondence (p, target bp at d2 = bd2) in the
+// sum columns: point-to-plane every term from the float32 p, q, n, each product
+// and sum rounded once in the oracle's order (no fused multiply-add);
+// point-to-point the moments of p2p_terms.  Zero when bp < 0.
+__device__ __forceinline__ void f64_terms(const PairDesc& P, float3 p, int bp, float bd2, double (&v)[32]) {
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = 0.0;
+  if (bp >= 0 && P.kind == kPointToPoint) {
+    p2p_terms(P, p, P.g.pts[bp], bd2, v);
+  } else if (bp >= 0) {
+    const float4 q = P.g.pts[bp];
+    const float4 n = P.g.nrm[bp];
+    const double px = p.x, py = p.y, pz = p.z, nx = n.x, ny = n.y, nz = n.z;
+    const double dx = __dsub_rn(px, static_cast<double>(q.x));
+    const double dy = __dsub_rn(py, static_cast<double>(q.y));
+    const double dz = __dsub_rn(pz, static_cast<double>(q.z));
+    const double res = __dadd_rn(__dadd_rn(__dmul_rn(dx, nx), __dmul_rn(dy, ny)), __dmul_rn(dz, nz));
+    double J[6];
+    J[0] = __dsub_rn(__dmul_rn(py, nz), __dmul_rn(pz, ny));
+    J[1] = __dsub_rn(__dmul_rn(pz, nx), __dmul_rn(px, nz));
+    J[2] = __dsub_rn(__dmul_rn(px, ny), __dmul_rn(py, nx));
+    J[3] = nx;
+    J[4] = ny;
+    J[5] = nz;
+    int k = 0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int b = a; b < 6; ++b) v[k++] = __dmul_rn(J[a], J[b]);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) v[21 + a] = __dmul_rn(J[a], res);
+    v[27] = __dmul_rn(res, res);
+    v[28] = static_cast<double>(bd2);
+    v[29] = 1.0;
+  }
+}
+
+// The float32 factors of one correspondence in a row of kRow slots (see kTerm):
+// point-to-plane J0..J5, r, d2, 1; point-to-point a = p - c and b = q - c as
+// exact (high, low) pairs, |a|^2, |b|^2, d2, 1.  Slot kOne holds 1, every other
+// slot 0 when bp < 0.
+template <class Row>
+__device__ __forceinline__ void row_factors(const PairDesc& P, float3 p, int bp, float bd2, Row&& row) {
+#pragma unroll
+  for (int k = 0; k < kRow; ++k) row(k) = 0.f;
+  row(kOne) = 1.f;
+  if (bp < 0) return;
+  const float4 q = P.g.pts[bp];
+  if (P.kind == kPointToPoint) {
+    // a = p - c and b = q - c as exact pairs (c = P.ctr, near the clouds)
+    const float pv[3] = {p.x, p.y, p.z}, qv[3] = {q.x, q.y, q.z};
+    float aa = 0.f, bb = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float ah, al, bh, bl;
+      two_sum(pv[k], -P.ctr[k], ah, al);
+      two_sum(qv[k], -P.ctr[k], bh, bl);
+      row(k) = ah;
+      row(3 + k) = al;
+      row(6 + k) = bh;
+      row(9 + k) = bl;
+      aa += ah * ah;
+      bb += bh * bh;
+    }
+    row(12) = aa;
+    row(13) = bb;
+    row(14) = bd2;
+    row(15) = 1.f;
+  } else {
+    const float4 n = P.g.nrm[bp];
+    const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+    row(0) = p.y * n.z - p.z * n.y;
+    row(1) = p.z * n.x - p.x * n.z;
+    row(2) = p.x * n.y - p.y * n.x;
+    row(3) = n.x;
+    row(4) = n.y;
+    row(5) = n.z;
+    row(6) = dx * n.x + dy * n.y + dz * n.z;
+    row(7) = bd2;
+    row(8) = 1.f;
+  }
+}
+
+// The queries an iteration launch leaves to the fallback pass (k_icp_fallback):
+// entry = (pair, source position, best d2 so far as bits, its sorted target
+// position or -1).  count[k & 1] / claim[k & 1] are the appended and claimed
+// entries of launch k of a sequence; launch k + 1 zeroes those of parity k & 1
+// (launch k's pass has ended by then).  items == null: no fallback pass, every
+// query is finished inside its tile.
+struct FallbackQueue {
+  int4* items = nullptr;
+  unsigned* count = nullptr;  // [2]
+  unsigned* claim = nullptr;  // [2]
+  int parity = 0;
+};
+
+// One tile (kThreads cell-sorted source points, tile j of pair P, which is
+// pair `pair` of the launch) of one ICP step.  mode kIterate: skipped once the
+// pair is done; the other modes always run.  kCorrOnly writes corr/d2 and no
+// sums.  Warm queries finish in the neighbour record of their best first
+// candidate; a tile with many queries left searches them block-staged, one with
+// few hands them to the fallback pass (or, without one, searches each from
+// global memory).  The tile's partial holds the rows of the queries it
+// finished; the last tile of the pair to arrive performs the pair's solve and
+// update (see finish) unless the fallback pass still has queries of the pair,
+// in which case the pass does.  Block-uniform control flow.
 template <bool F64, class St>
-__device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
+__device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage, int pair, const FallbackQueue& fq) {
   // every load the tile starts with (the stop flag, the pose, the source point
   // and its hint) is issued before any of them is used: one memory round trip
   const int done = P.st->done;
+  const int lists_on = P.st->lists_on;
   float R[9], t[3];
 #pragma unroll
   for (int k = 0; k < 9; ++k) R[k] = P.st->R[k];
 #pragma unroll
   for (int k = 0; k < 3; ++k) t[k] = P.st->t[k];
   const int i = j * kThreads + threadIdx.x;
-  // every lane runs the search (lanes past the end on a far-away dummy point) so
-  // that the warp-wide exchange of first candidates is convergent
   const bool live = i < P.ns;
+  const bool keep = P.lists.pb != nullptr;  // matches (and lists) are kept across launches
   const float4 s = live ? P.src4[i] : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
-  const int hint = (P.hints && live) ? P.hints[i] : -1;
+  const int hint = (keep && live) ? P.lists.hint[i] : -1;
+  float4 pb = make_float4(0.f, 0.f, 0.f, -1.f);
+  int4 l0 = make_int4(-1, -1, -1, -1), l1 = l0;
+  if (keep && live && lists_on) {
+    pb = P.lists.pb[i];
+    l0 = P.lists.idx[2 * i];
+    l1 = P.lists.idx[2 * i + 1];
+  }
   if (mode == kIterate && done) return;
+  const bool lists = keep && lists_on && P.kind == kPointToPlane;
   const float r2 = __fmul_rn(P.r, P.r);
+  const float sigma = __fmul_rn(P.r, kSkin), Rl = __fadd_rn(P.r, sigma);
   const float3 p = live ? xform_rn(R, t, s.x, s.y, s.z) : make_float3(3.0e38f, 3.0e38f, 3.0e38f);
+  // Once the pair keeps lists, a point whose list still covers it is decided by
+  // the list alone; the others search the grid from their last match (and
+  // rebuild their lists).  Before that, every point searches from the last
+  // matches of itself and its warp neighbours.  Searches run block-staged while
+  // many of the tile's points need one, else in the fallback pass (or, without
+  // one, each from global memory).
   Nearest nb{r2, 0x7fffffff, -1};
-  first_bound(P.g, p.x, p.y, p.z, hint, nb);
-  if (!staged_search(P.g, P.cell, p.x, p.y, p.z, P.r, live, nb, stage) && live)
-    box_search_global(P.g, P.cell, p.x, p.y, p.z, P.r, nb);
-  const float bd2 = nb.d2;
-  const int bp = live ? nb.pos : -1;
-  if (live) {
-    if (P.hints) P.hints[i] = bp;
-    if (mode == kCorrOnly) {
-      const int o = __float_as_int(s.w);
-      P.corr_out[o] = bp >= 0 ? __float_as_int(P.g.pts[bp].w) : -1;
-      P.d2_out[o] = bp >= 0 ? bd2 : 0.f;
+  bool need = live;
+  if (lists) {
+    need = live && !list_scan(P.g, pb, l0, l1, p.x, p.y, p.z, nb);
+    if (need && hint >= 0) consider(nb, P.g.pts[hint], hint, p.x, p.y, p.z);
+  } else {
+    first_bound(P.g, p.x, p.y, p.z, hint, nb);
+  }
+  // the lists being rebuilt (see ListSink) in the stage's last kListPts points
+  float(*const s_ld)[kThreads] = reinterpret_cast<float(*)[kThreads]>(&stage.pts[St::kStagePts - kListPts]);
+  int(*const s_lp)[kThreads] = reinterpret_cast<int(*)[kThreads]>(&s_ld[kList][0]);
+  const int n_need = __syncthreads_count(need);
+  bool queued = false;
+  if (n_need > kStagedMin) {
+    if (lists) {
+      ListSink ls{nb, s_ld, s_lp, list_lim(nb.d2, sigma), 0, 0.f, 0};
+      if (!staged_search(P.g, P.cell, p.x, p.y, p.z, Rl, need, ls, stage, St::kStagePts - kListPts) && need)
+        box_search_global(P.g, P.cell, p.x, p.y, p.z, Rl, ls);
+      if (need) list_store(P.lists, i, ls, p.x, p.y, p.z);
+      nb = ls.nb;
+    } else {
+      NnSink ns{nb};
+      if (!staged_search(P.g, P.cell, p.x, p.y, p.z, P.r, need, ns, stage) && need)
+        box_search_global(P.g, P.cell, p.x, p.y, p.z, P.r, ns);
+      nb = ns.nb;
+    }
+  } else if (n_need > 0 && fq.items) {
+    // append this tile's remaining points (in lane order) to the fallback queue
+    __shared__ unsigned s_wcnt[kThreads / 32], s_qbase;
+    const unsigned bal = __ballot_sync(0xffffffffu, need);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_wcnt[warp] = __popc(bal);
+    if (threadIdx.x == 0) s_qbase = atomicAdd(&fq.count[fq.parity], static_cast<unsigned>(n_need));
+    __syncthreads();
+    if (need) {
+      unsigned off = s_qbase + __popc(bal & ((1u << lane) - 1u));
+      for (int w = 0; w < warp; ++w) off += s_wcnt[w];
+      fq.items[off] = make_int4(pair, i, 0, 0);
+    }
+    queued = need;
+  } else if (need) {
+    if (lists) {
+      ListSink ls{nb, s_ld, s_lp, list_lim(nb.d2, sigma), 0, 0.f, 0};
+      box_search_global(P.g, P.cell, p.x, p.y, p.z, Rl, ls);
+      list_store(P.lists, i, ls, p.x, p.y, p.z);
+      nb = ls.nb;
+    } else {
+      NnSink ns{nb};
+      box_search_global(P.g, P.cell, p.x, p.y, p.z, P.r, ns);
+      nb = ns.nb;
     }
   }
+  const float bd2 = nb.d2;
+  const int bp = (live && !queued) ? nb.pos : -1;
+  if (keep && live && !queued) P.lists.hint[i] = bp;
+  if (live && !queued && P.corr_out) {  // kCorrOnly, or a final evaluation that reports its correspondence set
+    const int o = __float_as_int(s.w);
+    P.corr_out[o] = bp >= 0 ? __float_as_int(P.g.pts[bp].w) : -1;
+    P.d2_out[o] = bp >= 0 ? bd2 : 0.f;
+  }
   if (mode == kCorrOnly) return;
+  const int n_queued = fq.items && n_need <= kStagedMin ? n_need : 0;
   // this tile's partial of every sum goes to accumulator row j % nacc, scaled by
   // the bounds (nlen: the target normals' length bound)
   unsigned long long* const acc = P.acc + static_cast<size_t>(j % P.nacc) * kPartial;
   const float nlen = (P.kind == kPointToPlane && P.g.nrm) ? P.g.nrm[P.g.n].x : 0.f;
+  int E = 0;
+  if (threadIdx.x < kPartial) {
+    E = sum_exponent(P, threadIdx.x, nlen);
+    if (n_queued) P.st->E[threadIdx.x] = E;  // for the fallback pass (every tile writes the same values)
+  }
   if constexpr (F64) {
-    // every term in float64 from the float32 p, q, n, each product and sum
-    // rounded once in the oracle's order (no fused multiply-add)
     double v[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = 0.0;
-    if (bp >= 0 && P.kind == kPointToPoint) {
-      p2p_terms(P, p, P.g.pts[bp], bd2, v);
-    } else if (bp >= 0) {
-      const float4 q = P.g.pts[bp];
-      const float4 n = P.g.nrm[bp];
-      const double px = p.x, py = p.y, pz = p.z, nx = n.x, ny = n.y, nz = n.z;
-      const double dx = __dsub_rn(px, static_cast<double>(q.x));
-      const double dy = __dsub_rn(py, static_cast<double>(q.y));
-      const double dz = __dsub_rn(pz, static_cast<double>(q.z));
-      const double res = __dadd_rn(__dadd_rn(__dmul_rn(dx, nx), __dmul_rn(dy, ny)), __dmul_rn(dz, nz));
-      double J[6];
-      J[0] = __dsub_rn(__dmul_rn(py, nz), __dmul_rn(pz, ny));
-      J[1] = __dsub_rn(__dmul_rn(pz, nx), __dmul_rn(px, nz));
-      J[2] = __dsub_rn(__dmul_rn(px, ny), __dmul_rn(py, nx));
-      J[3] = nx;
-      J[4] = ny;
-      J[5] = nz;
-      int k = 0;
-#pragma unroll
-      for (int a = 0; a < 6; ++a)
-#pragma unroll
-        for (int b = a; b < 6; ++b) v[k++] = __dmul_rn(J[a], J[b]);
-#pragma unroll
-      for (int a = 0; a < 6; ++a) v[21 + a] = __dmul_rn(J[a], res);
-      v[27] = __dmul_rn(res, res);
-      v[28] = static_cast<double>(bd2);
-      v[29] = 1.0;
-    }
+    f64_terms(P, p, bp, bd2, v);
     double col = 0.0;
     block_reduce_f64(v, col);
-    if (threadIdx.x < kPartial) add_fixed_f64(acc, threadIdx.x, col, sum_exponent(P, threadIdx.x, nlen));
+    if (threadIdx.x < kPartial) add_fixed_f64(acc, threadIdx.x, col, E);
   } else {
     // per-correspondence factors as one row per thread in shared memory (the
     // staged points are no longer needed), then the transposed reduction
     __syncthreads();  // every thread has finished reading the staged points
     float* rows = reinterpret_cast<float*>(stage.pts);
     float* row = rows + threadIdx.x * kRow;
-#pragma unroll
-    for (int k = 0; k < kRow; ++k) row[k] = 0.f;
-    row[kOne] = 1.f;
-    if (bp >= 0) {
-      const float4 q = P.g.pts[bp];
-      if (P.kind == kPointToPoint) {
-        // a = p - c and b = q - c as exact pairs (c = P.ctr, near the clouds)
-        const float pv[3] = {p.x, p.y, p.z}, qv[3] = {q.x, q.y, q.z};
-        float aa = 0.f, bb = 0.f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          float ah, al, bh, bl;
-          two_sum(pv[k], -P.ctr[k], ah, al);
-          two_sum(qv[k], -P.ctr[k], bh, bl);
-          row[k] = ah;
-          row[3 + k] = al;
-          row[6 + k] = bh;
-          row[9 + k] = bl;
-          aa += ah * ah;
-          bb += bh * bh;
-        }
-        row[12] = aa;
-        row[13] = bb;
-        row[14] = bd2;
-        row[15] = 1.f;
-      } else {
-        const float4 n = P.g.nrm[bp];
-        const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
-        row[0] = p.y * n.z - p.z * n.y;
-        row[1] = p.z * n.x - p.x * n.z;
-        row[2] = p.x * n.y - p.y * n.x;
-        row[3] = n.x;
-        row[4] = n.y;
-        row[5] = n.z;
-        row[6] = dx * n.x + dy * n.y + dz * n.z;
-        row[7] = bd2;
-        row[8] = 1.f;
-      }
-    }
+    row_factors(P, p, bp, bd2, [&](int k) -> float& { return row[k]; });
     __syncthreads();
     float ts = 0.f, tc = 0.f;
     block_reduce_rows(rows, P.kind, ts, tc);
-    if (threadIdx.x < kPartial) add_fixed(acc, threadIdx.x, ts, tc, sum_exponent(P, threadIdx.x, nlen));
+    if (threadIdx.x < kPartial) add_fixed(acc, threadIdx.x, ts, tc, E);
   }
-  // the last tile of the pair to arrive finishes the launch for the pair
+  // the last tile of the pair to arrive finishes the launch for the pair, unless
+  // queries of the pair wait in the fallback pass
   __shared__ bool last;
   if (threadIdx.x < kPartial) __threadfence();  // the lanes that added the partial publish it
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&P.st->arrived, 1u) == static_cast<unsigned>(P.ntiles - 1);
+  if (threadIdx.x == 0) {
+    if (n_queued) {
+      atomicAdd(&P.st->pending, static_cast<unsigned>(n_queued));
+      __threadfence();
+    }
+    last = atomicAdd(&P.st->arrived, 1u) == static_cast<unsigned>(P.ntiles - 1);
+    if (last) {
+      __threadfence();
+      P.st->arrived = 0u;  // ready for the next launch
+      last = atomicAdd(&P.st->pending, 0u) == 0u;
+    }
+  }
   __syncthreads();
   if (!last) return;
   __threadfence();
@@ -1259,7 +1578,8 @@ template <bool F64, class Cfg>
 __global__ void __launch_bounds__(kThreads, Cfg::kMinBlocks) k_icp_iter(PairDesc one, const PairDesc* __restrict__ pairs,
                                                                      const int* __restrict__ tile_pair,
                                                                      const int* __restrict__ ntiles_total, int mode,
-                                                                     unsigned* __restrict__ queue, int parity) {
+                                                                     unsigned* __restrict__ queue, int parity,
+                                                                     FallbackQueue fq) {
   __shared__ Stage<Cfg> stage;
   __shared__ PairDesc P;
   __shared__ int s_next;
@@ -1277,15 +1597,185 @@ __global__ void __launch_bounds__(kThreads, Cfg::kMinBlocks) k_icp_iter(PairDesc
   // partial).  queue[parity ^ 1] is the counter of the next launch on
   // this queue; the previous launch, which used it, has finished here.
   if (queue && blockIdx.x == 0 && threadIdx.x == 0) queue[parity ^ 1] = 0u;
+  if (fq.items && blockIdx.x == 0 && threadIdx.x == 0) {
+    fq.count[fq.parity ^ 1] = 0u;
+    fq.claim[fq.parity ^ 1] = 0u;
+  }
+  __shared__ int s_pair;
   int tile = blockIdx.x;
   while (tile < n) {
-    if (threadIdx.x == 0) P = pairs ? pairs[tile_pair[tile]] : one;
+    if (threadIdx.x == 0) {
+      s_pair = pairs ? tile_pair[tile] : 0;
+      P = pairs ? pairs[s_pair] : one;
+    }
     __syncthreads();
-    icp_tile<F64>(P, tile - P.tile0, mode, stage);
+    icp_tile<F64>(P, tile - P.tile0, mode, stage, s_pair, fq);
     if (threadIdx.x == 0)
       s_next = queue ? static_cast<int>(gridDim.x + atomicAdd(&queue[parity], 1u)) : tile + static_cast<int>(gridDim.x);
     __syncthreads();
     tile = s_next;
+  }
+}
+
+// The fallback pass of an iteration launch: the queries its tiles left (see
+// icp_tile), searched one per thread from global memory in dense blocks, the
+// search continuing from the best candidate the tile found.  Each query's terms
+// enter the sums as 64-bit fixed point in the units of their columns (those of
+// the tiles' partials): a warp whose queries belong to one pair first adds
+// them exactly by integer shuffles.  Integer sums do not depend on which block
+// or warp adds a query, nor on the order of the queue.  The warp that adds a
+// pair's last pending query marks the pair, and the block then finishes the
+// pair's launch (solve and update, or the stored results).
+template <bool F64>
+__global__ void __launch_bounds__(kThreads) k_icp_fallback(PairDesc one, const PairDesc* __restrict__ pairs, int mode,
+                                                           FallbackQueue fq) {
+  // launched as a programmatic dependent of the iteration launch whose queue it
+  // drains: wait for that grid's completion, then let the next launch place
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const unsigned full = 0xffffffffu;
+  const unsigned total = *reinterpret_cast<volatile unsigned*>(&fq.count[fq.parity]);
+  __shared__ unsigned s_base;
+  __shared__ int s_fin[kThreads];  // pair whose last pending query this lane added, or -1
+  __shared__ float s_rows[kThreads][kRow + 1];
+  __shared__ float s_ld[kList][kThreads];  // the lists being rebuilt (see ListSink)
+  __shared__ int s_lp[kList][kThreads];
+  __shared__ PairDesc s_P;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (;;) {
+    if (threadIdx.x == 0) s_base = atomicAdd(&fq.claim[fq.parity], static_cast<unsigned>(kThreads));
+    s_fin[threadIdx.x] = -1;
+    __syncthreads();
+    const unsigned base = s_base;
+    __syncthreads();
+    if (base >= total) break;
+    const unsigned e = base + threadIdx.x;
+    const bool live = e < total;
+    const int4 item = live ? fq.items[e] : make_int4(0, 0, 0, -1);
+    const bool warp_live = __any_sync(full, live);
+    // lanes past the end take lane 0's pair (lane 0 is live whenever any lane is);
+    // every lane takes part in the shuffle
+    const int pair0 = __shfl_sync(full, item.x, 0);
+    const int pair = live ? item.x : pair0;
+    const PairDesc& P = pairs ? pairs[pair] : one;
+    int bp = -1;
+    float bd2 = 0.f;
+    float3 p = make_float3(0.f, 0.f, 0.f);
+    if (live) {
+      const IcpState* st = P.st;
+      float R[9], t[3];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) R[k] = st->R[k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) t[k] = st->t[k];
+      const int i = item.y;
+      const float4 sp = P.src4[i];
+      p = xform_rn(R, t, sp.x, sp.y, sp.z);
+      Nearest nb{__fmul_rn(P.r, P.r), 0x7fffffff, -1};
+      const int hint = P.lists.pb ? P.lists.hint[i] : -1;
+      if (hint >= 0) consider(nb, P.g.pts[hint], hint, p.x, p.y, p.z);
+      if (P.lists.pb && st->lists_on && P.kind == kPointToPlane) {
+        // the point's old list bounds the rebuild; the search rebuilds it
+        const float sigma = __fmul_rn(P.r, kSkin), Rl = __fadd_rn(P.r, sigma);
+        (void)list_scan(P.g, P.lists.pb[i], P.lists.idx[2 * i], P.lists.idx[2 * i + 1], p.x, p.y, p.z, nb);
+        ListSink ls{nb, s_ld, s_lp, list_lim(nb.d2, sigma), 0, 0.f, 0};
+        box_search_batched(P.g, P.cell, p.x, p.y, p.z, Rl, ls);
+        list_store(P.lists, i, ls, p.x, p.y, p.z);
+        nb = ls.nb;
+      } else {
+        NnSink ns{nb};
+        box_search_batched(P.g, P.cell, p.x, p.y, p.z, P.r, ns);
+        nb = ns.nb;
+      }
+      bp = nb.pos;
+      bd2 = nb.d2;
+      if (P.lists.pb) P.lists.hint[i] = bp;
+      if (P.corr_out) {
+        const int o = __float_as_int(sp.w);
+        P.corr_out[o] = bp >= 0 ? __float_as_int(P.g.pts[bp].w) : -1;
+        P.d2_out[o] = bp >= 0 ? bd2 : 0.f;
+      }
+    }
+    if (mode != kCorrOnly && warp_live) {
+      // this query's value of every sum column as a fixed-point integer
+      long long v[32];
+      bool bad = false;
+      if constexpr (F64) {
+        double d[32];
+        f64_terms(P, p, bp, bd2, d);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const int E = live ? P.st->E[k] : 0;
+          const double h = d[k] * __longlong_as_double(static_cast<long long>(1023 - E) << 52);  // exact
+          const bool ok = (__double_as_longlong(h) & 0x7fffffffffffffffLL) < 0x43D0000000000000LL;  // |h| < 2^62
+          bad |= !ok;
+          v[k] = ok ? __double2ll_rn(h) : 0;
+        }
+      } else {
+        float* row = s_rows[threadIdx.x];
+        row_factors(P, p, bp, bd2, [&](int k) -> float& { return row[k]; });
+        row[kRow] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const uchar4 ix = *reinterpret_cast<const uchar4*>(kTerm[P.kind][k]);
+          const float x = row[ix.x], y = row[ix.y], xl = row[ix.z], yl = row[ix.w];
+          const float hi = __fmul_rn(x, y);
+          const float lo = fmaf(x, y, -hi) + fmaf(x, yl, xl * y);  // exact for point-to-plane (lows are 0)
+          const int E = live ? P.st->E[k] : 0;
+          const float sc = __int_as_float((127 - E) << 23);  // 2^-E
+          const float hs = hi * sc, ls = lo * sc;
+          const bool ok = fabsf(hs) < 0x1p62f && fabsf(ls) < 0x1p62f;
+          bad |= !ok;
+          v[k] = ok ? __float2ll_rn(hs) + __float2ll_rn(ls) : 0;
+        }
+      }
+      v[kBadCol] = bad ? 1 : 0;
+      if (!live) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = 0;
+      }
+      const int row = (blockIdx.x * (kThreads / 32) + warp) % P.nacc;
+      unsigned long long* const acc = P.acc + static_cast<size_t>(row) * kPartial;
+      const unsigned live_mask = __ballot_sync(full, live);
+      if (__match_any_sync(full, pair) == full) {
+        // one pair: butterfly reduce-scatter, column `lane` ends on lane `lane`
+#pragma unroll
+        for (int half = 16; half >= 1; half >>= 1) {
+          const bool upper = (lane & half) != 0;
+#pragma unroll
+          for (int j = 0; j < half; ++j) {
+            const long long send = upper ? v[j] : v[j + half];
+            const long long keep = upper ? v[j + half] : v[j];
+            v[j] = keep + __shfl_xor_sync(full, send, half);
+          }
+        }
+        if (v[0] != 0) atomicAdd(acc + lane, static_cast<unsigned long long>(v[0]));
+        __threadfence();
+        __syncwarp();
+        if (lane == 0 && mode != kCorrOnly) {
+          const unsigned n = static_cast<unsigned>(__popc(live_mask));
+          if (atomicSub(&P.st->pending, n) == n) s_fin[threadIdx.x] = pair;
+        }
+      } else if (live) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+          if (v[k] != 0) atomicAdd(acc + k, static_cast<unsigned long long>(v[k]));
+        __threadfence();
+        if (atomicSub(&P.st->pending, 1u) == 1u) s_fin[threadIdx.x] = pair;
+      }
+    }
+    __syncthreads();
+    // finish every pair whose last pending query this block added
+    for (int t = 0; t < kThreads; ++t) {
+      const int fin = s_fin[t];  // block-uniform
+      if (fin < 0) continue;
+      if (threadIdx.x == 0) s_P = pairs ? pairs[fin] : one;
+      __syncthreads();
+      __threadfence();
+      const float nlen = (s_P.kind == kPointToPlane && s_P.g.nrm) ? s_P.g.nrm[s_P.g.n].x : 0.f;
+      finish(s_P, mode, nlen);
+      __syncthreads();
+    }
   }
 }
 
@@ -1337,10 +1827,10 @@ struct TileQueue {
 
 template <bool F64, class Cfg>
 void launch_form(int ntiles, const PairDesc& one, const PairDesc* pairs, const int* tile_pair, const int* d_ntiles,
-                 int mode, cudaStream_t s, bool dependent, TileQueue q) {
+                 int mode, cudaStream_t s, bool dependent, TileQueue q, const FallbackQueue& fq) {
   const int grid = grid_for(ntiles, resident_blocks<F64, Cfg>());
   if (!dependent) {
-    k_icp_iter<F64, Cfg><<<grid, kThreads, 0, s>>>(one, pairs, tile_pair, d_ntiles, mode, q.counters, q.parity);
+    k_icp_iter<F64, Cfg><<<grid, kThreads, 0, s>>>(one, pairs, tile_pair, d_ntiles, mode, q.counters, q.parity, fq);
     return;
   }
   // programmatic dependent launch: the grid is placed while the previous
@@ -1354,21 +1844,67 @@ void launch_form(int ntiles, const PairDesc& one, const PairDesc* pairs, const i
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, k_icp_iter<F64, Cfg>, one, pairs, tile_pair, d_ntiles, mode, q.counters, q.parity) !=
-      cudaSuccess) {
+  if (cudaLaunchKernelEx(&cfg, k_icp_iter<F64, Cfg>, one, pairs, tile_pair, d_ntiles, mode, q.counters, q.parity,
+                         fq) != cudaSuccess) {
     (void)cudaGetLastError();
-    k_icp_iter<F64, Cfg><<<grid, kThreads, 0, s>>>(one, pairs, tile_pair, d_ntiles, mode, q.counters, q.parity);
+    k_icp_iter<F64, Cfg><<<grid, kThreads, 0, s>>>(one, pairs, tile_pair, d_ntiles, mode, q.counters, q.parity, fq);
   }
 }
 
-// One launch of the iteration kernel over `ntiles` work items on stream s;
-// `dependent`: as a programmatic dependent of the preceding kernel of s.
+// Blocks of the fallback pass resident on the GPU together (computed once).
+template <bool F64>
+int fallback_blocks() {
+  static const int resident = [] {
+    int dev = 0, sms = kNumSMs, per_sm = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_icp_fallback<F64>, kThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    (void)cudaGetLastError();
+    return sms * per_sm;
+  }();
+  return resident;
+}
+
+// The fallback pass after an iteration launch over `ntiles` tiles (at most
+// kStagedMin queued queries each), as a programmatic dependent when `pdl`.
+template <bool F64>
+void launch_fallback(int ntiles, const PairDesc& one, const PairDesc* pairs, int mode, cudaStream_t s, bool pdl,
+                     const FallbackQueue& fq) {
+  const int64_t cap = static_cast<int64_t>(ntiles) * kStagedMin;
+  const int grid = static_cast<int>(std::min<int64_t>(fallback_blocks<F64>(), (cap + kThreads - 1) / kThreads));
+  if (pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid < 1 ? 1 : grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_icp_fallback<F64>, one, pairs, mode, fq) == cudaSuccess) return;
+    (void)cudaGetLastError();
+  }
+  k_icp_fallback<F64><<<grid < 1 ? 1 : grid, kThreads, 0, s>>>(one, pairs, mode, fq);
+}
+
+// One launch of the iteration kernel over `ntiles` work items on stream s, and
+// its fallback pass when fq has a queue; `dependent`: the iteration launch as a
+// programmatic dependent of the preceding kernel of s; `pdl`: the pass as one
+// of the iteration launch.
 void launch_iter(bool f64, int ntiles, const PairDesc& one, const PairDesc* pairs, const int* tile_pair,
-                 const int* d_ntiles, int mode, cudaStream_t s, bool dependent = false, TileQueue q = TileQueue{}) {
-  if (f64) launch_form<true, CfgLatency>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent, q);
+                 const int* d_ntiles, int mode, cudaStream_t s, bool dependent = false, TileQueue q = TileQueue{},
+                 const FallbackQueue& fq = FallbackQueue{}, bool pdl = true) {
+  if (f64) launch_form<true, CfgLatency>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent, q, fq);
   else if (throughput_form(ntiles))
-    launch_form<false, CfgThroughput>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent, q);
-  else launch_form<false, CfgLatency>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent, q);
+    launch_form<false, CfgThroughput>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent, q, fq);
+  else launch_form<false, CfgLatency>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent, q, fq);
+  if (fq.items && kStagedMin > 0) {
+    if (f64) launch_fallback<true>(ntiles, one, pairs, mode, s, pdl, fq);
+    else launch_fallback<false>(ntiles, one, pairs, mode, s, pdl, fq);
+    count_launch();
+  }
 }
 
 inline int iter_blocks(int64_t ns) {
@@ -1432,11 +1968,12 @@ struct Work {
   const int* aux = nullptr;     // its flags (aux[6]: a non-finite coordinate)
   DevBuf state;
   DevBuf acc;    // accum_rows(nblk) x kPartial fixed-point sums
-  DevBuf hints;  // per source point: sorted target position of its last match, or -1
-  DevBuf queue;  // the dynamic tile queue (2 counters)
+  DevBuf lists;  // per source point candidate lists (see ListSink): ns float4, then 2 ns int4
+  DevBuf queue;  // the dynamic tile queue (2 counters), then the fallback queue's counters (4)
+  DevBuf fq_items;  // the fallback queue (nblk x kStagedMin entries)
   int nblk = 1;
   int launches = 0;  // launches so far (the queue parity)
-  explicit Work(cudaStream_t s) : src(s), state(s), acc(s), hints(s), queue(s) {}
+  explicit Work(cudaStream_t s) : src(s), state(s), acc(s), lists(s), queue(s), fq_items(s) {}
   int32_t prepare(const float* d_src, int64_t ns, int32_t stride, float cell, const double* T, cudaStream_t s,
                   const SortedCloud* pre = nullptr) {
     if (pre) {
@@ -1452,10 +1989,11 @@ struct Work {
     const size_t acc_bytes = sizeof(unsigned long long) * kPartial * accum_rows(nblk);
     O3G_TRY(acc.alloc(acc_bytes));
     O3G_TRY(cudaMemsetAsync(acc.p, 0, acc_bytes, s));
-    O3G_TRY(queue.alloc(sizeof(unsigned) * 2));
-    O3G_TRY(cudaMemsetAsync(queue.p, 0, sizeof(unsigned) * 2, s));
-    O3G_TRY(hints.alloc(sizeof(int32_t) * (ns > 0 ? ns : 1)));
-    O3G_TRY(cudaMemsetAsync(hints.p, 0xff, sizeof(int32_t) * (ns > 0 ? ns : 1), s));
+    O3G_TRY(queue.alloc(sizeof(unsigned) * 6));
+    O3G_TRY(cudaMemsetAsync(queue.p, 0, sizeof(unsigned) * 6, s));
+    O3G_TRY(fq_items.alloc(sizeof(int4) * static_cast<size_t>(nblk) * kStagedMin));
+    O3G_TRY(lists.alloc(kListBytes * (ns > 0 ? ns : 1)));
+    O3G_TRY(cudaMemsetAsync(lists.p, 0xff, kListBytes * (ns > 0 ? ns : 1), s));  // no lists yet
     k_init_state<<<1, 32, 0, s>>>(state.as<IcpState>(), to_pose(T));
     count_launch();
     return O3G_OK;
@@ -1479,11 +2017,17 @@ struct Work {
     P.tile0 = 0;
     P.st = state.as<IcpState>();
     set_sums(P, g, acc.as<unsigned long long>());
-    P.hints = (mode == kIterate || mode == kEvaluate) ? hints.as<int32_t>() : nullptr;
+    P.lists = (mode == kIterate || mode == kEvaluate) ? list_ref(lists.p, ns) : ListRef{nullptr, nullptr, nullptr};
+    P.list_motion = list_motion(ns, r);
     P.corr_out = corr;
     P.d2_out = d2;
+    FallbackQueue fq;
+    fq.items = fq_items.as<int4>();
+    fq.count = queue.as<unsigned>() + 2;
+    fq.claim = queue.as<unsigned>() + 4;
+    fq.parity = launches & 1;
     launch_iter(f64, nblk, P, nullptr, nullptr, nullptr, mode, s, dependent,
-                TileQueue{queue.as<unsigned>(), launches & 1});
+                TileQueue{queue.as<unsigned>(), launches & 1}, fq);
     ++launches;
     count_launch();
     return O3G_OK;
@@ -1495,7 +2039,7 @@ struct Work {
 int32_t icp_run(const o3g_grid* g, const float* d_src, int64_t ns, int32_t stride, const double* init_T,
                 double max_corr_dist, int32_t max_iter, double eps, double* out_T, double* out_fitness,
                 double* out_rmse, int32_t* out_iters, cudaStream_t s, int32_t precision, bool point_to_point,
-                const SortedCloud* pre) {
+                const SortedCloud* pre, int32_t* d_corr, float* d_d2) {
   const char* fn = point_to_point ? "o3g_icp_point_to_point_grid" : "o3g_icp_point_to_plane_grid";
   const int kind = point_to_point ? kPointToPoint : kPointToPlane;
   if (precision != O3G_PREC_F32_COMPENSATED && precision != O3G_PREC_F64) {
@@ -1525,7 +2069,7 @@ int32_t icp_run(const o3g_grid* g, const float* d_src, int64_t ns, int32_t strid
     TimedRegion tr(O3G_KERNEL_ICP_CORR, s);
     w.launch(g, n, r, eps, kIterate, nullptr, nullptr, s, f64, kind, it > 0);
   }
-  w.launch(g, n, r, eps, kEvaluate, nullptr, nullptr, s, f64, kind, max_iter > 0);
+  w.launch(g, n, r, eps, kEvaluate, d_corr, d_d2, s, f64, kind, max_iter > 0);
   O3G_TRY(cudaGetLastError());
   IcpState h;
   int aux[8];
@@ -1647,6 +2191,19 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_ex(const o3g_grid* g, const float
                                                   double* out_rmse, int32_t* out_iters, void* stream) {
   return icp_run(g, d_src, ns, stride, init_T, max_corr_dist, max_iter, eps, out_T, out_fitness, out_rmse, out_iters,
                  static_cast<cudaStream_t>(stream), precision);
+}
+
+extern "C" int32_t o3g_icp_point_to_plane_grid_corr(const o3g_grid* g, const float* d_src, int64_t ns,
+                                                    int32_t stride, const double* init_T, double max_corr_dist,
+                                                    int32_t max_iter, double eps, int32_t precision, double* out_T,
+                                                    double* out_fitness, double* out_rmse, int32_t* out_iters,
+                                                    int32_t* d_corr, float* d_d2, void* stream) {
+  if (ns > 0 && (!d_corr || !d_d2)) {
+    set_error("o3g_icp_point_to_plane_grid_corr: the correspondence outputs are null");
+    return O3G_ERR_ARG;
+  }
+  return icp_run(g, d_src, ns, stride, init_T, max_corr_dist, max_iter, eps, out_T, out_fitness, out_rmse, out_iters,
+                 static_cast<cudaStream_t>(stream), precision, false, nullptr, d_corr, d_d2);
 }
 
 extern "C" int32_t o3g_icp_point_to_plane(const float* d_src, int64_t ns, int32_t src_stride, const float* d_tgt,
@@ -1789,7 +2346,8 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const 
     P.tile0 = 0;
     P.st = st;
     set_sums(P, g, acc);
-    P.hints = nullptr;
+    P.lists = ListRef{nullptr, nullptr, nullptr};
+    P.list_motion = -1.f;
     P.corr_out = nullptr;
     P.d2_out = nullptr;
     launch_iter(false, nblk, P, nullptr, nullptr, nullptr, mode, s);
@@ -1849,12 +2407,18 @@ cudaError_t graph_stream(cudaStream_t* out) {
 // Launches `iters` iteration steps and one evaluation step of the batch on s,
 // through a captured CUDA graph when capture works, else directly.
 int32_t run_iterations(const PairDesc* descs, const int* tile_pair, const int* d_ntiles, int ntiles, int max_iter,
-                       double eps, unsigned* queue, cudaStream_t s) {
+                       double eps, unsigned* queue, int4* fq_items, cudaStream_t s) {
   PairDesc dummy{};
   auto enqueue = [&](cudaStream_t q) {
-    for (int it = 0; it <= max_iter; ++it)
+    for (int it = 0; it <= max_iter; ++it) {
+      FallbackQueue fq;
+      fq.items = fq_items;
+      fq.count = queue + 2;
+      fq.claim = queue + 4;
+      fq.parity = it & 1;
       launch_iter(false, ntiles, dummy, descs, tile_pair, d_ntiles, it < max_iter ? kIterate : kEvaluate, q, false,
-                  TileQueue{queue, it & 1});
+                  TileQueue{queue, it & 1}, fq, false);
+    }
   };
   cudaStream_t cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -1881,7 +2445,7 @@ int32_t run_iterations(const PairDesc* descs, const int* tile_pair, const int* d
     (void)cudaGetLastError();
     enqueue(s);  // capture unavailable: plain launches, same work
   }
-  count_launch(max_iter + 1);
+  count_launch(max_iter + 1);  // the iteration launches (launch_iter counts the fallback passes)
   O3G_TRY(cudaGetLastError());
   return O3G_OK;
 }
@@ -1943,7 +2507,8 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t total = off[n_pairs];
-  DevBuf d_ptrs(s), d_strides(s), d_off(s), d_src4(s), d_aux(s), d_states(s), d_acc(s), d_cnt(s), d_hints(s),
+  DevBuf d_fq(s);
+  DevBuf d_ptrs(s), d_strides(s), d_off(s), d_src4(s), d_aux(s), d_states(s), d_acc(s), d_cnt(s), d_lists(s),
       d_descs(s), d_tiles(s), d_poses(s);
   O3G_TRY(d_ptrs.alloc(sizeof(float*) * n_pairs));
   O3G_TRY(d_strides.alloc(sizeof(int32_t) * n_pairs));
@@ -1952,8 +2517,9 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   O3G_TRY(d_aux.alloc(sizeof(int) * 8 * n_pairs));
   O3G_TRY(d_states.alloc(sizeof(IcpState) * n_pairs));
   O3G_TRY(d_acc.alloc(sizeof(unsigned long long) * kPartial * rows_total));
-  O3G_TRY(d_cnt.alloc(sizeof(unsigned) * 2));  // the tile queue
-  O3G_TRY(d_hints.alloc(sizeof(int32_t) * (total > 0 ? total : 1)));
+  O3G_TRY(d_cnt.alloc(sizeof(unsigned) * 6));  // the tile queue, then the fallback queue's counters
+  O3G_TRY(d_fq.alloc(sizeof(int4) * static_cast<size_t>(tiles_total) * kStagedMin));
+  O3G_TRY(d_lists.alloc(kListBytes * (total > 0 ? total : 1)));
   O3G_TRY(d_descs.alloc(sizeof(PairDesc) * n_pairs));
   O3G_TRY(d_tiles.alloc(sizeof(int) * (tiles_total + 1)));
   O3G_TRY(d_poses.alloc(sizeof(double) * 16 * n_pairs));
@@ -1978,7 +2544,8 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
     P.tile0 = static_cast<int>(t0);
     P.st = states + p;
     set_sums(P, tgts[p], acc + static_cast<size_t>(kPartial) * a0);
-    P.hints = d_hints.as<int32_t>() + off[p];
+    P.lists = list_ref(static_cast<unsigned char*>(d_lists.p) + kListBytes * off[p], ns[p]);
+    P.list_motion = list_motion(ns[p], P.r);
     P.corr_out = nullptr;
     P.d2_out = nullptr;
     for (int k = 0; k < ntiles[p]; ++k) tile_pair[t0 + k] = p;
@@ -1993,9 +2560,9 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   O3G_TRY(cudaMemcpyAsync(d_descs.p, descs.data(), sizeof(PairDesc) * n_pairs, cudaMemcpyHostToDevice, s));
   O3G_TRY(cudaMemcpyAsync(d_tiles.p, tile_pair.data(), sizeof(int) * (tiles_total + 1), cudaMemcpyHostToDevice, s));
   O3G_TRY(cudaMemcpyAsync(d_poses.p, init_T, sizeof(double) * 16 * n_pairs, cudaMemcpyHostToDevice, s));
-  O3G_TRY(cudaMemsetAsync(d_cnt.p, 0, sizeof(unsigned) * 2, s));
+  O3G_TRY(cudaMemsetAsync(d_cnt.p, 0, sizeof(unsigned) * 6, s));
   O3G_TRY(cudaMemsetAsync(d_acc.p, 0, sizeof(unsigned long long) * kPartial * rows_total, s));
-  O3G_TRY(cudaMemsetAsync(d_hints.p, 0xff, sizeof(int32_t) * (total > 0 ? total : 1), s));
+  O3G_TRY(cudaMemsetAsync(d_lists.p, 0xff, kListBytes * (total > 0 ? total : 1), s));
   O3G_TRY_STATUS(sort_clouds_batch(reinterpret_cast<const float* const*>(d_ptrs.p), d_strides.as<int32_t>(),
                                    d_off.as<int64_t>(), n_pairs, total, s, d_src4.as<float4>(), d_aux.as<int>()));
   k_init_states<<<(n_pairs + 127) / 128, 128, 0, s>>>(states, d_poses.as<double>(), n_pairs);
@@ -2003,7 +2570,8 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   {
     TimedRegion tr(O3G_KERNEL_ICP_BATCH, s);
     O3G_TRY_STATUS(run_iterations(d_descs.as<PairDesc>(), d_tiles.as<int>(), d_tiles.as<int>() + tiles_total,
-                                  static_cast<int>(tiles_total), max_iter, eps, d_cnt.as<unsigned>(), s));
+                                  static_cast<int>(tiles_total), max_iter, eps, d_cnt.as<unsigned>(),
+                                  d_fq.as<int4>(), s));
   }
   std::vector<IcpState> h(n_pairs);
   std::vector<int> aux(8 * n_pairs);
@@ -2049,7 +2617,7 @@ struct o3g_server {
     o3g_grid* grid = nullptr;
     float4* src4 = nullptr;
     int* src_aux = nullptr;
-    int32_t* hints = nullptr;
+    void* lists = nullptr;  // candidate lists (kListBytes per source point)
     unsigned long long* acc = nullptr;  // accum_rows(ntiles) x kPartial fixed-point sums
     int ns = 0, ntiles = 1;
     int max_iter = 0;
@@ -2075,7 +2643,9 @@ struct o3g_server {
   void* descs = nullptr;    // max_active PairDesc
   int* tiles = nullptr;     // tile table (+1 count), grows
   int64_t tiles_cap = 0;
-  unsigned* queue = nullptr;  // the dynamic tile queue of the server's launches (2 counters)
+  unsigned* queue = nullptr;  // the dynamic tile queue of the server's launches (2 counters), then the
+                              // fallback queue's counters (4)
+  int4* fq_items = nullptr;   // the fallback queue, kStagedMin entries per tile of tiles_cap
   int64_t launches = 0;
   std::map<int64_t, Result> finished;
 };
@@ -2086,15 +2656,15 @@ namespace {
 // Device memory a request will hold while admitted (upper bound before its grid exists).
 int64_t request_bytes(int64_t ns, int64_t nt) {
   const int64_t rows = accum_rows(iter_blocks(ns));
-  return ns * (16 + 4 + 12) + rows * kPartial * 8 + nt * (16 + 16 + 4 + 12 + 12) + 4 * (32 * nt + (1 << 20)) +
-         sizeof(IcpState);
+  return ns * (16 + 48 + 12) + rows * kPartial * 8 + nt * (16 + 16 + 4 + 12 + 12) +
+         4 * (32 * nt + (1 << 20)) + sizeof(IcpState);
 }
 
 void release_slot(o3g_server* sv, o3g_server::Slot& sl) {
   if (sl.grid) o3g_free_grid(sl.grid);
   dfree(sl.src4, sv->s);
   dfree(sl.src_aux, sv->s);
-  dfree(sl.hints, sv->s);
+  dfree(sl.lists, sv->s);
   dfree(sl.acc, sv->s);
   sv->used -= sl.bytes;
   sl = o3g_server::Slot();
@@ -2133,8 +2703,8 @@ int32_t admit(o3g_server* sv, int k, o3g_server::Request& rq) {
   sl.src_aux = sc.aux.as<int>();
   sc.buf.p = nullptr;  // now owned by the slot
   sc.aux.p = nullptr;
-  O3G_TRY(dmalloc(reinterpret_cast<void**>(&sl.hints), sizeof(int32_t) * (ns > 0 ? ns : 1), s));
-  O3G_TRY(cudaMemsetAsync(sl.hints, 0xff, sizeof(int32_t) * (ns > 0 ? ns : 1), s));
+  O3G_TRY(dmalloc(&sl.lists, kListBytes * (ns > 0 ? ns : 1), s));
+  O3G_TRY(cudaMemsetAsync(sl.lists, 0xff, kListBytes * (ns > 0 ? ns : 1), s));
   const size_t acc_bytes = sizeof(unsigned long long) * kPartial * accum_rows(sl.ntiles);
   O3G_TRY(dmalloc(reinterpret_cast<void**>(&sl.acc), acc_bytes, s));
   O3G_TRY(cudaMemsetAsync(sl.acc, 0, acc_bytes, s));
@@ -2162,7 +2732,8 @@ PairDesc slot_desc(o3g_server* sv, int k, int tile0) {
   P.tile0 = tile0;
   P.st = static_cast<IcpState*>(sv->states) + k;
   set_sums(P, sl.grid, sl.acc);
-  P.hints = sl.hints;
+  P.lists = list_ref(sl.lists, sl.ns);
+  P.list_motion = list_motion(sl.ns, sl.r);
   P.corr_out = nullptr;
   P.d2_out = nullptr;
   return P;
@@ -2182,15 +2753,23 @@ int32_t launch_slots(o3g_server* sv, const std::vector<int>& ks, int mode) {
   tiles.push_back(static_cast<int>(t0));
   if (static_cast<int64_t>(tiles.size()) > sv->tiles_cap) {
     dfree(sv->tiles, s);
+    dfree(sv->fq_items, s);
     sv->tiles = nullptr;
+    sv->fq_items = nullptr;
     sv->tiles_cap = static_cast<int64_t>(tiles.size()) * 2;
     O3G_TRY(dmalloc(reinterpret_cast<void**>(&sv->tiles), sizeof(int) * sv->tiles_cap, s));
+    O3G_TRY(dmalloc(reinterpret_cast<void**>(&sv->fq_items), sizeof(int4) * sv->tiles_cap * kStagedMin, s));
   }
   O3G_TRY(cudaMemcpyAsync(sv->descs, d.data(), sizeof(PairDesc) * d.size(), cudaMemcpyHostToDevice, s));
   O3G_TRY(cudaMemcpyAsync(sv->tiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice, s));
   PairDesc dummy{};
+  FallbackQueue fq;
+  fq.items = sv->fq_items;
+  fq.count = sv->queue + 2;
+  fq.claim = sv->queue + 4;
+  fq.parity = static_cast<int>(sv->launches & 1);
   launch_iter(false, static_cast<int>(t0), dummy, static_cast<const PairDesc*>(sv->descs), sv->tiles, sv->tiles + t0,
-              mode, s, false, TileQueue{sv->queue, static_cast<int>(sv->launches & 1)});
+              mode, s, false, TileQueue{sv->queue, static_cast<int>(sv->launches & 1)}, fq);
   ++sv->launches;
   count_launch();
   O3G_TRY(cudaGetLastError());
@@ -2223,8 +2802,8 @@ extern "C" int32_t o3g_server_create(int32_t max_active, int64_t hbm_budget_byte
   sv->slots.resize(max_active);
   cudaError_t e = dmalloc(&sv->states, sizeof(IcpState) * max_active, sv->s);
   if (e == cudaSuccess) e = dmalloc(&sv->descs, sizeof(PairDesc) * max_active, sv->s);
-  if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void**>(&sv->queue), sizeof(unsigned) * 2, sv->s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(sv->queue, 0, sizeof(unsigned) * 2, sv->s);
+  if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void**>(&sv->queue), sizeof(unsigned) * 6, sv->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sv->queue, 0, sizeof(unsigned) * 6, sv->s);
   if (e != cudaSuccess) {
     dfree(sv->states, sv->s);
     dfree(sv->descs, sv->s);
@@ -2244,6 +2823,7 @@ extern "C" int32_t o3g_server_destroy(o3g_server* sv) {
   dfree(sv->states, sv->s);
   dfree(sv->descs, sv->s);
   dfree(sv->tiles, sv->s);
+  dfree(sv->fq_items, sv->s);
   dfree(sv->queue, sv->s);
   (void)cudaStreamSynchronize(sv->s);
   delete sv;
@@ -2458,9 +3038,10 @@ __global__ void __launch_bounds__(kThreads, Cfg::kMinBlocks) k_eval_poses(GridVi
     const bool live = i < ns;
     const float4 s = live ? src4[i] : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
     const float3 p = live ? xform_rn(R, t, s.x, s.y, s.z) : make_float3(3.0e38f, 3.0e38f, 3.0e38f);
-    Nearest nb{r2, 0x7fffffff, -1};
-    if (!staged_search(g, cell, p.x, p.y, p.z, r, live, nb, stage) && live)
-      box_search_global(g, cell, p.x, p.y, p.z, r, nb);
+    NnSink ns{Nearest{r2, 0x7fffffff, -1}};
+    if (!staged_search(g, cell, p.x, p.y, p.z, r, live, ns, stage) && live)
+      box_search_global(g, cell, p.x, p.y, p.z, r, ns);
+    const Nearest nb = ns.nb;
     double cnt = (live && nb.pos >= 0) ? 1.0 : 0.0;
     double d2 = (live && nb.pos >= 0) ? static_cast<double>(nb.d2) : 0.0;
 #pragma unroll

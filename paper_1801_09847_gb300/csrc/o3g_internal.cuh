@@ -140,6 +140,13 @@ __device__ __forceinline__ float search_margin(float cell, float r, float px, fl
                    __fmul_rn(fmaxf(fmaxf(fabsf(px), fabsf(py)), fabsf(pz)), 4e-6f));
 }
 
+// sqrt(x) for x >= 0 from the hardware reciprocal square root (a few ulp): the
+// search bounds add a relative margin far larger than that error.
+__device__ __forceinline__ float fast_sqrt(float x) {
+  const float y = fmaxf(x, 1e-30f);
+  return y * rsqrtf(y);
+}
+
 // d2 = (dx*dx + dy*dy) + dz*dz with d = p - q, every operation rounded on its own.
 __device__ __forceinline__ float dist2_rn(float px, float py, float pz, float4 q) {
   float dx = __fsub_rn(px, q.x), dy = __fsub_rn(py, q.y), dz = __fsub_rn(pz, q.z);
@@ -165,7 +172,8 @@ namespace o3g {
 int32_t icp_run(const o3g_grid* g, const float* d_src, int64_t ns, int32_t stride, const double* init_T,
                 double max_corr_dist, int32_t max_iter, double eps, double* out_T, double* out_fitness,
                 double* out_rmse, int32_t* out_iters, cudaStream_t s, int32_t precision = O3G_PREC_F32_COMPENSATED,
-                bool point_to_point = false, const SortedCloud* pre = nullptr);
+                bool point_to_point = false, const SortedCloud* pre = nullptr, int32_t* d_corr = nullptr,
+                float* d_d2 = nullptr);
 // A library-owned non-blocking stream per device for work beside the caller's stream.
 cudaError_t side_stream(cudaStream_t* out);
 int32_t estimate_normals_impl(o3g_grid* g, float radius, int32_t max_nn, const float* viewpoint, float* d_out,

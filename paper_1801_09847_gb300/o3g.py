@@ -66,6 +66,8 @@ _SIGNATURES = {
                                         _i32p, _vp], _i32),
     "o3g_icp_point_to_plane_grid": ([_vp, _vp, _i64, _i32, _f64p, _f64, _i32, _f64, _f64p, _f64p, _f64p, _i32p, _vp],
                                     _i32),
+    "o3g_icp_point_to_plane_grid_corr": ([_vp, _vp, _i64, _i32, _f64p, _f64, _i32, _f64, _i32, _f64p, _f64p, _f64p,
+                                          _i32p, _vp, _vp, _vp], _i32),
     "o3g_icp_point_to_plane": ([_vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64, _i32, _f64p, _f64, _i32, _f64p, _f64p,
                                 _f64p], _i32),
     "o3g_register_point_to_plane": ([_vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _f32, _i32, _f64p, _f64, _i32, _f64,
@@ -285,15 +287,29 @@ def _result(st, T, fit, rmse, iters):
 
 
 def icp_point_to_plane_grid(grid: Grid, src, init_T, max_corr_dist: float, max_iter: int, eps: float = 0.0,
-                            stream=None, precision="f32") -> dict:
+                            stream=None, precision="f32", correspondences: bool = False) -> dict:
     """registration_icp(..., TransformationEstimationPointToPlane()) against a resident target grid.
 
-    precision "f32" (float32 terms, compensated block sums) or "f64" (all float64).
+    precision "f32" (float32 terms, compensated block sums) or "f64" (all float64).  correspondences=True adds the
+    correspondence set at the final pose: "corr" (int32 [ns], original target index or -1) and "d2" (float32 [ns])
+    as CUDA tensors (o3g_icp_point_to_plane_grid_corr).
     """
     p, ns, stride = _cloud(src, "src")
     T0 = _pose(init_T)
     T = np.zeros(16)
     fit, rmse, iters = _f64(), _f64(), _i32()
+    if correspondences:
+        torch = _torch()
+        corr = torch.empty((ns,), dtype=torch.int32, device="cuda")
+        d2 = torch.empty((ns,), dtype=torch.float32, device="cuda")
+        st = lib().o3g_icp_point_to_plane_grid_corr(grid.handle, p, ns, stride, _pp(T0), float(max_corr_dist),
+                                                    int(max_iter), float(eps), _precision(precision), _pp(T),
+                                                    ctypes.byref(fit), ctypes.byref(rmse), ctypes.byref(iters),
+                                                    _vp(corr.data_ptr()), _vp(d2.data_ptr()), _stream(stream))
+        st = _check(st, "o3g_icp_point_to_plane_grid_corr")
+        out = _result(st, T, fit, rmse, iters)
+        out["corr"], out["d2"] = corr, d2
+        return out
     if _precision(precision) == PREC_F32_COMPENSATED:
         st = lib().o3g_icp_point_to_plane_grid(grid.handle, p, ns, stride, _pp(T0), float(max_corr_dist),
                                                int(max_iter), float(eps), _pp(T), ctypes.byref(fit),

@@ -668,6 +668,40 @@ def test_combined_call_with_gpu_normals_shadows_oracle(o3g, room):
     assert last["rmse"] == pytest.approx(ev["rmse"], rel=1e-6)
 
 
+@pytest.mark.parametrize("case", ["room", "ties", "sphere_plane"])
+def test_warm_search_correspondence_set_bitexact(o3g, room, case):
+    """The correspondence set at the final pose of an ICP run, found by the warm-started search the iterations
+    use (the previous matches as first candidates, the walk through the first candidate's neighbour record when
+    it covers the query, the grid search otherwise), bit-exact against the oracle at the GPU's own final pose:
+    the full RGB-D-frame pair, a quantised cloud with exact ties and duplicate points, and the sphere-plane pair,
+    after several iteration counts (0 = the cold search alone)."""
+    if case == "room":
+        src, tgt, r = room.src, room.tgt, room.max_corr_dist
+        nrm = oracle.estimate_normals(tgt, 0.05, 30)
+        method = "grid"
+    elif case == "ties":
+        g = synth.rng(4321)
+        tgt = tie_cloud(g, 6000, quant=0.01)
+        # a moved copy, quantised again: many exactly equal distances, duplicate sources
+        src = np.round(synth.apply_T(synth.perturbation(g, 2.0, 0.02), tgt[:5000]) / 0.01) * 0.01
+        src = src.astype(np.float32)
+        nrm = g.normal(size=tgt.shape)
+        nrm = (nrm / np.linalg.norm(nrm, axis=1, keepdims=True)).astype(np.float32)
+        r, method = 0.08, "brute"
+    else:
+        pr = synth.sphere_plane_pair()
+        src, tgt, nrm, r, method = pr.src, pr.tgt, pr.tgt_nrm, pr.max_corr_dist, "brute"
+    grid = o3g.build_grid(cuda(tgt), r * 1.002)
+    grid.set_normals(cuda(nrm))
+    d_src = cuda(src)
+    for k in (0, 1, 2, 5, 30):
+        res = o3g.icp_point_to_plane_grid(grid, d_src, np.eye(4), r, k, correspondences=True)
+        p = oracle.transform(src, res["T"])
+        c_ref, d_ref = oracle.nn(p, tgt, r, method=method)
+        assert np.array_equal(res["corr"].cpu().numpy(), c_ref), (case, k)
+        assert np.array_equal(res["d2"].cpu().numpy(), d_ref), (case, k)
+
+
 def test_launch_forms_give_identical_results(o3g):
     """The latency and throughput forms of the iteration kernel differ only in stage size and occupancy: the
     correspondences are exact either way and the sums run in the same order, so results are bit-identical."""

@@ -184,3 +184,17 @@ def test_fragment_icp_both_precisions_within_1e6(o3g, frag, frag_oracle):
         ang, dt = synth.pose_error(res["T"], ref["T"])
         assert ang <= POSE_TOL and dt <= POSE_TOL, (prec, ang, dt)
         assert abs(res["fitness"] - ref["fitness"]) <= 1e-5
+
+
+def test_fragment_warm_search_correspondence_set_bitexact(o3g, frag):
+    """The correspondence set of the final evaluation (found by the warm-started search of the iterations: the
+    neighbour-record walk, with the grid search for the rest) after 1, 3 and 50 iterations: all 2M matches
+    bit-exact against the oracle's search at the GPU's own final pose."""
+    pr, grid, src = frag
+    for k in (1, 3, pr.max_iter):
+        res = o3g.icp_point_to_plane_grid(grid, src, np.eye(4), pr.max_corr_dist, k, correspondences=True)
+        p = oracle.transform(pr.src, res["T"])
+        c_ref, d_ref = oracle.nn(p, pr.tgt, pr.max_corr_dist, method="grid")
+        assert np.array_equal(res["corr"].cpu().numpy(), c_ref), k
+        assert np.array_equal(res["d2"].cpu().numpy(), d_ref), k
+        assert res["fitness"] == float(np.count_nonzero(c_ref >= 0)) / len(c_ref)
