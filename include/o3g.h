@@ -350,6 +350,22 @@ O3G_API int32_t o3g_set_tile_config(int32_t size_class, int32_t cfg);
 O3G_API int32_t o3g_get_tile_config(int32_t size_class);
 
 /*
+ * Points per thread of the ICP iteration kernels (the autotuner's second knob;
+ * no counterpart in the paper): a tile of the iteration kernel is ppt
+ * consecutive groups of 128 spatially sorted source points, reduced group by
+ * group into one partial of the pair's sums.  Set per size class of the PAIR,
+ * size_class = floor(log2(source points)), 0..31, so that a registration tiles
+ * the same way alone, in a batch and in the server (and gives the same result
+ * in all three).  ppt: 0 automatic (1 below 2^18 points, 2 below 2^20, 4 from there), 1, 2 or
+ * 4; anything else, or a class outside 0..31, is O3G_ERR_ARG.  A different ppt
+ * changes the order in which the block partials are formed, so results change
+ * in the last bits (within the parity tolerances).  Process-wide.
+ * o3g_get_points_per_thread returns the setting or O3G_ERR_ARG.
+ */
+O3G_API int32_t o3g_set_points_per_thread(int32_t size_class, int32_t ppt);
+O3G_API int32_t o3g_get_points_per_thread(int32_t size_class);
+
+/*
  * Hypothesis validation (the step RANSAC-based global registration spends its
  * time in, Sec. 3.3): for each candidate pose T_h, the correspondence step of
  * o3g_correspondences at T_h over the whole source, then

@@ -58,8 +58,6 @@ struct IcpState {
   int nonfinite;   // the normal equations were not finite
   int lists_on;    // candidate lists are kept (the updates have become small; see ListSink)
   unsigned arrived;  // tiles of the current launch whose sums are added
-  unsigned pending;  // queries of the current launch left to the fallback pass (see k_icp_fallback)
-  int E[32];         // fixed-point exponent of each sum column (see sum_exponent), written by the tiles
   double A[36];
   double b[6];
   double stats[3];  // sum r^2, sum d2, |C|
@@ -85,7 +83,6 @@ __global__ void k_init_state(IcpState* st, Pose T) {
   st->nonfinite = 0;
   st->lists_on = 0;
   st->arrived = 0u;
-  st->pending = 0u;
   st->fitness = 0.0;
   st->rmse = 0.0;
 }
@@ -108,7 +105,6 @@ __global__ void k_init_states(IcpState* st, const double* __restrict__ poses, in
     S.nonfinite = 0;
     S.lists_on = 0;
     S.arrived = 0u;
-    S.pending = 0u;
     S.fitness = 0.0;
     S.rmse = 0.0;
   }
@@ -161,6 +157,7 @@ struct NnSink {
 // about sigma; a point whose list no longer covers it searches the grid and
 // rebuilds its list.
 constexpr int kList = 8;
+constexpr int kListVec = kList / 4;  // int4 words of one point's list
 constexpr float kSkin = 0.1f;
 
 // The bound a list rebuilt at p takes its candidates within: (sqrt(D) + sigma)^2,
@@ -223,10 +220,11 @@ struct ListSink {
 // positions (-1: empty).  rho2 NaN (the initial all-ones bytes): no list.
 struct ListRef {
   float4* pb;  // per source point
-  int4* idx;   // 2 per source point
+  int4* idx;   // kListVec per source point
   int* hint;   // per source point: sorted target position of its last match, or -1
 };
-constexpr size_t kListBytes = 64;  // per source point (a multiple of 16: buffers of many pairs stay aligned)
+// bytes per source point, a multiple of 16 (buffers of many pairs stay aligned)
+constexpr size_t kListBytes = (sizeof(float4) * (1 + kListVec) + sizeof(int) + 15) / 16 * 16;
 
 // Candidate lists pay where an iteration launch is bound by throughput rather
 // than by the latency of one wave of tiles: a pair keeps them when it has at
@@ -240,15 +238,22 @@ inline float list_motion(int64_t ns, float r) { return ns >= kListMinPoints ? 0.
 inline ListRef list_ref(void* base, int64_t n) {
   float4* pb = static_cast<float4*>(base);
   int4* idx = reinterpret_cast<int4*>(pb + n);
-  return ListRef{pb, idx, reinterpret_cast<int*>(idx + 2 * n)};
+  return ListRef{pb, idx, reinterpret_cast<int*>(idx + kListVec * n)};
 }
 
 // Scans a query's list at its position p: the nearest listed target within r2
 // goes into nb (a first bound for a rebuild), and the result says whether the
 // list covers the query (see above).
-__device__ __forceinline__ bool list_scan(const GridView& g, float4 pb, int4 l0, int4 l1, float px, float py,
-                                          float pz, Nearest& nb) {
-  const int e[kList] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+__device__ __forceinline__ bool list_scan(const GridView& g, float4 pb, const int4 (&l)[kListVec], float px,
+                                          float py, float pz, Nearest& nb) {
+  int e[kList];
+#pragma unroll
+  for (int k = 0; k < kListVec; ++k) {
+    e[4 * k] = l[k].x;
+    e[4 * k + 1] = l[k].y;
+    e[4 * k + 2] = l[k].z;
+    e[4 * k + 3] = l[k].w;
+  }
   float4 q[kList];
 #pragma unroll
   for (int k = 0; k < kList; ++k) q[k] = e[k] >= 0 ? g.pts[e[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -267,8 +272,9 @@ __device__ __forceinline__ void list_store(const ListRef& L, int i, const ListSi
 #pragma unroll
   for (int k = 0; k < kList; ++k) e[k] = k < ls.m ? ls.p[k][threadIdx.x] : -1;
   L.pb[i] = make_float4(px, py, pz, ls.rho2());
-  L.idx[2 * i] = make_int4(e[0], e[1], e[2], e[3]);
-  L.idx[2 * i + 1] = make_int4(e[4], e[5], e[6], e[7]);
+#pragma unroll
+  for (int k = 0; k < kListVec; ++k)
+    L.idx[kListVec * i + k] = make_int4(e[4 * k], e[4 * k + 1], e[4 * k + 2], e[4 * k + 3]);
 }
 
 // Offers the sorted target positions [beg, end) to a sink, loading them
@@ -366,9 +372,6 @@ __device__ void box_search_global(const GridView& g, float cell, float px, float
 // nothing changed, when the staged set does not fit: the caller then searches
 // from global memory.  All threads of the block must call this.
 constexpr int kStageZ = 15;  // z-cells per column
-// A tile stages its search when more than this many of its queries are left
-// after the neighbour records.
-constexpr int kStagedMin = 0;
 
 // Two stage sizes, one per launch configuration.  Latency: every tile of a
 // launch is resident at once (5 blocks per SM), so a large stage keeps blocks
@@ -376,9 +379,11 @@ constexpr int kStagedMin = 0;
 // so a smaller stage and register budget buy 7 blocks per SM.
 struct CfgLatency {
   static constexpr int kPts = 1792, kCols = 128, kMinBlocks = 5;
+  static constexpr bool kLists = false;  // one wave of tiles: lists do not pay (see kListMinPoints)
 };
 struct CfgThroughput {
   static constexpr int kPts = 1024, kCols = 64, kMinBlocks = 7;
+  static constexpr bool kLists = true;
 };
 
 // The lists being rebuilt in a tile (see ListSink) take the last kListPts
@@ -388,6 +393,7 @@ constexpr int kListPts = kList * kThreads * 2 * 4 / 16;
 template <class Cfg>
 struct Stage {
   static constexpr int kStagePts = Cfg::kPts, kStageCols = Cfg::kCols;
+  static constexpr bool kLists = Cfg::kLists;
   float4 pts[kStagePts];
   uint32_t off[kStageCols][kStageZ + 1];  // global cell_start of each z-cell of each column
   uint32_t base[kStageCols + 1];          // staged position of each column's first staged point
@@ -414,47 +420,6 @@ __device__ __forceinline__ void column_range(const GridView& g, float cell, floa
   const float rz = __fadd_rn(fast_sqrt(lim), margin);
   zl = max(az, cell_coord(__fsub_rn(pz, rz), g.inv_cell) - g.lo_z);
   zh = min(bz, cell_coord(__fadd_rn(pz, rz), g.inv_cell) - g.lo_z);
-}
-
-// The exact search of one query from global memory with its memory accesses
-// batched: the columns of the box its bound allows are taken kBatchCols at a
-// time, each column's z-range from its slab gaps, the run bounds of the whole
-// batch are loaded together (independent loads), then the runs are scanned.
-// Every planned run is scanned, so the result is exact; a batch is planned with
-// the bound of the moment, which the scan can only tighten.  For queries
-// searched one per thread (the fallback pass), where a chain of dependent
-// per-column loads would set the time.
-constexpr int kBatchCols = 8;
-
-template <class Sink>
-__device__ void box_search_batched(const GridView& g, float cell, float px, float py, float pz, float R, Sink& sk) {
-  const float margin = search_margin(cell, R, px, py, pz);
-  const float reach = __fadd_rn(fast_sqrt(__fmul_rn(sk.bound(), 1.0001f)), margin);
-  int ax, bx, ay, by, az, bz;
-  axis_range(px, reach, g.inv_cell, g.lo_x, g.sx, ax, bx);
-  axis_range(py, reach, g.inv_cell, g.lo_y, g.sy, ay, by);
-  axis_range(pz, reach, g.inv_cell, g.lo_z, g.sz, az, bz);
-  if (ax > bx || ay > by || az > bz) return;
-  const int ny = by - ay + 1, ncol = (bx - ax + 1) * ny;
-  for (int c0 = 0; c0 < ncol; c0 += kBatchCols) {
-    const float bound = sk.bound();
-    uint32_t beg[kBatchCols], end[kBatchCols];
-#pragma unroll
-    for (int k = 0; k < kBatchCols; ++k) {
-      beg[k] = end[k] = 0u;
-      const int c = c0 + k;
-      if (c >= ncol) continue;
-      const int x = ax + c / ny, y = ay + c % ny;
-      int zl, zh;
-      column_range(g, cell, px, py, pz, margin, bound, x, y, az, bz, zl, zh);
-      if (zl > zh) continue;
-      const int col = (x * g.sy + y) * g.sz;
-      beg[k] = g.cell_start[col + zl];
-      end[k] = g.cell_start[col + zh + 1];
-    }
-#pragma unroll
-    for (int k = 0; k < kBatchCols; ++k) offer_run(g, beg[k], end[k], px, py, pz, sk);
-  }
 }
 
 template <class St, class Sink>
@@ -1138,12 +1103,13 @@ struct PairDesc {
   float ctr[3];        // point-to-point: reference point subtracted before the moments
   const float4* src4;  // cell-sorted source, .w = original index bits
   int ns;
-  int ntiles;          // ceil(ns / kThreads), at least 1
+  int ntiles;          // ceil(ns / (kThreads ppt)), at least 1
   int tile0;           // first global tile of this pair
   IcpState* st;
   unsigned long long* acc;  // nacc x kPartial fixed-point sums (see add_fixed), zero between launches
   int nacc;                 // accumulator rows: min(kAccRows, ntiles)
   float bnd_a, bnd_b;       // per-correspondence bounds the sums are scaled by (see set_sums)
+  int ppt;             // sub-tiles of kThreads points per tile (see icp_tile)
   ListRef lists;       // per source point last matches and candidate lists (see ListSink); pb null: none kept
   float list_motion;   // the pair keeps candidate lists once an update moves points by less (< 0: never)
   int32_t* corr_out;   // kCorrOnly / kEvaluate outputs (by original source index), or null
@@ -1398,33 +1364,19 @@ __device__ __forceinline__ void row_factors(const PairDesc& P, float3 p, int bp,
   }
 }
 
-// The queries an iteration launch leaves to the fallback pass (k_icp_fallback):
-// entry = (pair, source position, best d2 so far as bits, its sorted target
-// position or -1).  count[k & 1] / claim[k & 1] are the appended and claimed
-// entries of launch k of a sequence; launch k + 1 zeroes those of parity k & 1
-// (launch k's pass has ended by then).  items == null: no fallback pass, every
-// query is finished inside its tile.
-struct FallbackQueue {
-  int4* items = nullptr;
-  unsigned* count = nullptr;  // [2]
-  unsigned* claim = nullptr;  // [2]
-  int parity = 0;
-};
-
-// One tile (kThreads cell-sorted source points, tile j of pair P, which is
-// pair `pair` of the launch) of one ICP step.  mode kIterate: skipped once the
-// pair is done; the other modes always run.  kCorrOnly writes corr/d2 and no
-// sums.  Warm queries finish in the neighbour record of their best first
-// candidate; a tile with many queries left searches them block-staged, one with
-// few hands them to the fallback pass (or, without one, searches each from
-// global memory).  The tile's partial holds the rows of the queries it
-// finished; the last tile of the pair to arrive performs the pair's solve and
-// update (see finish) unless the fallback pass still has queries of the pair,
-// in which case the pass does.  Block-uniform control flow.
+// One tile of one ICP step: P.ppt sub-tiles of kThreads consecutive
+// cell-sorted source points each (tile j of pair P).  mode kIterate: skipped
+// once the pair is done; the other modes always run.  kCorrOnly writes
+// corr/d2 and no sums.  Each sub-tile's partial of every sum column is the
+// transposed compensated reduction of its rows; the tile's partial is the
+// compensated sum of its sub-tiles' partials in order, added once to the
+// pair's fixed-point accumulators; the last tile of the pair to arrive
+// performs the pair's solve and update (see finish).  Block-uniform control
+// flow.
 template <bool F64, class St>
-__device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage, int pair, const FallbackQueue& fq) {
-  // every load the tile starts with (the stop flag, the pose, the source point
-  // and its hint) is issued before any of them is used: one memory round trip
+__device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
+  // the state the tile starts with (the stop flag, the list mode, the pose) is
+  // loaded together with the first sub-tile's points: one memory round trip
   const int done = P.st->done;
   const int lists_on = P.st->lists_on;
   float R[9], t[3];
@@ -1432,134 +1384,112 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage, int pair
   for (int k = 0; k < 9; ++k) R[k] = P.st->R[k];
 #pragma unroll
   for (int k = 0; k < 3; ++k) t[k] = P.st->t[k];
-  const int i = j * kThreads + threadIdx.x;
-  const bool live = i < P.ns;
   const bool keep = P.lists.pb != nullptr;  // matches (and lists) are kept across launches
-  const float4 s = live ? P.src4[i] : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
-  const int hint = (keep && live) ? P.lists.hint[i] : -1;
-  float4 pb = make_float4(0.f, 0.f, 0.f, -1.f);
-  int4 l0 = make_int4(-1, -1, -1, -1), l1 = l0;
-  if (keep && live && lists_on) {
-    pb = P.lists.pb[i];
-    l0 = P.lists.idx[2 * i];
-    l1 = P.lists.idx[2 * i + 1];
-  }
-  if (mode == kIterate && done) return;
-  const bool lists = keep && lists_on && P.kind == kPointToPlane;
+  // (a launch form without list support searches every point: the same
+  // correspondences and the same sums, only slower)
+  const bool lists = St::kLists && keep && lists_on && P.kind == kPointToPlane;
   const float r2 = __fmul_rn(P.r, P.r);
   const float sigma = __fmul_rn(P.r, kSkin), Rl = __fadd_rn(P.r, sigma);
-  const float3 p = live ? xform_rn(R, t, s.x, s.y, s.z) : make_float3(3.0e38f, 3.0e38f, 3.0e38f);
-  // Once the pair keeps lists, a point whose list still covers it is decided by
-  // the list alone; the others search the grid from their last match (and
-  // rebuild their lists).  Before that, every point searches from the last
-  // matches of itself and its warp neighbours.  Searches run block-staged while
-  // many of the tile's points need one, else in the fallback pass (or, without
-  // one, each from global memory).
-  Nearest nb{r2, 0x7fffffff, -1};
-  bool need = live;
-  if (lists) {
-    need = live && !list_scan(P.g, pb, l0, l1, p.x, p.y, p.z, nb);
-    if (need && hint >= 0) consider(nb, P.g.pts[hint], hint, p.x, p.y, p.z);
-  } else {
-    first_bound(P.g, p.x, p.y, p.z, hint, nb);
-  }
   // the lists being rebuilt (see ListSink) in the stage's last kListPts points
   float(*const s_ld)[kThreads] = reinterpret_cast<float(*)[kThreads]>(&stage.pts[St::kStagePts - kListPts]);
   int(*const s_lp)[kThreads] = reinterpret_cast<int(*)[kThreads]>(&s_ld[kList][0]);
-  const int n_need = __syncthreads_count(need);
-  bool queued = false;
-  if (n_need > kStagedMin) {
+  float tile_s = 0.f, tile_c = 0.f;  // the tile's partial (threads < kPartial)
+  double tile_f64 = 0.0;
+  for (int sub = 0; sub < P.ppt; ++sub) {
+    const int i = (j * P.ppt + sub) * kThreads + threadIdx.x;
+    const bool live = i < P.ns;
+    const float4 s = live ? P.src4[i] : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
+    // the last match seeds the search (before lists, every point searches; with
+    // lists, only the points their lists no longer cover, which read it later)
+    int hint = (keep && live && !lists_on) ? P.lists.hint[i] : -1;
+    float4 pb = make_float4(0.f, 0.f, 0.f, -1.f);
+    int4 l[kListVec];
+#pragma unroll
+    for (int k = 0; k < kListVec; ++k) l[k] = make_int4(-1, -1, -1, -1);
+    if (lists && live) {
+      pb = P.lists.pb[i];
+#pragma unroll
+      for (int k = 0; k < kListVec; ++k) l[k] = P.lists.idx[kListVec * i + k];
+    }
+    if (mode == kIterate && done) return;
+    const float3 p = live ? xform_rn(R, t, s.x, s.y, s.z) : make_float3(3.0e38f, 3.0e38f, 3.0e38f);
+    // Once the pair keeps lists, a point whose list still covers it is decided
+    // by the list alone; the others search the grid from their last match (and
+    // rebuild their lists).  Before that, every point searches from the last
+    // matches of itself and its warp neighbours.  The searches of a sub-tile run
+    // block-staged in shared memory (each from global memory when the staged
+    // set does not fit).
+    Nearest nb{r2, 0x7fffffff, -1};
+    bool need = live;
     if (lists) {
-      ListSink ls{nb, s_ld, s_lp, list_lim(nb.d2, sigma), 0, 0.f, 0};
-      if (!staged_search(P.g, P.cell, p.x, p.y, p.z, Rl, need, ls, stage, St::kStagePts - kListPts) && need)
-        box_search_global(P.g, P.cell, p.x, p.y, p.z, Rl, ls);
-      if (need) list_store(P.lists, i, ls, p.x, p.y, p.z);
-      nb = ls.nb;
+      need = live && !list_scan(P.g, pb, l, p.x, p.y, p.z, nb);
+      if (need) {
+        hint = P.lists.hint[i];
+        if (hint >= 0) consider(nb, P.g.pts[hint], hint, p.x, p.y, p.z);
+      }
     } else {
-      NnSink ns{nb};
-      if (!staged_search(P.g, P.cell, p.x, p.y, p.z, P.r, need, ns, stage) && need)
-        box_search_global(P.g, P.cell, p.x, p.y, p.z, P.r, ns);
-      nb = ns.nb;
+      first_bound(P.g, p.x, p.y, p.z, hint, nb);
     }
-  } else if (n_need > 0 && fq.items) {
-    // append this tile's remaining points (in lane order) to the fallback queue
-    __shared__ unsigned s_wcnt[kThreads / 32], s_qbase;
-    const unsigned bal = __ballot_sync(0xffffffffu, need);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_wcnt[warp] = __popc(bal);
-    if (threadIdx.x == 0) s_qbase = atomicAdd(&fq.count[fq.parity], static_cast<unsigned>(n_need));
-    __syncthreads();
-    if (need) {
-      unsigned off = s_qbase + __popc(bal & ((1u << lane) - 1u));
-      for (int w = 0; w < warp; ++w) off += s_wcnt[w];
-      fq.items[off] = make_int4(pair, i, 0, 0);
+    if (__syncthreads_or(need)) {
+      if (lists) {
+        ListSink ls{nb, s_ld, s_lp, list_lim(nb.d2, sigma), 0, 0.f, 0};
+        if (!staged_search(P.g, P.cell, p.x, p.y, p.z, Rl, need, ls, stage, St::kStagePts - kListPts) && need)
+          box_search_global(P.g, P.cell, p.x, p.y, p.z, Rl, ls);
+        if (need) list_store(P.lists, i, ls, p.x, p.y, p.z);
+        nb = ls.nb;
+      } else {
+        NnSink ns{nb};
+        if (!staged_search(P.g, P.cell, p.x, p.y, p.z, P.r, need, ns, stage) && need)
+          box_search_global(P.g, P.cell, p.x, p.y, p.z, P.r, ns);
+        nb = ns.nb;
+      }
     }
-    queued = need;
-  } else if (need) {
-    if (lists) {
-      ListSink ls{nb, s_ld, s_lp, list_lim(nb.d2, sigma), 0, 0.f, 0};
-      box_search_global(P.g, P.cell, p.x, p.y, p.z, Rl, ls);
-      list_store(P.lists, i, ls, p.x, p.y, p.z);
-      nb = ls.nb;
+    const float bd2 = nb.d2;
+    const int bp = live ? nb.pos : -1;
+    if (keep && live && (!lists || need)) P.lists.hint[i] = bp;
+    if (live && P.corr_out) {  // kCorrOnly, or a final evaluation that reports its correspondence set
+      const int o = __float_as_int(s.w);
+      P.corr_out[o] = bp >= 0 ? __float_as_int(P.g.pts[bp].w) : -1;
+      P.d2_out[o] = bp >= 0 ? bd2 : 0.f;
+    }
+    if (mode == kCorrOnly) continue;
+    if constexpr (F64) {
+      double v[32];
+      f64_terms(P, p, bp, bd2, v);
+      double col = 0.0;
+      block_reduce_f64(v, col);
+      if (threadIdx.x < kPartial) tile_f64 += col;
+      __syncthreads();  // the reduction's shared words are free again
     } else {
-      NnSink ns{nb};
-      box_search_global(P.g, P.cell, p.x, p.y, p.z, P.r, ns);
-      nb = ns.nb;
+      // per-correspondence factors as one row per thread in shared memory (the
+      // staged points are no longer needed), then the transposed reduction
+      __syncthreads();  // every thread has finished reading the staged points
+      float* rows = reinterpret_cast<float*>(stage.pts);
+      float* row = rows + threadIdx.x * kRow;
+      row_factors(P, p, bp, bd2, [&](int k) -> float& { return row[k]; });
+      __syncthreads();
+      float ts = 0.f, tc = 0.f;
+      block_reduce_rows(rows, P.kind, ts, tc);
+      if (threadIdx.x < kPartial) add_pair(tile_s, tile_c, ts, tc);
     }
-  }
-  const float bd2 = nb.d2;
-  const int bp = (live && !queued) ? nb.pos : -1;
-  if (keep && live && !queued) P.lists.hint[i] = bp;
-  if (live && !queued && P.corr_out) {  // kCorrOnly, or a final evaluation that reports its correspondence set
-    const int o = __float_as_int(s.w);
-    P.corr_out[o] = bp >= 0 ? __float_as_int(P.g.pts[bp].w) : -1;
-    P.d2_out[o] = bp >= 0 ? bd2 : 0.f;
   }
   if (mode == kCorrOnly) return;
-  const int n_queued = fq.items && n_need <= kStagedMin ? n_need : 0;
   // this tile's partial of every sum goes to accumulator row j % nacc, scaled by
   // the bounds (nlen: the target normals' length bound)
   unsigned long long* const acc = P.acc + static_cast<size_t>(j % P.nacc) * kPartial;
   const float nlen = (P.kind == kPointToPlane && P.g.nrm) ? P.g.nrm[P.g.n].x : 0.f;
-  int E = 0;
   if (threadIdx.x < kPartial) {
-    E = sum_exponent(P, threadIdx.x, nlen);
-    if (n_queued) P.st->E[threadIdx.x] = E;  // for the fallback pass (every tile writes the same values)
+    const int E = sum_exponent(P, threadIdx.x, nlen);
+    if constexpr (F64) add_fixed_f64(acc, threadIdx.x, tile_f64, E);
+    else add_fixed(acc, threadIdx.x, tile_s, tile_c, E);
   }
-  if constexpr (F64) {
-    double v[32];
-    f64_terms(P, p, bp, bd2, v);
-    double col = 0.0;
-    block_reduce_f64(v, col);
-    if (threadIdx.x < kPartial) add_fixed_f64(acc, threadIdx.x, col, E);
-  } else {
-    // per-correspondence factors as one row per thread in shared memory (the
-    // staged points are no longer needed), then the transposed reduction
-    __syncthreads();  // every thread has finished reading the staged points
-    float* rows = reinterpret_cast<float*>(stage.pts);
-    float* row = rows + threadIdx.x * kRow;
-    row_factors(P, p, bp, bd2, [&](int k) -> float& { return row[k]; });
-    __syncthreads();
-    float ts = 0.f, tc = 0.f;
-    block_reduce_rows(rows, P.kind, ts, tc);
-    if (threadIdx.x < kPartial) add_fixed(acc, threadIdx.x, ts, tc, E);
-  }
-  // the last tile of the pair to arrive finishes the launch for the pair, unless
-  // queries of the pair wait in the fallback pass
+  // the last tile of the pair to arrive finishes the launch for the pair
   __shared__ bool last;
   if (threadIdx.x < kPartial) __threadfence();  // the lanes that added the partial publish it
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (n_queued) {
-      atomicAdd(&P.st->pending, static_cast<unsigned>(n_queued));
-      __threadfence();
-    }
     last = atomicAdd(&P.st->arrived, 1u) == static_cast<unsigned>(P.ntiles - 1);
-    if (last) {
-      __threadfence();
-      P.st->arrived = 0u;  // ready for the next launch
-      last = atomicAdd(&P.st->pending, 0u) == 0u;
-    }
+    if (last) P.st->arrived = 0u;  // ready for the next launch
   }
   __syncthreads();
   if (!last) return;
@@ -1578,8 +1508,7 @@ template <bool F64, class Cfg>
 __global__ void __launch_bounds__(kThreads, Cfg::kMinBlocks) k_icp_iter(PairDesc one, const PairDesc* __restrict__ pairs,
                                                                      const int* __restrict__ tile_pair,
                                                                      const int* __restrict__ ntiles_total, int mode,
-                                                                     unsigned* __restrict__ queue, int parity,
-                                                                     FallbackQueue fq) {
+                                                                     unsigned* __restrict__ queue, int parity) {
   __shared__ Stage<Cfg> stage;
   __shared__ PairDesc P;
   __shared__ int s_next;
@@ -1597,10 +1526,6 @@ __global__ void __launch_bounds__(kThreads, Cfg::kMinBlocks) k_icp_iter(PairDesc
   // partial).  queue[parity ^ 1] is the counter of the next launch on
   // this queue; the previous launch, which used it, has finished here.
   if (queue && blockIdx.x == 0 && threadIdx.x == 0) queue[parity ^ 1] = 0u;
-  if (fq.items && blockIdx.x == 0 && threadIdx.x == 0) {
-    fq.count[fq.parity ^ 1] = 0u;
-    fq.claim[fq.parity ^ 1] = 0u;
-  }
   __shared__ int s_pair;
   int tile = blockIdx.x;
   while (tile < n) {
@@ -1609,173 +1534,11 @@ __global__ void __launch_bounds__(kThreads, Cfg::kMinBlocks) k_icp_iter(PairDesc
       P = pairs ? pairs[s_pair] : one;
     }
     __syncthreads();
-    icp_tile<F64>(P, tile - P.tile0, mode, stage, s_pair, fq);
+    icp_tile<F64>(P, tile - P.tile0, mode, stage);
     if (threadIdx.x == 0)
       s_next = queue ? static_cast<int>(gridDim.x + atomicAdd(&queue[parity], 1u)) : tile + static_cast<int>(gridDim.x);
     __syncthreads();
     tile = s_next;
-  }
-}
-
-// The fallback pass of an iteration launch: the queries its tiles left (see
-// icp_tile), searched one per thread from global memory in dense blocks, the
-// search continuing from the best candidate the tile found.  Each query's terms
-// enter the sums as 64-bit fixed point in the units of their columns (those of
-// the tiles' partials): a warp whose queries belong to one pair first adds
-// them exactly by integer shuffles.  Integer sums do not depend on which block
-// or warp adds a query, nor on the order of the queue.  The warp that adds a
-// pair's last pending query marks the pair, and the block then finishes the
-// pair's launch (solve and update, or the stored results).
-template <bool F64>
-__global__ void __launch_bounds__(kThreads) k_icp_fallback(PairDesc one, const PairDesc* __restrict__ pairs, int mode,
-                                                           FallbackQueue fq) {
-  // launched as a programmatic dependent of the iteration launch whose queue it
-  // drains: wait for that grid's completion, then let the next launch place
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  const unsigned full = 0xffffffffu;
-  const unsigned total = *reinterpret_cast<volatile unsigned*>(&fq.count[fq.parity]);
-  __shared__ unsigned s_base;
-  __shared__ int s_fin[kThreads];  // pair whose last pending query this lane added, or -1
-  __shared__ float s_rows[kThreads][kRow + 1];
-  __shared__ float s_ld[kList][kThreads];  // the lists being rebuilt (see ListSink)
-  __shared__ int s_lp[kList][kThreads];
-  __shared__ PairDesc s_P;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (;;) {
-    if (threadIdx.x == 0) s_base = atomicAdd(&fq.claim[fq.parity], static_cast<unsigned>(kThreads));
-    s_fin[threadIdx.x] = -1;
-    __syncthreads();
-    const unsigned base = s_base;
-    __syncthreads();
-    if (base >= total) break;
-    const unsigned e = base + threadIdx.x;
-    const bool live = e < total;
-    const int4 item = live ? fq.items[e] : make_int4(0, 0, 0, -1);
-    const bool warp_live = __any_sync(full, live);
-    // lanes past the end take lane 0's pair (lane 0 is live whenever any lane is);
-    // every lane takes part in the shuffle
-    const int pair0 = __shfl_sync(full, item.x, 0);
-    const int pair = live ? item.x : pair0;
-    const PairDesc& P = pairs ? pairs[pair] : one;
-    int bp = -1;
-    float bd2 = 0.f;
-    float3 p = make_float3(0.f, 0.f, 0.f);
-    if (live) {
-      const IcpState* st = P.st;
-      float R[9], t[3];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) R[k] = st->R[k];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) t[k] = st->t[k];
-      const int i = item.y;
-      const float4 sp = P.src4[i];
-      p = xform_rn(R, t, sp.x, sp.y, sp.z);
-      Nearest nb{__fmul_rn(P.r, P.r), 0x7fffffff, -1};
-      const int hint = P.lists.pb ? P.lists.hint[i] : -1;
-      if (hint >= 0) consider(nb, P.g.pts[hint], hint, p.x, p.y, p.z);
-      if (P.lists.pb && st->lists_on && P.kind == kPointToPlane) {
-        // the point's old list bounds the rebuild; the search rebuilds it
-        const float sigma = __fmul_rn(P.r, kSkin), Rl = __fadd_rn(P.r, sigma);
-        (void)list_scan(P.g, P.lists.pb[i], P.lists.idx[2 * i], P.lists.idx[2 * i + 1], p.x, p.y, p.z, nb);
-        ListSink ls{nb, s_ld, s_lp, list_lim(nb.d2, sigma), 0, 0.f, 0};
-        box_search_batched(P.g, P.cell, p.x, p.y, p.z, Rl, ls);
-        list_store(P.lists, i, ls, p.x, p.y, p.z);
-        nb = ls.nb;
-      } else {
-        NnSink ns{nb};
-        box_search_batched(P.g, P.cell, p.x, p.y, p.z, P.r, ns);
-        nb = ns.nb;
-      }
-      bp = nb.pos;
-      bd2 = nb.d2;
-      if (P.lists.pb) P.lists.hint[i] = bp;
-      if (P.corr_out) {
-        const int o = __float_as_int(sp.w);
-        P.corr_out[o] = bp >= 0 ? __float_as_int(P.g.pts[bp].w) : -1;
-        P.d2_out[o] = bp >= 0 ? bd2 : 0.f;
-      }
-    }
-    if (mode != kCorrOnly && warp_live) {
-      // this query's value of every sum column as a fixed-point integer
-      long long v[32];
-      bool bad = false;
-      if constexpr (F64) {
-        double d[32];
-        f64_terms(P, p, bp, bd2, d);
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const int E = live ? P.st->E[k] : 0;
-          const double h = d[k] * __longlong_as_double(static_cast<long long>(1023 - E) << 52);  // exact
-          const bool ok = (__double_as_longlong(h) & 0x7fffffffffffffffLL) < 0x43D0000000000000LL;  // |h| < 2^62
-          bad |= !ok;
-          v[k] = ok ? __double2ll_rn(h) : 0;
-        }
-      } else {
-        float* row = s_rows[threadIdx.x];
-        row_factors(P, p, bp, bd2, [&](int k) -> float& { return row[k]; });
-        row[kRow] = 0.f;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const uchar4 ix = *reinterpret_cast<const uchar4*>(kTerm[P.kind][k]);
-          const float x = row[ix.x], y = row[ix.y], xl = row[ix.z], yl = row[ix.w];
-          const float hi = __fmul_rn(x, y);
-          const float lo = fmaf(x, y, -hi) + fmaf(x, yl, xl * y);  // exact for point-to-plane (lows are 0)
-          const int E = live ? P.st->E[k] : 0;
-          const float sc = __int_as_float((127 - E) << 23);  // 2^-E
-          const float hs = hi * sc, ls = lo * sc;
-          const bool ok = fabsf(hs) < 0x1p62f && fabsf(ls) < 0x1p62f;
-          bad |= !ok;
-          v[k] = ok ? __float2ll_rn(hs) + __float2ll_rn(ls) : 0;
-        }
-      }
-      v[kBadCol] = bad ? 1 : 0;
-      if (!live) {
-#pragma unroll
-        for (int k = 0; k < 32; ++k) v[k] = 0;
-      }
-      const int row = (blockIdx.x * (kThreads / 32) + warp) % P.nacc;
-      unsigned long long* const acc = P.acc + static_cast<size_t>(row) * kPartial;
-      const unsigned live_mask = __ballot_sync(full, live);
-      if (__match_any_sync(full, pair) == full) {
-        // one pair: butterfly reduce-scatter, column `lane` ends on lane `lane`
-#pragma unroll
-        for (int half = 16; half >= 1; half >>= 1) {
-          const bool upper = (lane & half) != 0;
-#pragma unroll
-          for (int j = 0; j < half; ++j) {
-            const long long send = upper ? v[j] : v[j + half];
-            const long long keep = upper ? v[j + half] : v[j];
-            v[j] = keep + __shfl_xor_sync(full, send, half);
-          }
-        }
-        if (v[0] != 0) atomicAdd(acc + lane, static_cast<unsigned long long>(v[0]));
-        __threadfence();
-        __syncwarp();
-        if (lane == 0 && mode != kCorrOnly) {
-          const unsigned n = static_cast<unsigned>(__popc(live_mask));
-          if (atomicSub(&P.st->pending, n) == n) s_fin[threadIdx.x] = pair;
-        }
-      } else if (live) {
-#pragma unroll
-        for (int k = 0; k < 32; ++k)
-          if (v[k] != 0) atomicAdd(acc + k, static_cast<unsigned long long>(v[k]));
-        __threadfence();
-        if (atomicSub(&P.st->pending, 1u) == 1u) s_fin[threadIdx.x] = pair;
-      }
-    }
-    __syncthreads();
-    // finish every pair whose last pending query this block added
-    for (int t = 0; t < kThreads; ++t) {
-      const int fin = s_fin[t];  // block-uniform
-      if (fin < 0) continue;
-      if (threadIdx.x == 0) s_P = pairs ? pairs[fin] : one;
-      __syncthreads();
-      __threadfence();
-      const float nlen = (s_P.kind == kPointToPlane && s_P.g.nrm) ? s_P.g.nrm[s_P.g.n].x : 0.f;
-      finish(s_P, mode, nlen);
-      __syncthreads();
-    }
   }
 }
 
@@ -1827,10 +1590,10 @@ struct TileQueue {
 
 template <bool F64, class Cfg>
 void launch_form(int ntiles, const PairDesc& one, const PairDesc* pairs, const int* tile_pair, const int* d_ntiles,
-                 int mode, cudaStream_t s, bool dependent, TileQueue q, const FallbackQueue& fq) {
+                 int mode, cudaStream_t s, bool dependent, TileQueue q) {
   const int grid = grid_for(ntiles, resident_blocks<F64, Cfg>());
   if (!dependent) {
-    k_icp_iter<F64, Cfg><<<grid, kThreads, 0, s>>>(one, pairs, tile_pair, d_ntiles, mode, q.counters, q.parity, fq);
+    k_icp_iter<F64, Cfg><<<grid, kThreads, 0, s>>>(one, pairs, tile_pair, d_ntiles, mode, q.counters, q.parity);
     return;
   }
   // programmatic dependent launch: the grid is placed while the previous
@@ -1844,67 +1607,43 @@ void launch_form(int ntiles, const PairDesc& one, const PairDesc* pairs, const i
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, k_icp_iter<F64, Cfg>, one, pairs, tile_pair, d_ntiles, mode, q.counters, q.parity,
-                         fq) != cudaSuccess) {
+  if (cudaLaunchKernelEx(&cfg, k_icp_iter<F64, Cfg>, one, pairs, tile_pair, d_ntiles, mode, q.counters, q.parity) !=
+      cudaSuccess) {
     (void)cudaGetLastError();
-    k_icp_iter<F64, Cfg><<<grid, kThreads, 0, s>>>(one, pairs, tile_pair, d_ntiles, mode, q.counters, q.parity, fq);
+    k_icp_iter<F64, Cfg><<<grid, kThreads, 0, s>>>(one, pairs, tile_pair, d_ntiles, mode, q.counters, q.parity);
   }
 }
 
-// Blocks of the fallback pass resident on the GPU together (computed once).
-template <bool F64>
-int fallback_blocks() {
-  static const int resident = [] {
-    int dev = 0, sms = kNumSMs, per_sm = 1;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_icp_fallback<F64>, kThreads, 0) != cudaSuccess ||
-        per_sm < 1)
-      per_sm = 1;
-    (void)cudaGetLastError();
-    return sms * per_sm;
-  }();
-  return resident;
-}
-
-// The fallback pass after an iteration launch over `ntiles` tiles (at most
-// kStagedMin queued queries each), as a programmatic dependent when `pdl`.
-template <bool F64>
-void launch_fallback(int ntiles, const PairDesc& one, const PairDesc* pairs, int mode, cudaStream_t s, bool pdl,
-                     const FallbackQueue& fq) {
-  const int64_t cap = static_cast<int64_t>(ntiles) * kStagedMin;
-  const int grid = static_cast<int>(std::min<int64_t>(fallback_blocks<F64>(), (cap + kThreads - 1) / kThreads));
-  if (pdl) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid < 1 ? 1 : grid);
-    cfg.blockDim = dim3(kThreads);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, k_icp_fallback<F64>, one, pairs, mode, fq) == cudaSuccess) return;
-    (void)cudaGetLastError();
-  }
-  k_icp_fallback<F64><<<grid < 1 ? 1 : grid, kThreads, 0, s>>>(one, pairs, mode, fq);
-}
-
-// One launch of the iteration kernel over `ntiles` work items on stream s, and
-// its fallback pass when fq has a queue; `dependent`: the iteration launch as a
-// programmatic dependent of the preceding kernel of s; `pdl`: the pass as one
-// of the iteration launch.
+// One launch of the iteration kernel over `ntiles` work items on stream s;
+// `dependent`: as a programmatic dependent of the preceding kernel of s.
 void launch_iter(bool f64, int ntiles, const PairDesc& one, const PairDesc* pairs, const int* tile_pair,
-                 const int* d_ntiles, int mode, cudaStream_t s, bool dependent = false, TileQueue q = TileQueue{},
-                 const FallbackQueue& fq = FallbackQueue{}, bool pdl = true) {
-  if (f64) launch_form<true, CfgLatency>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent, q, fq);
+                 const int* d_ntiles, int mode, cudaStream_t s, bool dependent = false, TileQueue q = TileQueue{}) {
+  if (f64) launch_form<true, CfgLatency>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent, q);
   else if (throughput_form(ntiles))
-    launch_form<false, CfgThroughput>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent, q, fq);
-  else launch_form<false, CfgLatency>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent, q, fq);
-  if (fq.items && kStagedMin > 0) {
-    if (f64) launch_fallback<true>(ntiles, one, pairs, mode, s, pdl, fq);
-    else launch_fallback<false>(ntiles, one, pairs, mode, s, pdl, fq);
-    count_launch();
-  }
+    launch_form<false, CfgThroughput>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent, q);
+  else launch_form<false, CfgLatency>(ntiles, one, pairs, tile_pair, d_ntiles, mode, s, dependent, q);
+}
+
+// Sub-tiles per tile (points per thread) of a pair of ns source points, per
+// size class of the pair (floor(log2(ns))): 0 automatic (kAutoPpt), else 1, 2
+// or 4.  A property of the pair, so that it tiles the same way alone, in a
+// batch and in the server.
+std::atomic<int> g_ppt[32];
+int pair_ppt(int64_t ns) {
+  int c = 0;
+  while (c < 31 && (2LL << c) <= ns) ++c;
+  const int pin = g_ppt[c].load(std::memory_order_relaxed);
+  if (pin == 1 || pin == 2 || pin == 4) return pin;
+  // automatic: measured on a 94,829-point pair (one wave of tiles: 1 best) and
+  // a 2,000,000-point pair (4 best, 2 between)
+  return ns >= (1 << 20) ? 4 : (ns >= (1 << 18) ? 2 : 1);
+}
+
+// Tiles of a pair of ns points with ppt sub-tiles of kThreads points each.
+inline int pair_tiles(int64_t ns, int ppt) {
+  const int64_t per = static_cast<int64_t>(kThreads) * ppt;
+  const int64_t b = (ns + per - 1) / per;
+  return static_cast<int>(b < 1 ? 1 : b);
 }
 
 inline int iter_blocks(int64_t ns) {
@@ -1969,11 +1708,11 @@ struct Work {
   DevBuf state;
   DevBuf acc;    // accum_rows(nblk) x kPartial fixed-point sums
   DevBuf lists;  // per source point candidate lists (see ListSink): ns float4, then 2 ns int4
-  DevBuf queue;  // the dynamic tile queue (2 counters), then the fallback queue's counters (4)
-  DevBuf fq_items;  // the fallback queue (nblk x kStagedMin entries)
+  DevBuf queue;  // the dynamic tile queue (2 counters)
   int nblk = 1;
+  int ppt = 1;
   int launches = 0;  // launches so far (the queue parity)
-  explicit Work(cudaStream_t s) : src(s), state(s), acc(s), lists(s), queue(s), fq_items(s) {}
+  explicit Work(cudaStream_t s) : src(s), state(s), acc(s), lists(s), queue(s) {}
   int32_t prepare(const float* d_src, int64_t ns, int32_t stride, float cell, const double* T, cudaStream_t s,
                   const SortedCloud* pre = nullptr) {
     if (pre) {
@@ -1984,14 +1723,14 @@ struct Work {
       pts = src.pts;
       aux = src.aux.as<int>();
     }
-    nblk = iter_blocks(ns);
+    ppt = pair_ppt(ns);
+    nblk = pair_tiles(ns, ppt);
     O3G_TRY(state.alloc(sizeof(IcpState)));
     const size_t acc_bytes = sizeof(unsigned long long) * kPartial * accum_rows(nblk);
     O3G_TRY(acc.alloc(acc_bytes));
     O3G_TRY(cudaMemsetAsync(acc.p, 0, acc_bytes, s));
-    O3G_TRY(queue.alloc(sizeof(unsigned) * 6));
-    O3G_TRY(cudaMemsetAsync(queue.p, 0, sizeof(unsigned) * 6, s));
-    O3G_TRY(fq_items.alloc(sizeof(int4) * static_cast<size_t>(nblk) * kStagedMin));
+    O3G_TRY(queue.alloc(sizeof(unsigned) * 2));
+    O3G_TRY(cudaMemsetAsync(queue.p, 0, sizeof(unsigned) * 2, s));
     O3G_TRY(lists.alloc(kListBytes * (ns > 0 ? ns : 1)));
     O3G_TRY(cudaMemsetAsync(lists.p, 0xff, kListBytes * (ns > 0 ? ns : 1), s));  // no lists yet
     k_init_state<<<1, 32, 0, s>>>(state.as<IcpState>(), to_pose(T));
@@ -2014,6 +1753,7 @@ struct Work {
     P.src4 = pts;
     P.ns = ns;
     P.ntiles = nblk;
+    P.ppt = ppt;
     P.tile0 = 0;
     P.st = state.as<IcpState>();
     set_sums(P, g, acc.as<unsigned long long>());
@@ -2021,13 +1761,8 @@ struct Work {
     P.list_motion = list_motion(ns, r);
     P.corr_out = corr;
     P.d2_out = d2;
-    FallbackQueue fq;
-    fq.items = fq_items.as<int4>();
-    fq.count = queue.as<unsigned>() + 2;
-    fq.claim = queue.as<unsigned>() + 4;
-    fq.parity = launches & 1;
     launch_iter(f64, nblk, P, nullptr, nullptr, nullptr, mode, s, dependent,
-                TileQueue{queue.as<unsigned>(), launches & 1}, fq);
+                TileQueue{queue.as<unsigned>(), launches & 1});
     ++launches;
     count_launch();
     return O3G_OK;
@@ -2343,6 +2078,7 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const 
     P.src4 = src4;
     P.ns = n;
     P.ntiles = nblk;
+    P.ppt = 1;
     P.tile0 = 0;
     P.st = st;
     set_sums(P, g, acc);
@@ -2407,18 +2143,12 @@ cudaError_t graph_stream(cudaStream_t* out) {
 // Launches `iters` iteration steps and one evaluation step of the batch on s,
 // through a captured CUDA graph when capture works, else directly.
 int32_t run_iterations(const PairDesc* descs, const int* tile_pair, const int* d_ntiles, int ntiles, int max_iter,
-                       double eps, unsigned* queue, int4* fq_items, cudaStream_t s) {
+                       double eps, unsigned* queue, cudaStream_t s) {
   PairDesc dummy{};
   auto enqueue = [&](cudaStream_t q) {
-    for (int it = 0; it <= max_iter; ++it) {
-      FallbackQueue fq;
-      fq.items = fq_items;
-      fq.count = queue + 2;
-      fq.claim = queue + 4;
-      fq.parity = it & 1;
+    for (int it = 0; it <= max_iter; ++it)
       launch_iter(false, ntiles, dummy, descs, tile_pair, d_ntiles, it < max_iter ? kIterate : kEvaluate, q, false,
-                  TileQueue{queue, it & 1}, fq, false);
-    }
+                  TileQueue{queue, it & 1});
   };
   cudaStream_t cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -2445,7 +2175,7 @@ int32_t run_iterations(const PairDesc* descs, const int* tile_pair, const int* d
     (void)cudaGetLastError();
     enqueue(s);  // capture unavailable: plain launches, same work
   }
-  count_launch(max_iter + 1);  // the iteration launches (launch_iter counts the fallback passes)
+  count_launch(max_iter + 1);
   O3G_TRY(cudaGetLastError());
   return O3G_OK;
 }
@@ -2484,7 +2214,7 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   }
   if (n_pairs == 0) return O3G_OK;
   std::vector<int64_t> off(n_pairs + 1, 0);
-  std::vector<int> ntiles(n_pairs);
+  std::vector<int> ntiles(n_pairs), ppts(n_pairs);
   int64_t tiles_total = 0, rows_total = 0;
   for (int p = 0; p < n_pairs; ++p) {
     if (!tgts[p] || !tgts[p]->has_normals || !(max_corr_dist[p] >= 0.0) || !std::isfinite(max_corr_dist[p])) {
@@ -2497,7 +2227,8 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
       return O3G_ERR_NONFINITE;
     }
     off[p + 1] = off[p] + ns[p];
-    ntiles[p] = iter_blocks(ns[p]);
+    ppts[p] = pair_ppt(ns[p]);
+    ntiles[p] = pair_tiles(ns[p], ppts[p]);
     tiles_total += ntiles[p];
     rows_total += accum_rows(ntiles[p]);
   }
@@ -2507,7 +2238,6 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t total = off[n_pairs];
-  DevBuf d_fq(s);
   DevBuf d_ptrs(s), d_strides(s), d_off(s), d_src4(s), d_aux(s), d_states(s), d_acc(s), d_cnt(s), d_lists(s),
       d_descs(s), d_tiles(s), d_poses(s);
   O3G_TRY(d_ptrs.alloc(sizeof(float*) * n_pairs));
@@ -2517,8 +2247,7 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   O3G_TRY(d_aux.alloc(sizeof(int) * 8 * n_pairs));
   O3G_TRY(d_states.alloc(sizeof(IcpState) * n_pairs));
   O3G_TRY(d_acc.alloc(sizeof(unsigned long long) * kPartial * rows_total));
-  O3G_TRY(d_cnt.alloc(sizeof(unsigned) * 6));  // the tile queue, then the fallback queue's counters
-  O3G_TRY(d_fq.alloc(sizeof(int4) * static_cast<size_t>(tiles_total) * kStagedMin));
+  O3G_TRY(d_cnt.alloc(sizeof(unsigned) * 2));  // the tile queue
   O3G_TRY(d_lists.alloc(kListBytes * (total > 0 ? total : 1)));
   O3G_TRY(d_descs.alloc(sizeof(PairDesc) * n_pairs));
   O3G_TRY(d_tiles.alloc(sizeof(int) * (tiles_total + 1)));
@@ -2541,6 +2270,7 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
     P.src4 = d_src4.as<float4>() + off[p];
     P.ns = static_cast<int>(ns[p]);
     P.ntiles = ntiles[p];
+    P.ppt = ppts[p];
     P.tile0 = static_cast<int>(t0);
     P.st = states + p;
     set_sums(P, tgts[p], acc + static_cast<size_t>(kPartial) * a0);
@@ -2560,7 +2290,7 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   O3G_TRY(cudaMemcpyAsync(d_descs.p, descs.data(), sizeof(PairDesc) * n_pairs, cudaMemcpyHostToDevice, s));
   O3G_TRY(cudaMemcpyAsync(d_tiles.p, tile_pair.data(), sizeof(int) * (tiles_total + 1), cudaMemcpyHostToDevice, s));
   O3G_TRY(cudaMemcpyAsync(d_poses.p, init_T, sizeof(double) * 16 * n_pairs, cudaMemcpyHostToDevice, s));
-  O3G_TRY(cudaMemsetAsync(d_cnt.p, 0, sizeof(unsigned) * 6, s));
+  O3G_TRY(cudaMemsetAsync(d_cnt.p, 0, sizeof(unsigned) * 2, s));
   O3G_TRY(cudaMemsetAsync(d_acc.p, 0, sizeof(unsigned long long) * kPartial * rows_total, s));
   O3G_TRY(cudaMemsetAsync(d_lists.p, 0xff, kListBytes * (total > 0 ? total : 1), s));
   O3G_TRY_STATUS(sort_clouds_batch(reinterpret_cast<const float* const*>(d_ptrs.p), d_strides.as<int32_t>(),
@@ -2570,8 +2300,7 @@ extern "C" int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid*
   {
     TimedRegion tr(O3G_KERNEL_ICP_BATCH, s);
     O3G_TRY_STATUS(run_iterations(d_descs.as<PairDesc>(), d_tiles.as<int>(), d_tiles.as<int>() + tiles_total,
-                                  static_cast<int>(tiles_total), max_iter, eps, d_cnt.as<unsigned>(),
-                                  d_fq.as<int4>(), s));
+                                  static_cast<int>(tiles_total), max_iter, eps, d_cnt.as<unsigned>(), s));
   }
   std::vector<IcpState> h(n_pairs);
   std::vector<int> aux(8 * n_pairs);
@@ -2619,7 +2348,7 @@ struct o3g_server {
     int* src_aux = nullptr;
     void* lists = nullptr;  // candidate lists (kListBytes per source point)
     unsigned long long* acc = nullptr;  // accum_rows(ntiles) x kPartial fixed-point sums
-    int ns = 0, ntiles = 1;
+    int ns = 0, ntiles = 1, ppt = 1;
     int max_iter = 0;
     double eps = 0.0;
     float r = 0.f;
@@ -2643,9 +2372,7 @@ struct o3g_server {
   void* descs = nullptr;    // max_active PairDesc
   int* tiles = nullptr;     // tile table (+1 count), grows
   int64_t tiles_cap = 0;
-  unsigned* queue = nullptr;  // the dynamic tile queue of the server's launches (2 counters), then the
-                              // fallback queue's counters (4)
-  int4* fq_items = nullptr;   // the fallback queue, kStagedMin entries per tile of tiles_cap
+  unsigned* queue = nullptr;  // the dynamic tile queue of the server's launches (2 counters)
   int64_t launches = 0;
   std::map<int64_t, Result> finished;
 };
@@ -2656,7 +2383,7 @@ namespace {
 // Device memory a request will hold while admitted (upper bound before its grid exists).
 int64_t request_bytes(int64_t ns, int64_t nt) {
   const int64_t rows = accum_rows(iter_blocks(ns));
-  return ns * (16 + 48 + 12) + rows * kPartial * 8 + nt * (16 + 16 + 4 + 12 + 12) +
+  return ns * (16 + static_cast<int64_t>(kListBytes) + 12) + rows * kPartial * 8 + nt * (16 + 16 + 4 + 12 + 12) +
          4 * (32 * nt + (1 << 20)) + sizeof(IcpState);
 }
 
@@ -2678,7 +2405,8 @@ int32_t admit(o3g_server* sv, int k, o3g_server::Request& rq) {
   sl.used = true;
   sl.id = rq.id;
   sl.ns = static_cast<int>(ns);
-  sl.ntiles = iter_blocks(ns);
+  sl.ppt = pair_ppt(ns);
+  sl.ntiles = pair_tiles(ns, sl.ppt);
   sl.max_iter = rq.max_iter;
   sl.eps = rq.eps;
   sl.r = static_cast<float>(rq.r);
@@ -2729,6 +2457,7 @@ PairDesc slot_desc(o3g_server* sv, int k, int tile0) {
   P.src4 = sl.src4;
   P.ns = sl.ns;
   P.ntiles = sl.ntiles;
+  P.ppt = sl.ppt;
   P.tile0 = tile0;
   P.st = static_cast<IcpState*>(sv->states) + k;
   set_sums(P, sl.grid, sl.acc);
@@ -2753,23 +2482,15 @@ int32_t launch_slots(o3g_server* sv, const std::vector<int>& ks, int mode) {
   tiles.push_back(static_cast<int>(t0));
   if (static_cast<int64_t>(tiles.size()) > sv->tiles_cap) {
     dfree(sv->tiles, s);
-    dfree(sv->fq_items, s);
     sv->tiles = nullptr;
-    sv->fq_items = nullptr;
     sv->tiles_cap = static_cast<int64_t>(tiles.size()) * 2;
     O3G_TRY(dmalloc(reinterpret_cast<void**>(&sv->tiles), sizeof(int) * sv->tiles_cap, s));
-    O3G_TRY(dmalloc(reinterpret_cast<void**>(&sv->fq_items), sizeof(int4) * sv->tiles_cap * kStagedMin, s));
   }
   O3G_TRY(cudaMemcpyAsync(sv->descs, d.data(), sizeof(PairDesc) * d.size(), cudaMemcpyHostToDevice, s));
   O3G_TRY(cudaMemcpyAsync(sv->tiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice, s));
   PairDesc dummy{};
-  FallbackQueue fq;
-  fq.items = sv->fq_items;
-  fq.count = sv->queue + 2;
-  fq.claim = sv->queue + 4;
-  fq.parity = static_cast<int>(sv->launches & 1);
   launch_iter(false, static_cast<int>(t0), dummy, static_cast<const PairDesc*>(sv->descs), sv->tiles, sv->tiles + t0,
-              mode, s, false, TileQueue{sv->queue, static_cast<int>(sv->launches & 1)}, fq);
+              mode, s, false, TileQueue{sv->queue, static_cast<int>(sv->launches & 1)});
   ++sv->launches;
   count_launch();
   O3G_TRY(cudaGetLastError());
@@ -2802,8 +2523,8 @@ extern "C" int32_t o3g_server_create(int32_t max_active, int64_t hbm_budget_byte
   sv->slots.resize(max_active);
   cudaError_t e = dmalloc(&sv->states, sizeof(IcpState) * max_active, sv->s);
   if (e == cudaSuccess) e = dmalloc(&sv->descs, sizeof(PairDesc) * max_active, sv->s);
-  if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void**>(&sv->queue), sizeof(unsigned) * 6, sv->s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(sv->queue, 0, sizeof(unsigned) * 6, sv->s);
+  if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void**>(&sv->queue), sizeof(unsigned) * 2, sv->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sv->queue, 0, sizeof(unsigned) * 2, sv->s);
   if (e != cudaSuccess) {
     dfree(sv->states, sv->s);
     dfree(sv->descs, sv->s);
@@ -2823,7 +2544,6 @@ extern "C" int32_t o3g_server_destroy(o3g_server* sv) {
   dfree(sv->states, sv->s);
   dfree(sv->descs, sv->s);
   dfree(sv->tiles, sv->s);
-  dfree(sv->fq_items, sv->s);
   dfree(sv->queue, sv->s);
   (void)cudaStreamSynchronize(sv->s);
   delete sv;
@@ -3179,4 +2899,18 @@ extern "C" int32_t o3g_set_tile_config(int32_t size_class, int32_t cfg) {
 extern "C" int32_t o3g_get_tile_config(int32_t size_class) {
   if (size_class < 0 || size_class > 31) return O3G_ERR_ARG;
   return o3g::g_tile_cfg[size_class].load(std::memory_order_relaxed);
+}
+
+extern "C" int32_t o3g_set_points_per_thread(int32_t size_class, int32_t ppt) {
+  if (size_class < 0 || size_class > 31 || !(ppt == 0 || ppt == 1 || ppt == 2 || ppt == 4)) {
+    o3g::set_error("o3g_set_points_per_thread: size class %d or points per thread %d out of range", size_class, ppt);
+    return O3G_ERR_ARG;
+  }
+  o3g::g_ppt[size_class].store(ppt, std::memory_order_relaxed);
+  return O3G_OK;
+}
+
+extern "C" int32_t o3g_get_points_per_thread(int32_t size_class) {
+  if (size_class < 0 || size_class > 31) return O3G_ERR_ARG;
+  return o3g::g_ppt[size_class].load(std::memory_order_relaxed);
 }

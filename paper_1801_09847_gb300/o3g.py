@@ -57,6 +57,8 @@ _SIGNATURES = {
     "o3g_knn_hybrid_batch": ([_i32, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp], _i32),
     "o3g_set_tile_config": ([_i32, _i32], _i32),
     "o3g_get_tile_config": ([_i32], _i32),
+    "o3g_set_points_per_thread": ([_i32, _i32], _i32),
+    "o3g_get_points_per_thread": ([_i32], _i32),
     "o3g_evaluate_poses": ([_vp, _vp, _i64, _i32, _i32, _f64p, _f64, _f64p, _f64p,
                             ctypes.POINTER(ctypes.c_int64), _vp], _i32),
     "o3g_voxel_down_sample": ([_vp, _i64, _i32, _f32, _vp, _vp, ctypes.POINTER(ctypes.c_int64), _vp], _i32),
@@ -394,6 +396,20 @@ def set_tile_config(size_class: int, cfg: int) -> None:
 
 def get_tile_config(size_class: int) -> int:
     return _check(lib().o3g_get_tile_config(int(size_class)), "o3g_get_tile_config")
+
+
+def pair_size_class(n_points: int) -> int:
+    """floor(log2(source points)) clamped to 0..31: the index o3g_set_points_per_thread uses."""
+    return max(0, min(31, int(n_points).bit_length() - 1))
+
+
+def set_points_per_thread(size_class: int, ppt: int) -> None:
+    """Pins the points per thread (0 automatic, 1, 2 or 4) of the pairs of one size class (o3g_set_points_per_thread)."""
+    _check(lib().o3g_set_points_per_thread(int(size_class), int(ppt)), "o3g_set_points_per_thread")
+
+
+def get_points_per_thread(size_class: int) -> int:
+    return _check(lib().o3g_get_points_per_thread(int(size_class)), "o3g_get_points_per_thread")
 
 
 def evaluate_poses(grid: Grid, src, poses, max_corr_dist: float, stream=None):
