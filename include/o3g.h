@@ -403,12 +403,15 @@ O3G_API int32_t o3g_voxel_down_sample(const float* d_xyz, int64_t n, int32_t str
  * slot (max_active) and the device-memory budget (hbm_budget_bytes, estimated
  * per request from its sizes) allow their admission; admission copies the
  * request's clouds to the device, builds its target grid (cell = 1.002 x
- * max_corr_dist), attaches or estimates target normals and lays out its source.
- * Each o3g_server_step then advances every admitted request by one ICP iteration
- * in a single persistent launch, and retires the requests that have converged,
- * stopped or used max_iter iterations (their results wait for
- * o3g_server_poll).  Target grids and per-request pose state stay resident on
- * the device between steps.  Each request's result is the one the single-pair
+ * max_corr_dist), attaches or estimates target normals and lays out its source,
+ * on a stream of the library's own, so that it overlaps the iterations already
+ * enqueued.  Each o3g_server_step then makes 8 persistent launches; in each,
+ * every admitted request advances by one stage of its own, decided on the
+ * device: an ICP iteration, or, once it has converged, stopped or used max_iter
+ * iterations, its final evaluation.  The step reads the requests' state back
+ * once, after the 8 launches, and retires the evaluated ones (their results
+ * wait for o3g_server_poll).  Target grids and per-request pose state stay
+ * resident on the device between steps.  Each request's result is the one the single-pair
  * entry points give for it (same arithmetic, order and tiling), whatever else is
  * being served.  A server and its requests belong to one host thread at a time.
  *   o3g_server_submit copies the host clouds (packed xyz; h_tgt_nrm may be NULL

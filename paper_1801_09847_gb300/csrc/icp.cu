@@ -57,6 +57,8 @@ struct IcpState {
   int few_corr;    // stopped with < 6 correspondences
   int nonfinite;   // the normal equations were not finite
   int lists_on;    // candidate lists are kept (the updates have become small; see ListSink)
+  int phase;       // served pairs (mode kServe): 0 iterating, 1 evaluation next, 2 evaluated
+  int cap;         // served pairs: the iteration limit
   unsigned arrived;  // tiles of the current launch whose sums are added
   double A[36];
   double b[6];
@@ -64,12 +66,15 @@ struct IcpState {
   double fitness, rmse;
 };
 
-enum Mode : int { kIterate = 0, kEquations = 1, kEvaluate = 2, kCorrOnly = 3 };
+// kServe: every pair advances by one stage of its own phase (see IcpState):
+// an iteration, or the final evaluation after the last one.
+enum Mode : int { kIterate = 0, kEquations = 1, kEvaluate = 2, kCorrOnly = 3, kServe = 4 };
 
 // Which transformation estimate an iteration makes (Sec. 3.3).
 enum Kind : int { kPointToPlane = 0, kPointToPoint = 1 };
 
-__global__ void k_init_state(IcpState* st, Pose T) {
+// cap: the iteration limit a served pair stops at (its evaluation comes next at once when 0).
+__global__ void k_init_state(IcpState* st, Pose T, int cap = 0x7fffffff) {
   if (threadIdx.x != 0) return;
   for (int k = 0; k < 16; ++k) st->T[k] = T.m[k];
   for (int r = 0; r < 3; ++r) {
@@ -82,6 +87,8 @@ __global__ void k_init_state(IcpState* st, Pose T) {
   st->few_corr = 0;
   st->nonfinite = 0;
   st->lists_on = 0;
+  st->phase = cap > 0 ? 0 : 1;
+  st->cap = cap;
   st->arrived = 0u;
   st->fitness = 0.0;
   st->rmse = 0.0;
@@ -104,6 +111,8 @@ __global__ void k_init_states(IcpState* st, const double* __restrict__ poses, in
     S.few_corr = 0;
     S.nonfinite = 0;
     S.lists_on = 0;
+    S.phase = 0;
+    S.cap = 0x7fffffff;
     S.arrived = 0u;
     S.fitness = 0.0;
     S.rmse = 0.0;
@@ -1379,11 +1388,17 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
   // loaded together with the first sub-tile's points: one memory round trip
   const int done = P.st->done;
   const int lists_on = P.st->lists_on;
+  const int phase = P.st->phase;
   float R[9], t[3];
 #pragma unroll
   for (int k = 0; k < 9; ++k) R[k] = P.st->R[k];
 #pragma unroll
   for (int k = 0; k < 3; ++k) t[k] = P.st->t[k];
+  const int mode_in = mode;
+  if (mode == kServe) {
+    if (phase >= 2) return;
+    mode = phase == 0 ? kIterate : kEvaluate;
+  }
   const bool keep = P.lists.pb != nullptr;  // matches (and lists) are kept across launches
   // (a launch form without list support searches every point: the same
   // correspondences and the same sums, only slower)
@@ -1495,6 +1510,10 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
   if (!last) return;
   __threadfence();
   finish(P, mode, nlen);
+  if (mode_in == kServe && threadIdx.x == 0) {  // the thread that wrote the state in finish
+    IcpState* const st = P.st;
+    st->phase = mode == kEvaluate ? 2 : ((st->done || st->iters >= st->cap) ? 1 : 0);
+  }
 }
 
 // One ICP step of every pair: a persistent kernel whose blocks walk the global
@@ -2362,7 +2381,9 @@ struct o3g_server {
     double fitness, rmse;
     int32_t iters;
   };
-  cudaStream_t s = nullptr;
+  cudaStream_t s = nullptr;   // the stream the iterations run on (the caller's)
+  cudaStream_t as = nullptr;  // the library's admission stream
+  cudaEvent_t admitted = nullptr;  // recorded on `as` after admissions; `s` waits for it
   int max_active = 0;
   int64_t budget = 0, used = 0;
   int64_t next_id = 0;
@@ -2399,7 +2420,7 @@ void release_slot(o3g_server* sv, o3g_server::Slot& sl) {
 
 // Admission of one request into free slot k (device copies, grid, normals, layout, state).
 int32_t admit(o3g_server* sv, int k, o3g_server::Request& rq) {
-  cudaStream_t s = sv->s;
+  cudaStream_t s = sv->as;  // the admission stream: copies, grid, normals and sort overlap the iterations
   o3g_server::Slot& sl = sv->slots[k];
   const int64_t ns = static_cast<int64_t>(rq.src.size() / 3), nt = static_cast<int64_t>(rq.tgt.size() / 3);
   sl.used = true;
@@ -2436,7 +2457,7 @@ int32_t admit(o3g_server* sv, int k, o3g_server::Request& rq) {
   const size_t acc_bytes = sizeof(unsigned long long) * kPartial * accum_rows(sl.ntiles);
   O3G_TRY(dmalloc(reinterpret_cast<void**>(&sl.acc), acc_bytes, s));
   O3G_TRY(cudaMemsetAsync(sl.acc, 0, acc_bytes, s));
-  k_init_state<<<1, 32, 0, s>>>(static_cast<IcpState*>(sv->states) + k, to_pose(rq.T0));
+  k_init_state<<<1, 32, 0, s>>>(static_cast<IcpState*>(sv->states) + k, to_pose(rq.T0), rq.max_iter);
   count_launch();
   O3G_TRY(cudaGetLastError());
   sl.iters = 0;
@@ -2468,8 +2489,12 @@ PairDesc slot_desc(o3g_server* sv, int k, int tile0) {
   return P;
 }
 
-// One launch of `mode` over the given slots.
-int32_t launch_slots(o3g_server* sv, const std::vector<int>& ks, int mode) {
+// Launches per o3g_server_step (stages every admitted request advances by).
+constexpr int kServeStages = 8;
+
+// `launches` launches of `mode` over the given slots (after the first, each as a
+// programmatic dependent of the one before).
+int32_t launch_slots(o3g_server* sv, const std::vector<int>& ks, int mode, int launches = 1) {
   cudaStream_t s = sv->s;
   std::vector<PairDesc> d;
   std::vector<int> tiles;
@@ -2489,10 +2514,12 @@ int32_t launch_slots(o3g_server* sv, const std::vector<int>& ks, int mode) {
   O3G_TRY(cudaMemcpyAsync(sv->descs, d.data(), sizeof(PairDesc) * d.size(), cudaMemcpyHostToDevice, s));
   O3G_TRY(cudaMemcpyAsync(sv->tiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice, s));
   PairDesc dummy{};
-  launch_iter(false, static_cast<int>(t0), dummy, static_cast<const PairDesc*>(sv->descs), sv->tiles, sv->tiles + t0,
-              mode, s, false, TileQueue{sv->queue, static_cast<int>(sv->launches & 1)});
-  ++sv->launches;
-  count_launch();
+  for (int l = 0; l < launches; ++l) {
+    launch_iter(false, static_cast<int>(t0), dummy, static_cast<const PairDesc*>(sv->descs), sv->tiles,
+                sv->tiles + t0, mode, s, l > 0, TileQueue{sv->queue, static_cast<int>(sv->launches & 1)});
+    ++sv->launches;
+    count_launch();
+  }
   O3G_TRY(cudaGetLastError());
   return O3G_OK;
 }
@@ -2518,6 +2545,12 @@ extern "C" int32_t o3g_server_create(int32_t max_active, int64_t hbm_budget_byte
     return O3G_ERR_OOM;
   }
   sv->s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamCreateWithFlags(&sv->as, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&sv->admitted, cudaEventDisableTiming) != cudaSuccess) {
+    if (sv->as) cudaStreamDestroy(sv->as);
+    delete sv;
+    return cuda_fail(cudaGetLastError(), "o3g_server_create");
+  }
   sv->max_active = max_active;
   sv->budget = hbm_budget_bytes;
   sv->slots.resize(max_active);
@@ -2529,6 +2562,9 @@ extern "C" int32_t o3g_server_create(int32_t max_active, int64_t hbm_budget_byte
     dfree(sv->states, sv->s);
     dfree(sv->descs, sv->s);
     dfree(sv->queue, sv->s);
+    (void)cudaStreamSynchronize(sv->s);
+    cudaEventDestroy(sv->admitted);
+    cudaStreamDestroy(sv->as);
     delete sv;
     return cuda_fail(e, "o3g_server_create");
   }
@@ -2545,7 +2581,10 @@ extern "C" int32_t o3g_server_destroy(o3g_server* sv) {
   dfree(sv->descs, sv->s);
   dfree(sv->tiles, sv->s);
   dfree(sv->queue, sv->s);
+  (void)cudaStreamSynchronize(sv->as);
   (void)cudaStreamSynchronize(sv->s);
+  cudaEventDestroy(sv->admitted);
+  cudaStreamDestroy(sv->as);
   delete sv;
   return O3G_OK;
 }
@@ -2595,6 +2634,7 @@ extern "C" int32_t o3g_server_step(o3g_server* sv, int32_t* out_active, int32_t*
     return O3G_ERR_ARG;
   }
   cudaStream_t s = sv->s;
+  bool admitted = false;
   // admit while a slot is free and the budget allows (first come, first served)
   while (!sv->waiting.empty()) {
     int k = -1;
@@ -2607,6 +2647,7 @@ extern "C" int32_t o3g_server_step(o3g_server* sv, int32_t* out_active, int32_t*
     const int64_t need = request_bytes(static_cast<int64_t>(rq.src.size() / 3), static_cast<int64_t>(rq.tgt.size() / 3));
     if (k < 0 || sv->used + need > sv->budget) break;
     const int32_t st = admit(sv, k, rq);
+    admitted = true;
     if (st < 0) {
       release_slot(sv, sv->slots[k]);
       o3g_server::Result res{};
@@ -2617,48 +2658,50 @@ extern "C" int32_t o3g_server_step(o3g_server* sv, int32_t* out_active, int32_t*
     }
     sv->waiting.pop_front();
   }
-  std::vector<int> iterate, finishing;
-  for (int k = 0; k < sv->max_active; ++k) {
-    const auto& sl = sv->slots[k];
-    if (!sl.used) continue;
-    if (!sl.done && sl.iters < sl.max_iter) iterate.push_back(k);
-    else finishing.push_back(k);
+  // the launches of this step see the requests admitted so far
+  if (admitted) {
+    O3G_TRY(cudaEventRecord(sv->admitted, sv->as));
+    O3G_TRY(cudaStreamWaitEvent(s, sv->admitted, 0));
   }
-  if (!iterate.empty()) {
-    O3G_TRY_STATUS(launch_slots(sv, iterate, kIterate));
+  std::vector<int> active_slots;
+  for (int k = 0; k < sv->max_active; ++k)
+    if (sv->slots[k].used) active_slots.push_back(k);
+  int completed = 0;
+  if (!active_slots.empty()) {
+    // kServeStages launches, each advancing every admitted request by one
+    // stage of its own (an iteration, or the evaluation after the last one),
+    // with the state read back once
+    O3G_TRY_STATUS(launch_slots(sv, active_slots, kServe, kServeStages));
     std::vector<IcpState> h(sv->max_active);
     O3G_TRY(cudaMemcpyAsync(h.data(), sv->states, sizeof(IcpState) * sv->max_active, cudaMemcpyDeviceToHost, s));
     O3G_TRY(cudaStreamSynchronize(s));
-    for (int k : iterate) {
+    std::vector<int> finishing;
+    for (int k : active_slots) {
       auto& sl = sv->slots[k];
       sl.iters = h[k].iters;
       sl.done = h[k].done != 0;
-      if (sl.done || sl.iters >= sl.max_iter) finishing.push_back(k);
+      if (h[k].phase >= 2) finishing.push_back(k);
     }
-  }
-  int completed = 0;
-  if (!finishing.empty()) {
-    O3G_TRY_STATUS(launch_slots(sv, finishing, kEvaluate));
-    std::vector<IcpState> h(sv->max_active);
-    O3G_TRY(cudaMemcpyAsync(h.data(), sv->states, sizeof(IcpState) * sv->max_active, cudaMemcpyDeviceToHost, s));
-    std::vector<int> aux(8 * sv->max_active, 0);
-    for (int k : finishing)
-      O3G_TRY(cudaMemcpyAsync(aux.data() + 8 * k, sv->slots[k].src_aux, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
-    O3G_TRY(cudaStreamSynchronize(s));
-    for (int k : finishing) {
-      auto& sl = sv->slots[k];
-      o3g_server::Result res;
-      for (int q = 0; q < 16; ++q) res.T[q] = h[k].T[q];
-      res.fitness = h[k].fitness;
-      res.rmse = h[k].rmse;
-      res.iters = h[k].iters;
-      res.status = aux[8 * k + 6] || h[k].nonfinite ? O3G_ERR_NONFINITE
-                   : h[k].few_corr                  ? O3G_WARN_FEW_CORR
-                   : h[k].degenerate                ? O3G_WARN_DEGENERATE
-                                                    : O3G_OK;
-      sv->finished[sl.id] = res;
-      release_slot(sv, sl);
-      ++completed;
+    if (!finishing.empty()) {
+      std::vector<int> aux(8 * sv->max_active, 0);
+      for (int k : finishing)
+        O3G_TRY(cudaMemcpyAsync(aux.data() + 8 * k, sv->slots[k].src_aux, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
+      O3G_TRY(cudaStreamSynchronize(s));
+      for (int k : finishing) {
+        auto& sl = sv->slots[k];
+        o3g_server::Result res;
+        for (int q = 0; q < 16; ++q) res.T[q] = h[k].T[q];
+        res.fitness = h[k].fitness;
+        res.rmse = h[k].rmse;
+        res.iters = h[k].iters;
+        res.status = aux[8 * k + 6] || h[k].nonfinite ? O3G_ERR_NONFINITE
+                     : h[k].few_corr                  ? O3G_WARN_FEW_CORR
+                     : h[k].degenerate                ? O3G_WARN_DEGENERATE
+                                                      : O3G_OK;
+        sv->finished[sl.id] = res;
+        release_slot(sv, sl);
+        ++completed;
+      }
     }
   }
   int active = 0;

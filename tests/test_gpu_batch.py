@@ -155,3 +155,41 @@ def test_autotune_picks_a_measured_candidate_and_pins_it(o3g, problems):
         assert all(np.array_equal(a["T"], b["T"]) for a, b in zip(tuned, ref))
     finally:
         o3g.set_tile_config(cls, o3g.TILE_AUTO)
+
+
+def test_points_per_thread_alone_batch_and_oracle(o3g, problems):
+    """Points per thread (the autotuner's tile-size knob) pinned to 1, 2 and 4 for the pairs' size classes: a
+    pair still gives the same result alone and in the batch bit for bit (the setting belongs to the pair's size
+    class), the correspondence set at the final pose is the oracle's bit for bit, and every iterate of the
+    well-conditioned corner pair is the oracle's Gauss-Newton step from the previous one (1e-7 rad / m)."""
+    classes = sorted({o3g.pair_size_class(int(p[1].shape[0])) for p in problems})
+    grid, d_src, T0, r, src, tgt, nrm = problems[5]
+    try:
+        for ppt in (1, 2, 4):
+            for c in classes:
+                o3g.set_points_per_thread(c, ppt)
+                assert o3g.get_points_per_thread(c) == ppt
+            alone = [o3g.icp_point_to_plane_grid(g, s, T, rr, 12) for g, s, T, rr, *_ in problems]
+            batch = o3g.icp_point_to_plane_batch([p[0] for p in problems], [p[1] for p in problems],
+                                                 [p[2] for p in problems], [p[3] for p in problems], 12)
+            for a, b in zip(alone, batch):
+                _same(a, b)
+            res = o3g.icp_point_to_plane_grid(grid, d_src, T0, r, 12, correspondences=True)
+            p = oracle.transform(src, res["T"])
+            c_ref, d_ref = oracle.nn(p, tgt, r)
+            assert np.array_equal(res["corr"].cpu().numpy(), c_ref) and np.array_equal(res["d2"].cpu().numpy(), d_ref)
+            T = T0
+            for k in range(1, 6):
+                Tk = o3g.icp_point_to_plane_grid(grid, d_src, T0, r, k)["T"]
+                pk = oracle.transform(src, T)
+                corr, d2 = oracle.nn(pk, tgt, r)
+                A, b, _, _, _ = oracle.normal_equations(pk, tgt, nrm, corr, d2)
+                xi, _ = oracle.ldlt_solve(A, b)
+                ang, dt = synth.pose_error(Tk, oracle.delta_T(xi) @ T)
+                assert ang <= 1e-7 and dt <= 1e-7, (ppt, k, ang, dt)
+                T = Tk
+        with pytest.raises(o3g.O3GError):
+            o3g.set_points_per_thread(classes[0], 3)
+    finally:
+        for c in classes:
+            o3g.set_points_per_thread(c, 0)
