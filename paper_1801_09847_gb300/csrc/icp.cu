@@ -286,23 +286,12 @@ __device__ __forceinline__ void list_store(const ListRef& L, int i, const ListSi
     L.idx[kListVec * i + k] = make_int4(e[4 * k], e[4 * k + 1], e[4 * k + 2], e[4 * k + 3]);
 }
 
-// Offers the sorted target positions [beg, end) to a sink, loading them
-// kRunGroup at a time (the loads of a group are independent, so they overlap;
-// offering one candidate at a time would expose a full memory latency per
-// candidate).
-constexpr int kRunGroup = 4;
-
+// Offers the sorted target positions [beg, end) to a sink in order.
 template <class Sink>
 __device__ __forceinline__ void offer_run(const GridView& g, uint32_t beg, uint32_t end, float px, float py, float pz,
                                           Sink& sk) {
-  for (uint32_t j = beg; j < end; j += kRunGroup) {
-    float4 q[kRunGroup];
-#pragma unroll
-    for (int k = 0; k < kRunGroup; ++k) q[k] = j + k < end ? g.pts[j + k] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k < kRunGroup; ++k)
-      if (j + k < end) sk.offer(q[k], static_cast<int>(j + k), px, py, pz);
-  }
+#pragma unroll 4
+  for (uint32_t j = beg; j < end; ++j) sk.offer(g.pts[j], static_cast<int>(j), px, py, pz);
 }
 
 // Candidates that give a first bound: this point's match in the previous
@@ -1414,9 +1403,10 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
     const int i = (j * P.ppt + sub) * kThreads + threadIdx.x;
     const bool live = i < P.ns;
     const float4 s = live ? P.src4[i] : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
-    // the last match seeds the search (before lists, every point searches; with
-    // lists, only the points their lists no longer cover, which read it later)
-    int hint = (keep && live && !lists_on) ? P.lists.hint[i] : -1;
+    // the last match seeds the search (before lists, of every point; with lists,
+    // of the points their lists no longer cover); loaded with the point, not
+    // after the state, so that the tile starts with one memory round trip
+    int hint = (keep && live) ? P.lists.hint[i] : -1;
     float4 pb = make_float4(0.f, 0.f, 0.f, -1.f);
     int4 l[kListVec];
 #pragma unroll
@@ -1438,14 +1428,12 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
     bool need = live;
     if (lists) {
       need = live && !list_scan(P.g, pb, l, p.x, p.y, p.z, nb);
-      if (need) {
-        hint = P.lists.hint[i];
-        if (hint >= 0) consider(nb, P.g.pts[hint], hint, p.x, p.y, p.z);
-      }
+      if (need && hint >= 0) consider(nb, P.g.pts[hint], hint, p.x, p.y, p.z);
     } else {
       first_bound(P.g, p.x, p.y, p.z, hint, nb);
     }
-    if (__syncthreads_or(need)) {
+    // (before lists every live point searches: no vote needed)
+    if (!lists || __syncthreads_or(need)) {
       if (lists) {
         ListSink ls{nb, s_ld, s_lp, list_lim(nb.d2, sigma), 0, 0.f, 0};
         if (!staged_search(P.g, P.cell, p.x, p.y, p.z, Rl, need, ls, stage, St::kStagePts - kListPts) && need)
@@ -2374,6 +2362,7 @@ struct o3g_server {
     int64_t bytes = 0;
     int iters = 0;
     bool done = false;
+    bool fresh = false;  // admitted in the current step (its first launches come in the next)
   };
   struct Result {
     int32_t status;
@@ -2634,6 +2623,14 @@ extern "C" int32_t o3g_server_step(o3g_server* sv, int32_t* out_active, int32_t*
     return O3G_ERR_ARG;
   }
   cudaStream_t s = sv->s;
+  // kServeStages launches over the requests admitted in earlier steps, each
+  // launch advancing every one by one stage of its own (an iteration, or the
+  // evaluation after the last one); the admissions of this step run on the
+  // admission stream while they execute, and join in the next step
+  std::vector<int> active_slots;
+  for (int k = 0; k < sv->max_active; ++k)
+    if (sv->slots[k].used && !sv->slots[k].fresh) active_slots.push_back(k);
+  if (!active_slots.empty()) O3G_TRY_STATUS(launch_slots(sv, active_slots, kServe, kServeStages));
   bool admitted = false;
   // admit while a slot is free and the budget allows (first come, first served)
   while (!sv->waiting.empty()) {
@@ -2656,22 +2653,25 @@ extern "C" int32_t o3g_server_step(o3g_server* sv, int32_t* out_active, int32_t*
       sv->waiting.pop_front();
       continue;
     }
+    sv->slots[k].fresh = true;
     sv->waiting.pop_front();
   }
-  // the launches of this step see the requests admitted so far
+  // later launches see the requests admitted so far
   if (admitted) {
     O3G_TRY(cudaEventRecord(sv->admitted, sv->as));
     O3G_TRY(cudaStreamWaitEvent(s, sv->admitted, 0));
   }
-  std::vector<int> active_slots;
-  for (int k = 0; k < sv->max_active; ++k)
-    if (sv->slots[k].used) active_slots.push_back(k);
+  if (active_slots.empty()) {  // nothing was running: the new requests start at once
+    for (int k = 0; k < sv->max_active; ++k)
+      if (sv->slots[k].used && sv->slots[k].fresh) {
+        sv->slots[k].fresh = false;
+        active_slots.push_back(k);
+      }
+    if (!active_slots.empty()) O3G_TRY_STATUS(launch_slots(sv, active_slots, kServe, kServeStages));
+  }
+  for (auto& sl : sv->slots) sl.fresh = false;
   int completed = 0;
   if (!active_slots.empty()) {
-    // kServeStages launches, each advancing every admitted request by one
-    // stage of its own (an iteration, or the evaluation after the last one),
-    // with the state read back once
-    O3G_TRY_STATUS(launch_slots(sv, active_slots, kServe, kServeStages));
     std::vector<IcpState> h(sv->max_active);
     O3G_TRY(cudaMemcpyAsync(h.data(), sv->states, sizeof(IcpState) * sv->max_active, cudaMemcpyDeviceToHost, s));
     O3G_TRY(cudaStreamSynchronize(s));
