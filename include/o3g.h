@@ -56,7 +56,8 @@ typedef enum {
   O3G_ERR_OOM = -2,        /* device allocation failed */
   O3G_ERR_CUDA = -3,       /* a CUDA runtime call failed; see o3g_last_error() */
   O3G_ERR_NONFINITE = -4,  /* a coordinate, a normal or the pose is NaN or infinite */
-  O3G_ERR_TIMEOUT = -5     /* a bounded device-side wait gave up */
+  O3G_ERR_TIMEOUT = -5     /* reserved for a bounded device-side wait that gives up; no entry point of this
+                              library returns it, since no kernel here waits on a flag */
 } o3g_status;
 
 /* Largest max_nn accepted by the hybrid search and normal estimation. */
@@ -462,6 +463,8 @@ O3G_API int32_t o3g_server_completed(o3g_server* server, int64_t* ids, int32_t c
  *   - Every call uses the same array.  Calls whose work overlaps on the GPU
  *     (other streams, other host threads) race and corrupt each other's state:
  *     serialise them.  Each call clears what must start at zero.
+ *   - Like the other ICP entry points it returns host values, so it
+ *     synchronises `stream` before returning.
  */
 #define O3G_NOALLOC_MAX_POINTS 262144
 O3G_API int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* tgt, const float* d_src, int64_t ns,
