@@ -225,15 +225,20 @@ struct ListSink {
   __device__ __forceinline__ float rho2() const { return m < kList ? lim : maxv; }
 };
 
-// The state of one source point's list: (p_b, rho2) and kList sorted target
-// positions (-1: empty).  rho2 NaN (the initial all-ones bytes): no list.
+// The state of one source point's list: (p_b, rho2), its kList entries (sorted
+// target positions, -1: empty) ordered by (d2 from p_b, position), and for
+// entries 1 .. kList-1 a code c_k with c_k sigma / kGapScale <= (distance of
+// entry k from p_b) - (distance of entry 0 from p_b), saturating at 255.
+// rho2 NaN (the initial all-ones bytes): no list.
 struct ListRef {
   float4* pb;  // per source point
   int4* idx;   // kListVec per source point
+  uint2* gap;  // per source point: c_1..c_4 in the bytes of .x, c_5..c_7 in .y
   int* hint;   // per source point: sorted target position of its last match, or -1
 };
+constexpr float kGapScale = 127.5f;  // codes in units of sigma / 127.5: 255 = two skins
 // bytes per source point, a multiple of 16 (buffers of many pairs stay aligned)
-constexpr size_t kListBytes = (sizeof(float4) * (1 + kListVec) + sizeof(int) + 15) / 16 * 16;
+constexpr size_t kListBytes = (sizeof(float4) * (1 + kListVec) + sizeof(uint2) + sizeof(int) + 15) / 16 * 16;
 
 // Candidate lists pay where an iteration launch is bound by throughput rather
 // than by the latency of one wave of tiles: a pair keeps them when it has at
@@ -247,14 +252,22 @@ inline float list_motion(int64_t ns, float r) { return ns >= kListMinPoints ? 0.
 inline ListRef list_ref(void* base, int64_t n) {
   float4* pb = static_cast<float4*>(base);
   int4* idx = reinterpret_cast<int4*>(pb + n);
-  return ListRef{pb, idx, reinterpret_cast<int*>(idx + kListVec * n)};
+  uint2* gap = reinterpret_cast<uint2*>(idx + kListVec * n);
+  return ListRef{pb, idx, gap, reinterpret_cast<int*>(gap + n)};
 }
 
 // Scans a query's list at its position p: the nearest listed target within r2
 // goes into nb (a first bound for a rebuild), and the result says whether the
-// list covers the query (see above).
-__device__ __forceinline__ bool list_scan(const GridView& g, float4 pb, const int4 (&l)[kListVec], float px,
-                                          float py, float pz, Nearest& nb) {
+// list covers the query (see above).  With d = |p - p_b|, entry k lies at least
+// (its distance from p_b) - d from p, and entry 0 at most (its distance) + d;
+// so an entry whose code puts it farther from p_b than entry 0 by more than
+// 2 d (plus a relative margin of 2e-4 of a bound on both distances, which keeps
+// its float32 d2 strictly above entry 0's) can neither win nor tie, and is not
+// loaded.  Entries 0-3 are scanned in every warp, 4-7 only in a warp where
+// some lane needs one of them.  All lanes of the warp must call this (a lane
+// without a list has only empty entries).
+__device__ __forceinline__ bool list_scan(const GridView& g, float4 pb, const int4 (&l)[kListVec], uint2 gap,
+                                          float sigma, float px, float py, float pz, Nearest& nb) {
   int e[kList];
 #pragma unroll
   for (int k = 0; k < kListVec; ++k) {
@@ -263,27 +276,85 @@ __device__ __forceinline__ bool list_scan(const GridView& g, float4 pb, const in
     e[4 * k + 2] = l[k].z;
     e[4 * k + 3] = l[k].w;
   }
-  float4 q[kList];
-#pragma unroll
-  for (int k = 0; k < kList; ++k) q[k] = e[k] >= 0 ? g.pts[e[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-  for (int k = 0; k < kList; ++k)
-    if (e[k] >= 0) consider(nb, q[k], e[k], px, py, pz);
   const float moved = dist2_rn(px, py, pz, pb);  // NaN without a list
-  const float s = __fadd_rn(fast_sqrt(__fmul_rn(nb.d2, 1.0001f)), fast_sqrt(__fmul_rn(moved, 1.0001f)));
+  const float dm = fast_sqrt(__fmul_rn(moved, 1.0001f));
+  const float thr = __fmul_rn(__fadd_rn(__fmul_rn(2.f, dm), __fmul_rn(2e-4f, __fadd_rn(fast_sqrt(__fmul_rn(pb.w, 1.0001f)), dm))),
+                              1.0001f);
+  const float unit = __fmul_rn(sigma, 1.f / kGapScale);
+  unsigned need = e[0] >= 0 ? 1u : 0u;
+#pragma unroll
+  for (int k = 1; k < kList; ++k) {
+    const unsigned c = ((k <= 4 ? gap.x : gap.y) >> (8 * ((k - 1) & 3))) & 0xffu;
+    if (e[k] >= 0 && !(__fmul_rn(static_cast<float>(c), unit) > thr)) need |= 1u << k;
+  }
+  const unsigned any = __reduce_or_sync(0xffffffffu, need);
+  {
+    float4 q[kList / 2];
+#pragma unroll
+    for (int k = 0; k < kList / 2; ++k) q[k] = ((need >> k) & 1u) ? g.pts[e[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < kList / 2; ++k)
+      if ((need >> k) & 1u) consider(nb, q[k], e[k], px, py, pz);
+  }
+  if (any >> (kList / 2)) {
+    float4 q[kList / 2];
+#pragma unroll
+    for (int k = kList / 2; k < kList; ++k)
+      q[k - kList / 2] = ((need >> k) & 1u) ? g.pts[e[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = kList / 2; k < kList; ++k)
+      if ((need >> k) & 1u) consider(nb, q[k - kList / 2], e[k], px, py, pz);
+  }
+  const float s = __fadd_rn(fast_sqrt(__fmul_rn(nb.d2, 1.0001f)), dm);
   return __fadd_rn(__fmul_rn(__fmul_rn(s, s), 1.0001f), 1e-30f) < pb.w;
 }
 
-// Stores a rebuilt list of thread threadIdx.x for source point i.
+// Stores a rebuilt list of thread threadIdx.x for source point i: its entries
+// sorted by (d2, position) (a 19-comparator merging network; empty entries
+// last) and the gap codes of entries 1.. against entry 0, each rounded down
+// from a lower bound on the true difference of the distances (relative
+// margins of 1e-4 cover the float32 d2 and square roots).
 __device__ __forceinline__ void list_store(const ListRef& L, int i, const ListSink& ls, float px, float py,
-                                           float pz) {
+                                           float pz, float sigma) {
+  float d[kList];
   int e[kList];
 #pragma unroll
-  for (int k = 0; k < kList; ++k) e[k] = k < ls.m ? ls.p[k][threadIdx.x] : -1;
-  L.pb[i] = make_float4(px, py, pz, ls.rho2());
+  for (int k = 0; k < kList; ++k) {
+    d[k] = k < ls.m ? ls.d[k][threadIdx.x] : __int_as_float(0x7f800000);
+    e[k] = k < ls.m ? ls.p[k][threadIdx.x] : 0x7fffffff;
+  }
+  constexpr int kNet[19][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3}, {4, 6}, {5, 7}, {1, 2}, {5, 6},
+                               {0, 4}, {1, 5}, {2, 6}, {3, 7}, {2, 4}, {3, 5}, {1, 2}, {3, 4}, {5, 6}};
+#pragma unroll
+  for (int c = 0; c < 19; ++c) {
+    const int a = kNet[c][0], b = kNet[c][1];
+    if (d[a] > d[b] || (d[a] == d[b] && e[a] > e[b])) {
+      const float td = d[a];
+      d[a] = d[b];
+      d[b] = td;
+      const int te = e[a];
+      e[a] = e[b];
+      e[b] = te;
+    }
+  }
+  const float r0 = fast_sqrt(__fmul_rn(d[0], 1.0002f));
+  const float inv = __fdiv_rn(kGapScale, sigma);
+  unsigned code[kList];
+#pragma unroll
+  for (int k = 1; k < kList; ++k) {
+    const float gk = __fsub_rn(fast_sqrt(__fmul_rn(d[k], 0.9998f)), r0);
+    const float c = __fmul_rn(__fmul_rn(gk, inv), 0.9999f);
+    code[k] = k < ls.m && c > 0.f ? (c >= 255.f ? 255u : static_cast<unsigned>(c)) : 0u;
+  }
+#pragma unroll
+  for (int k = 0; k < kList; ++k)
+    if (k >= ls.m) e[k] = -1;
+  __stcs(&L.pb[i], make_float4(px, py, pz, ls.rho2()));
 #pragma unroll
   for (int k = 0; k < kListVec; ++k)
-    L.idx[kListVec * i + k] = make_int4(e[4 * k], e[4 * k + 1], e[4 * k + 2], e[4 * k + 3]);
+    __stcs(&L.idx[kListVec * i + k], make_int4(e[4 * k], e[4 * k + 1], e[4 * k + 2], e[4 * k + 3]));
+  __stcs(&L.gap[i], make_uint2(code[1] | (code[2] << 8) | (code[3] << 16) | (code[4] << 24),
+                               code[5] | (code[6] << 8) | (code[7] << 16)));
 }
 
 // Offers the sorted target positions [beg, end) to a sink in order.
@@ -1402,19 +1473,23 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
   for (int sub = 0; sub < P.ppt; ++sub) {
     const int i = (j * P.ppt + sub) * kThreads + threadIdx.x;
     const bool live = i < P.ns;
-    const float4 s = live ? P.src4[i] : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
+    // (the source, hints and lists are read once per launch: loaded with the
+    // streaming hint, so that the targets and normals the gathers reuse stay in L2)
+    const float4 s = live ? __ldcs(&P.src4[i]) : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
     // the last match seeds the search (before lists, of every point; with lists,
     // of the points their lists no longer cover); loaded with the point, not
     // after the state, so that the tile starts with one memory round trip
-    int hint = (keep && live) ? P.lists.hint[i] : -1;
+    int hint = (keep && live) ? __ldcs(&P.lists.hint[i]) : -1;
     float4 pb = make_float4(0.f, 0.f, 0.f, -1.f);
     int4 l[kListVec];
 #pragma unroll
     for (int k = 0; k < kListVec; ++k) l[k] = make_int4(-1, -1, -1, -1);
+    uint2 gap = make_uint2(0u, 0u);
     if (lists && live) {
-      pb = P.lists.pb[i];
+      pb = __ldcs(&P.lists.pb[i]);
 #pragma unroll
-      for (int k = 0; k < kListVec; ++k) l[k] = P.lists.idx[kListVec * i + k];
+      for (int k = 0; k < kListVec; ++k) l[k] = __ldcs(&P.lists.idx[kListVec * i + k]);
+      gap = __ldcs(&P.lists.gap[i]);
     }
     if (mode == kIterate && done) return;
     const float3 p = live ? xform_rn(R, t, s.x, s.y, s.z) : make_float3(3.0e38f, 3.0e38f, 3.0e38f);
@@ -1427,7 +1502,8 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
     Nearest nb{r2, 0x7fffffff, -1};
     bool need = live;
     if (lists) {
-      need = live && !list_scan(P.g, pb, l, p.x, p.y, p.z, nb);
+      const bool covered = list_scan(P.g, pb, l, gap, sigma, p.x, p.y, p.z, nb);  // every lane
+      need = live && !covered;
       if (need && hint >= 0) consider(nb, P.g.pts[hint], hint, p.x, p.y, p.z);
     } else {
       first_bound(P.g, p.x, p.y, p.z, hint, nb);
@@ -1438,7 +1514,7 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
         ListSink ls{nb, s_ld, s_lp, list_lim(nb.d2, sigma), 0, 0.f, 0};
         if (!staged_search(P.g, P.cell, p.x, p.y, p.z, Rl, need, ls, stage, St::kStagePts - kListPts) && need)
           box_search_global(P.g, P.cell, p.x, p.y, p.z, Rl, ls);
-        if (need) list_store(P.lists, i, ls, p.x, p.y, p.z);
+        if (need) list_store(P.lists, i, ls, p.x, p.y, p.z, sigma);
         nb = ls.nb;
       } else {
         NnSink ns{nb};
@@ -1764,7 +1840,7 @@ struct Work {
     P.tile0 = 0;
     P.st = state.as<IcpState>();
     set_sums(P, g, acc.as<unsigned long long>());
-    P.lists = (mode == kIterate || mode == kEvaluate) ? list_ref(lists.p, ns) : ListRef{nullptr, nullptr, nullptr};
+    P.lists = (mode == kIterate || mode == kEvaluate) ? list_ref(lists.p, ns) : ListRef{nullptr, nullptr, nullptr, nullptr};
     P.list_motion = list_motion(ns, r);
     P.corr_out = corr;
     P.d2_out = d2;
@@ -2089,7 +2165,7 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const 
     P.tile0 = 0;
     P.st = st;
     set_sums(P, g, acc);
-    P.lists = ListRef{nullptr, nullptr, nullptr};
+    P.lists = ListRef{nullptr, nullptr, nullptr, nullptr};
     P.list_motion = -1.f;
     P.corr_out = nullptr;
     P.d2_out = nullptr;

@@ -671,10 +671,11 @@ def test_combined_call_with_gpu_normals_shadows_oracle(o3g, room):
 @pytest.mark.parametrize("case", ["room", "ties", "sphere_plane"])
 def test_warm_search_correspondence_set_bitexact(o3g, room, case):
     """The correspondence set at the final pose of an ICP run, found by the warm-started search the iterations
-    use (the previous matches as first candidates, the walk through the first candidate's neighbour record when
-    it covers the query, the grid search otherwise), bit-exact against the oracle at the GPU's own final pose:
-    the full RGB-D-frame pair, a quantised cloud with exact ties and duplicate points, and the sphere-plane pair,
-    after several iteration counts (0 = the cold search alone)."""
+    use (the previous matches of the point and its warp neighbours as first candidates, then the grid search
+    within that bound), bit-exact against the oracle at the GPU's own final pose: the full RGB-D-frame pair, a
+    quantised cloud with exact ties and duplicate points, and the sphere-plane pair, after several iteration
+    counts (0 = the cold search alone).  These pairs are below the size that keeps candidate lists; the next
+    test covers those."""
     if case == "room":
         src, tgt, r = room.src, room.tgt, room.max_corr_dist
         nrm = oracle.estimate_normals(tgt, 0.05, 30)
@@ -700,6 +701,33 @@ def test_warm_search_correspondence_set_bitexact(o3g, room, case):
         c_ref, d_ref = oracle.nn(p, tgt, r, method=method)
         assert np.array_equal(res["corr"].cpu().numpy(), c_ref), (case, k)
         assert np.array_equal(res["d2"].cpu().numpy(), d_ref), (case, k)
+
+
+def test_candidate_lists_on_quantised_pair_bitexact(o3g):
+    """A pair large enough to keep candidate lists (at least 2^17 source points), with both clouds on a 2 mm
+    lattice so that listed candidates often lie at exactly equal distances, and duplicated target points that
+    tie at every distance: the correspondence set of the final evaluation after 0 to 40 iterations (no lists;
+    lists built once the updates are small; rebuilt as points drift past their skin; held) is bit-exact against
+    the oracle's search at the GPU's own final pose, and the fitness is its count."""
+    pr = synth.sphere_plane_pair(n=160_000, seed=77)
+    q = 0.002
+    tgt = (np.round(pr.tgt / q) * q).astype(np.float32)
+    nrm = pr.tgt_nrm.copy()
+    tgt[80_000:90_000] = tgt[:10_000]  # later copies must lose every tie
+    nrm[80_000:90_000] = nrm[:10_000]
+    src = (np.round(pr.src / q) * q).astype(np.float32)
+    r = pr.max_corr_dist
+    assert len(src) >= 1 << 17
+    grid = o3g.build_grid(cuda(tgt), r * 1.002)
+    grid.set_normals(cuda(nrm))
+    d_src = cuda(src)
+    for k in (0, 4, 8, 12, 20, 40):
+        res = o3g.icp_point_to_plane_grid(grid, d_src, np.eye(4), r, k, correspondences=True)
+        p = oracle.transform(src, res["T"])
+        c_ref, d_ref = oracle.nn(p, tgt, r, method="grid")
+        assert np.array_equal(res["corr"].cpu().numpy(), c_ref), k
+        assert np.array_equal(res["d2"].cpu().numpy(), d_ref), k
+        assert res["fitness"] == float(np.count_nonzero(c_ref >= 0)) / len(c_ref)
 
 
 def test_launch_forms_give_identical_results(o3g):

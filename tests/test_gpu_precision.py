@@ -187,11 +187,13 @@ def test_fragment_icp_both_precisions_within_1e6(o3g, frag, frag_oracle):
 
 
 def test_fragment_warm_search_correspondence_set_bitexact(o3g, frag):
-    """The correspondence set of the final evaluation (found by the warm-started search of the iterations: the
-    neighbour-record walk, with the grid search for the rest) after 1, 3 and 50 iterations: all 2M matches
-    bit-exact against the oracle's search at the GPU's own final pose."""
+    """The correspondence set of the final evaluation (found by the warm-started search of the iterations:
+    before candidate lists, the grid search from the previous matches; then each point's list where it still
+    covers the point, the grid search and a rebuilt list where it does not) after 1, 3, 11 (lists just built),
+    20 (lists being rebuilt as points drift) and 50 iterations: all 2M matches bit-exact against the oracle's
+    search at the GPU's own final pose."""
     pr, grid, src = frag
-    for k in (1, 3, pr.max_iter):
+    for k in (1, 3, 11, 20, pr.max_iter):
         res = o3g.icp_point_to_plane_grid(grid, src, np.eye(4), pr.max_corr_dist, k, correspondences=True)
         p = oracle.transform(pr.src, res["T"])
         c_ref, d_ref = oracle.nn(p, pr.tgt, pr.max_corr_dist, method="grid")
