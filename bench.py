@@ -292,15 +292,17 @@ def run_ours(args, ws, rank, local):
     ms_step = total_ms / args.steps
     value = units / (ms_step / 1e3)
     if rank == 0:
-        def roof(kern, result):
+        def roof(kern, result, traffic):
             ms, n = kern["icp"]
-            return roofline_hbm(icp_alg_bytes(ns, result["fitness"]), ms, n, "k_icp_iter",
-                                profiled_traffic("icp.cu", "k_icp_iter_fragment_2m.md"))
+            return roofline_hbm(icp_alg_bytes(ns, result["fitness"]), ms, n, "k_icp_iter", traffic)
 
+        # DRAM bytes per launch, averaged over one step's launches, from the committed capture of the float32
+        # path (the all-float64 variant is a different kernel: no capture, no traffic figure)
         study = {"f32_compensated": {"ms_per_step": ms_step, "value": ns * res["iters"] / (ms_step / 1e3),
-                                     "roofline": roof(k32, res), "grid_ms": k32["grid"][0] / 3},
+                                     "roofline": roof(k32, res, profiled_traffic("icp.cu", "k_icp_iter_fragment_2m.md")),
+                                     "grid_ms": k32["grid"][0] / 3},
                  "f64": {"ms_per_step": ms64 / f64_steps, "value": ns * res64["iters"] / (ms64 / f64_steps / 1e3),
-                         "roofline": roof(k64, res64)}}
+                         "roofline": roof(k64, res64, None)}}
         cpu = None
         if ws == 1 and not args.no_cpu_baseline:
             cpu = fragment_oracle_study(o3g, synth, pr, tgt, nrm, src, res, res64, study)

@@ -1470,47 +1470,28 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
   int(*const s_lp)[kThreads] = reinterpret_cast<int(*)[kThreads]>(&s_ld[kList][0]);
   float tile_s = 0.f, tile_c = 0.f;  // the tile's partial (threads < kPartial)
   double tile_f64 = 0.0;
-  // A sub-tile's point, its last match and its list, loaded one sub-tile ahead:
-  // the loads of sub-tile k + 1 go out once sub-tile k's correspondences are
-  // found and arrive while its rows are reduced.  (The source, hints and lists
-  // are read once per launch: loaded with the streaming hint, so that the
-  // targets and normals the gathers reuse stay in L2.)
-  struct SubIn {
-    float4 s, pb;
-    int4 l[kListVec];
-    uint2 gap;
-    int hint;
-  } in;
-  const auto load_sub = [&](int sub) {
-    const int i = (j * P.ppt + sub) * kThreads + threadIdx.x;
-    const bool live = i < P.ns;
-    in.s = live ? __ldcs(&P.src4[i]) : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
-    // the last match seeds the search (before lists, of every point; with lists,
-    // of the points their lists no longer cover); the first sub-tile's is loaded
-    // with the state, so that the tile starts with one memory round trip
-    in.hint = (keep && live) ? __ldcs(&P.lists.hint[i]) : -1;
-    in.pb = make_float4(0.f, 0.f, 0.f, -1.f);
-#pragma unroll
-    for (int k = 0; k < kListVec; ++k) in.l[k] = make_int4(-1, -1, -1, -1);
-    in.gap = make_uint2(0u, 0u);
-    if (lists && live) {
-      in.pb = __ldcs(&P.lists.pb[i]);
-#pragma unroll
-      for (int k = 0; k < kListVec; ++k) in.l[k] = __ldcs(&P.lists.idx[kListVec * i + k]);
-      in.gap = __ldcs(&P.lists.gap[i]);
-    }
-  };
-  load_sub(0);
-  if (mode == kIterate && done) return;
   for (int sub = 0; sub < P.ppt; ++sub) {
     const int i = (j * P.ppt + sub) * kThreads + threadIdx.x;
     const bool live = i < P.ns;
-    const float4 s = in.s, pb = in.pb;
-    const int hint = in.hint;
+    // (the source, hints and lists are read once per launch: loaded with the
+    // streaming hint, so that the targets and normals the gathers reuse stay in L2)
+    const float4 s = live ? __ldcs(&P.src4[i]) : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
+    // the last match seeds the search (before lists, of every point; with lists,
+    // of the points their lists no longer cover); loaded with the point, not
+    // after the state, so that the tile starts with one memory round trip
+    int hint = (keep && live) ? __ldcs(&P.lists.hint[i]) : -1;
+    float4 pb = make_float4(0.f, 0.f, 0.f, -1.f);
     int4 l[kListVec];
 #pragma unroll
-    for (int k = 0; k < kListVec; ++k) l[k] = in.l[k];
-    const uint2 gap = in.gap;
+    for (int k = 0; k < kListVec; ++k) l[k] = make_int4(-1, -1, -1, -1);
+    uint2 gap = make_uint2(0u, 0u);
+    if (lists && live) {
+      pb = __ldcs(&P.lists.pb[i]);
+#pragma unroll
+      for (int k = 0; k < kListVec; ++k) l[k] = __ldcs(&P.lists.idx[kListVec * i + k]);
+      gap = __ldcs(&P.lists.gap[i]);
+    }
+    if (mode == kIterate && done) return;
     const float3 p = live ? xform_rn(R, t, s.x, s.y, s.z) : make_float3(3.0e38f, 3.0e38f, 3.0e38f);
     // Once the pair keeps lists, a point whose list still covers it is decided
     // by the list alone; the others search the grid from their last match (and
@@ -1550,7 +1531,6 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
       P.corr_out[o] = bp >= 0 ? __float_as_int(P.g.pts[bp].w) : -1;
       P.d2_out[o] = bp >= 0 ? bd2 : 0.f;
     }
-    if (sub + 1 < P.ppt) load_sub(sub + 1);
     if (mode == kCorrOnly) continue;
     if constexpr (F64) {
       double v[32];
