@@ -323,16 +323,26 @@ __device__ uint64_t warp_knn(const GridView& g, float qx, float qy, float qz, fl
   float hi = r2;          // every buffered key has d2 <= hi
   int m = 0;              // keys in the buffer
   // The box's (x, y) columns, 32 at a time: lane c finds the run of sorted
-  // points of column c over the box's z-range (two loads, all columns at once),
-  // then the warp scans the runs one after another.
+  // points of column c over the z-range the radius allows there (the ball's
+  // extent above the column's nearest point, with the exact search's rounding
+  // margins; a column the ball misses has none), two loads for all columns at
+  // once, then the warp scans the runs one after another.
+  const float margin = search_margin(g.cell, r, qx, qy, qz);
   const uint32_t ny = by - ay + 1, ncols = (bx - ax + 1) * ny;  // <= the grid's cells < 2^31
   for (uint32_t c0 = 0; c0 < ncols; c0 += 32) {
     uint32_t rb = 0, re = 0;
     const uint32_t c = c0 + lane;
     if (c < ncols) {
       const int x = ax + static_cast<int>(c / ny), y = ay + static_cast<int>(c % ny);
-      int zl = az, zh = bz;
-      if (column_z(g, x * g.sy + y, zl, zh)) {
+      const float gx = slab_gap(qx, x + g.lo_x, g.cell, margin), gy = slab_gap(qy, y + g.lo_y, g.cell, margin);
+      const float lim = __fmul_rn(r2, 1.0001f) - (gx * gx + gy * gy);
+      int zl = 1, zh = 0;
+      if (lim >= 0.f) {
+        const float rz = __fadd_rn(fast_sqrt(lim), margin);
+        zl = max(az, cell_coord(__fsub_rn(qz, rz), g.inv_cell) - g.lo_z);
+        zh = min(bz, cell_coord(__fadd_rn(qz, rz), g.inv_cell) - g.lo_z);
+      }
+      if (zl <= zh && column_z(g, x * g.sy + y, zl, zh)) {
         const int col = (x * g.sy + y) * g.sz;
         rb = g.cell_start[col + zl];
         re = g.cell_start[col + zh + 1];
