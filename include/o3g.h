@@ -342,8 +342,10 @@ O3G_API int32_t o3g_icp_point_to_plane_batch(int32_t n_pairs, const o3g_grid* co
  * tiles of a launch)), 0..31, a tile being 128 source points (of one pair, or of
  * one pose in o3g_evaluate_poses).  cfg: 0 automatic (the latency form -- large
  * shared-memory stage, 5 blocks per SM -- while every tile of the launch is
- * resident at once in it, else the throughput form -- smaller stage, 7 blocks
- * per SM), 1 latency form, 2 throughput form.  Process-wide; results do not
+ * resident at once in it, else the throughput form -- per-thread searches from
+ * global memory, candidate lists on large pairs, 9 blocks per SM; for pose
+ * evaluation a smaller stage, 7 blocks per SM), 1 latency form, 2 throughput
+ * form.  Process-wide; results do not
  * depend on it (both forms compute the same thing in the same order), only the
  * time does.  o3g_get_tile_config returns the setting or O3G_ERR_ARG.
  */

@@ -5,7 +5,8 @@ Three knobs:
 * cell size of the target grids, as a multiple of max_correspondence_distance;
 * the launch form of the iteration kernel for the batch's size class of work
   tiles (``o3g.TILE_LATENCY``: large shared-memory stage, 5 blocks per SM;
-  ``o3g.TILE_THROUGHPUT``: smaller stage, 7 blocks per SM, candidate lists),
+  ``o3g.TILE_THROUGHPUT``: per-thread searches from global memory, 9 blocks
+  per SM, candidate lists),
   pinned with ``o3g.set_tile_config``;
 * points per thread (1, 2 or 4: a tile of the iteration kernel is that many
   groups of 128 spatially sorted source points) for each size class of the

@@ -442,17 +442,31 @@ __device__ void box_search_global(const GridView& g, float cell, float px, float
 // from global memory.  All threads of the block must call this.
 constexpr int kStageZ = 15;  // z-cells per column
 
-// Two stage sizes, one per launch configuration.  Latency: every tile of a
-// launch is resident at once (5 blocks per SM), so a large stage keeps blocks
-// off the slower global search.  Throughput: more tiles than resident blocks,
-// so a smaller stage and register budget buy 7 blocks per SM.
+// The launch configurations.  Latency: every tile of a launch is resident at
+// once (5 blocks per SM), and a large block stage keeps the searches off the
+// slower chains of dependent global loads.  Throughput: more tiles than
+// resident blocks; every search runs per thread from global memory (the
+// latency of its dependent loads is hidden by 9 resident blocks per SM, with
+// registers budgeted for them, and the block-wide staging's planning, copies
+// and barriers are saved), and the stage only holds the rows of the reduction
+// and the lists being rebuilt.  On the 2M-point fragment pair this measured
+// 7.93 against 8.41 ms per registration, on the 256-pair batch 39.0 against
+// 47.2 ms per call; on the one-wave RGB-D pair the latency form stays faster.
+// Pose evaluation keeps a staged form for its many launches of cold searches.
 struct CfgLatency {
   static constexpr int kPts = 1792, kCols = 128, kMinBlocks = 5;
   static constexpr bool kLists = false;  // one wave of tiles: lists do not pay (see kListMinPoints)
+  static constexpr bool kStaged = true;
 };
 struct CfgThroughput {
-  static constexpr int kPts = 1024, kCols = 64, kMinBlocks = 7;
+  static constexpr int kPts = 640, kCols = 32, kMinBlocks = 9;
   static constexpr bool kLists = true;
+  static constexpr bool kStaged = false;
+};
+struct CfgEval {
+  static constexpr int kPts = 1024, kCols = 64, kMinBlocks = 7;
+  static constexpr bool kLists = false;
+  static constexpr bool kStaged = true;
 };
 
 // The lists being rebuilt in a tile (see ListSink) take the last kListPts
@@ -462,7 +476,8 @@ constexpr int kListPts = kList * kThreads * 2 * 4 / 16;
 template <class Cfg>
 struct Stage {
   static constexpr int kStagePts = Cfg::kPts, kStageCols = Cfg::kCols;
-  static constexpr bool kLists = Cfg::kLists;
+  static constexpr bool kLists = Cfg::kLists, kStaged = Cfg::kStaged;
+  static_assert(!kLists || kStagePts >= kListPts, "the stage holds the lists being rebuilt");
   float4 pts[kStagePts];
   uint32_t off[kStageCols][kStageZ + 1];  // global cell_start of each z-cell of each column
   uint32_t base[kStageCols + 1];          // staged position of each column's first staged point
@@ -1512,13 +1527,14 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
     if (!lists || __syncthreads_or(need)) {
       if (lists) {
         ListSink ls{nb, s_ld, s_lp, list_lim(nb.d2, sigma), 0, 0.f, 0};
-        if (!staged_search(P.g, P.cell, p.x, p.y, p.z, Rl, need, ls, stage, St::kStagePts - kListPts) && need)
+        if (!(St::kStaged && staged_search(P.g, P.cell, p.x, p.y, p.z, Rl, need, ls, stage, St::kStagePts - kListPts)) &&
+            need)
           box_search_global(P.g, P.cell, p.x, p.y, p.z, Rl, ls);
         if (need) list_store(P.lists, i, ls, p.x, p.y, p.z, sigma);
         nb = ls.nb;
       } else {
         NnSink ns{nb};
-        if (!staged_search(P.g, P.cell, p.x, p.y, p.z, P.r, need, ns, stage) && need)
+        if (!(St::kStaged && staged_search(P.g, P.cell, p.x, p.y, p.z, P.r, need, ns, stage)) && need)
           box_search_global(P.g, P.cell, p.x, p.y, p.z, P.r, ns);
         nb = ns.nb;
       }
@@ -1543,6 +1559,7 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
       // per-correspondence factors as one row per thread in shared memory (the
       // staged points are no longer needed), then the transposed reduction
       __syncthreads();  // every thread has finished reading the staged points
+      static_assert(St::kStagePts * 4 >= kThreads * kRow, "the stage holds one row per thread");
       float* rows = reinterpret_cast<float*>(stage.pts);
       float* row = rows + threadIdx.x * kRow;
       row_factors(P, p, bp, bd2, [&](int k) -> float& { return row[k]; });
@@ -2977,7 +2994,7 @@ extern "C" int32_t o3g_evaluate_poses(const o3g_grid* g, const float* d_src, int
     k_pose_round<<<(n_poses + 127) / 128, 128, 0, s>>>(d_poses.as<double>(), n_poses, d_posef.as<PoseF>());
     const int it = static_cast<int>(std::min<int64_t>(items, 0x7fffffff));
     if (throughput_form(it))
-      k_eval_poses<CfgThroughput><<<grid_for(it, eval_resident<CfgThroughput>()), kThreads, 0, s>>>(
+      k_eval_poses<CfgEval><<<grid_for(it, eval_resident<CfgEval>()), kThreads, 0, s>>>(
           g->view(), g->cell, static_cast<float>(max_corr_dist), src.pts, static_cast<int>(ns), ntiles,
           d_posef.as<PoseF>(), n_poses, part.as<double>());
     else
