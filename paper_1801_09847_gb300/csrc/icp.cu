@@ -384,7 +384,8 @@ __device__ __forceinline__ void first_bound(const GridView& g, float px, float p
 // The exact search from global memory: the home cell first when the sink has no
 // bound yet, then every cell that can still hold a candidate within the sink's
 // bound (box sized from the bound; each column over the z-range the bound
-// allows, clipped to the column's occupied cells).  Every bound carries a
+// allows; empty cells add nothing to a run, so the columns' occupied extents
+// are not looked up: one dependent load fewer per column).  Every bound carries a
 // margin for float32 rounding and ties are kept, so the nearest neighbour is
 // exactly the brute-force minimum and a list holds exactly the nearest.
 // R: the largest radius the sink asks for (its margins are sized by it).
@@ -416,7 +417,7 @@ __device__ void box_search_global(const GridView& g, float cell, float px, float
       const float rz = __fadd_rn(fast_sqrt(lim), margin);
       int zl = max(az, cell_coord(__fsub_rn(pz, rz), g.inv_cell) - g.lo_z);
       int zh = min(bz, cell_coord(__fadd_rn(pz, rz), g.inv_cell) - g.lo_z);
-      if (zl > zh || !column_z(g, x * g.sy + y, zl, zh)) continue;
+      if (zl > zh) continue;
       const int col = (x * g.sy + y) * g.sz;
       const uint32_t b0 = g.cell_start[col + zl], e1 = g.cell_start[col + zh + 1];
       if (home_done && x == hx && y == hy && zl <= hz && hz <= zh) {
