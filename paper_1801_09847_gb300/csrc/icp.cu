@@ -10,7 +10,8 @@
 //      still covers it (see ListSink); otherwise the search starts from the
 //      last matches of the point and its warp neighbours and scans every cell
 //      column whose slab can still hold a point within the bound, over the
-//      z-range that bound allows, staged block-wide in shared memory;
+//      z-range that bound allows (staged block-wide in shared memory in the
+//      latency form, per thread from global memory in the throughput form);
 //   3. r = (p - q) . n, J = [p x n ; n]; the 21 upper entries of J^T J, J^T r,
 //      r^2, d2 and |C| as exact (value, error) pairs, summed over the tile's
 //      rows in a fixed order into one compensated float32 pair per sum, which
@@ -37,7 +38,6 @@ namespace o3g {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kPPT = 1;       // source points per thread
 constexpr int kPartial = 32;  // sum columns of a block partial (column kBadCol: see add_fixed)
 constexpr int kAccRows = 32;  // fixed-point accumulator rows of a pair (its tiles spread over them)
 constexpr int kBadCol = 31;   // accumulator column counting partials outside their bound
@@ -471,7 +471,7 @@ struct CfgEval {
 };
 
 // The lists being rebuilt in a tile (see ListSink) take the last kListPts
-// points of the stage, which then holds kListPts fewer candidates.
+// points of the stage (a staged search then holds kListPts fewer candidates).
 constexpr int kListPts = kList * kThreads * 2 * 4 / 16;
 
 template <class Cfg>
@@ -1512,9 +1512,10 @@ __device__ void icp_tile(const PairDesc& P, int j, int mode, St& stage) {
     // Once the pair keeps lists, a point whose list still covers it is decided
     // by the list alone; the others search the grid from their last match (and
     // rebuild their lists).  Before that, every point searches from the last
-    // matches of itself and its warp neighbours.  The searches of a sub-tile run
-    // block-staged in shared memory (each from global memory when the staged
-    // set does not fit).
+    // matches of itself and its warp neighbours.  In the latency form the
+    // searches of a sub-tile run block-staged in shared memory (each from
+    // global memory when the staged set does not fit); in the throughput form
+    // each runs from global memory.
     Nearest nb{r2, 0x7fffffff, -1};
     bool need = live;
     if (lists) {
@@ -1747,10 +1748,9 @@ inline int pair_tiles(int64_t ns, int ppt) {
   return static_cast<int>(b < 1 ? 1 : b);
 }
 
-inline int iter_blocks(int64_t ns) {
-  int64_t b = (ns + kThreads * kPPT - 1) / (kThreads * kPPT);
-  return static_cast<int>(b < 1 ? 1 : b);
-}
+// Tiles of kThreads points (one point per thread): the allocation-free call's
+// tiles, pose evaluation's, and an upper bound on any pair's tiles.
+inline int tiles_of(int64_t ns) { return pair_tiles(ns, 1); }
 
 bool pose_ok(const double* T) {
   if (!T) return false;
@@ -1766,7 +1766,7 @@ Pose to_pose(const double* T) {
 }
 
 int32_t check_src(const char* fn, const float* d_src, int64_t ns, int32_t stride) {
-  if (ns < 0 || ns > 0x7fffffffLL - kThreads * kPPT || (ns > 0 && !d_src) || stride < 3) {
+  if (ns < 0 || ns > 0x7fffffffLL - kThreads || (ns > 0 && !d_src) || stride < 3) {
     set_error("%s: invalid source cloud (n=%lld stride=%d)", fn, static_cast<long long>(ns), stride);
     return O3G_ERR_ARG;
   }
@@ -2154,7 +2154,7 @@ extern "C" int32_t o3g_icp_point_to_plane_grid_noalloc(const o3g_grid* g, const 
   unsigned long long* acc = reinterpret_cast<unsigned long long*>(base + kNaOffAcc);
   int* bad = reinterpret_cast<int*>(base + kNaOffFlag);
   const int n = static_cast<int>(ns);
-  const int nblk = iter_blocks(ns);
+  const int nblk = tiles_of(ns);
   // the accumulators and the input flag must start at zero; the state is rewritten by k_init_state
   O3G_TRY(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * kPartial * accum_rows(nblk), s));
   O3G_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
@@ -2486,7 +2486,7 @@ namespace {
 
 // Device memory a request will hold while admitted (upper bound before its grid exists).
 int64_t request_bytes(int64_t ns, int64_t nt) {
-  const int64_t rows = accum_rows(iter_blocks(ns));
+  const int64_t rows = accum_rows(tiles_of(ns));
   return ns * (16 + static_cast<int64_t>(kListBytes) + 12) + rows * kPartial * 8 + nt * (16 + 16 + 4 + 12 + 12) +
          4 * (32 * nt + (1 << 20)) + sizeof(IcpState);
 }
@@ -2979,7 +2979,7 @@ extern "C" int32_t o3g_evaluate_poses(const o3g_grid* g, const float* d_src, int
     }
   if (n_poses == 0) return O3G_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int ntiles = iter_blocks(ns);
+  const int ntiles = tiles_of(ns);
   const int64_t items = static_cast<int64_t>(ntiles) * n_poses;
   SortedCloud src(s);
   DevBuf d_poses(s), d_posef(s), part(s), out(s);
