@@ -318,8 +318,21 @@ __global__ void __launch_bounds__(kThreads) k_rs_scatter(const uint32_t* __restr
 
 // ------------------------------------------------------ cell table, gather
 
-__global__ void __launch_bounds__(kThreads) k_cell_start(const uint32_t* __restrict__ skeys, int n,
-                                                         uint32_t* __restrict__ cell_start, int64_t cells) {
+// cell_start[c] = the number of points whose key is < c (the first position
+// with key >= c), c = 0 .. cells.  Small tables: one binary search over all n
+// keys per cell (k_cell_start_direct).  Large tables (more cells than
+// kChunkedMinCells, where every thread of a full wave has several cells): a
+// block takes kCellsPerThread * kThreads consecutive cells, two threads find
+// the positions of the chunk's first cell and of the cell after it, every cell
+// of the chunk starts between those two, and each thread finds its cells'
+// starts by binary searches inside that narrow range (cached; coalesced
+// writes).  Measured: the 2M-point fragment's 8.5M-cell grid 0.316 -> 0.278 ms;
+// on the RGB-D frame's 53,200-cell table (52 chunks) the direct form stays
+// faster (0.077 against 0.090 ms).
+constexpr int kCellsPerThread = 8;
+constexpr int64_t kChunkedMinCells = int64_t{4} * kNumSMs * 16 * kThreads;
+__global__ void __launch_bounds__(kThreads) k_cell_start_direct(const uint32_t* __restrict__ skeys, int n,
+                                                                uint32_t* __restrict__ cell_start, int64_t cells) {
   for (int64_t c = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; c <= cells;
        c += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     int lo = 0, hi = n;  // first position with key >= c
@@ -329,6 +342,31 @@ __global__ void __launch_bounds__(kThreads) k_cell_start(const uint32_t* __restr
       else hi = mid;
     }
     cell_start[c] = static_cast<uint32_t>(lo);
+  }
+}
+__device__ __forceinline__ int key_lower_bound(const uint32_t* __restrict__ skeys, int lo, int hi, int64_t c) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (static_cast<int64_t>(skeys[mid]) < c) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+__global__ void __launch_bounds__(kThreads) k_cell_start(const uint32_t* __restrict__ skeys, int n,
+                                                         uint32_t* __restrict__ cell_start, int64_t cells) {
+  __shared__ int range[2];
+  const int64_t chunk = static_cast<int64_t>(kThreads) * kCellsPerThread;
+  for (int64_t c0 = static_cast<int64_t>(blockIdx.x) * chunk; c0 <= cells;
+       c0 += static_cast<int64_t>(gridDim.x) * chunk) {
+    if (threadIdx.x < 2) range[threadIdx.x] = key_lower_bound(skeys, 0, n, threadIdx.x == 0 ? c0 : c0 + chunk);
+    __syncthreads();
+    const int rlo = range[0], rhi = range[1];
+    for (int k = 0; k < kCellsPerThread; ++k) {
+      const int64_t c = c0 + static_cast<int64_t>(k) * kThreads + threadIdx.x;
+      if (c > cells) break;
+      cell_start[c] = static_cast<uint32_t>(key_lower_bound(skeys, rlo, rhi, c));
+    }
+    __syncthreads();  // range is rewritten for the next chunk
   }
 }
 
@@ -875,9 +913,11 @@ static int32_t build_impl(const float* d_xyz, int64_t n64, int stride, float cel
   O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->pts), sizeof(float4) * n, s));
   O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->nrm), sizeof(float4) * (n + 1), s));
   O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->pos_of), sizeof(int32_t) * n, s));
-  int nbc = blocks_for(cells + 1, kThreads);
+  const bool chunked = cells + 1 > kChunkedMinCells;
+  int nbc = blocks_for(cells + 1, chunked ? kThreads * kCellsPerThread : kThreads);
   if (nbc > kNumSMs * 16) nbc = kNumSMs * 16;
-  k_cell_start<<<nbc, kThreads, 0, s>>>(keys.as<uint32_t>(), n, g->cell_start, cells);
+  if (chunked) k_cell_start<<<nbc, kThreads, 0, s>>>(keys.as<uint32_t>(), n, g->cell_start, cells);
+  else k_cell_start_direct<<<nbc, kThreads, 0, s>>>(keys.as<uint32_t>(), n, g->cell_start, cells);
   const int ncol = g->span[0] * g->span[1];
   O3G_TRY(dmalloc(reinterpret_cast<void**>(&g->col_z), sizeof(uint32_t) * ncol, s));
   int nbz = blocks_for(ncol, kThreads);
