@@ -134,3 +134,61 @@ def test_codes_rounded_up_are_caught():
     sigma = f32(0.002)
     bad = sum(violations(*_collinear(g, 20000, sigma), sigma, g, round_up=True)[0] for _ in range(3))
     assert bad > 0
+
+
+def _lists(g, tgt, pb, r, sigma):
+    """Lists built at pb as the kernel builds them: lim from the nearest within r (r2 when none), the <= 8
+    nearest by (d2, index) within lim, rho2 = lim when fewer are held, else the 8th d2."""
+    r2 = (f32(r) * f32(r)).astype(f32)
+    d2 = dist2_rn(pb[:, None, :], tgt[None, :, :])
+    idx = np.arange(len(tgt))[None, :].repeat(len(pb), 0)
+    order = np.lexsort((idx, d2), axis=1)
+    d2s = np.take_along_axis(d2, order, axis=1)
+    D = np.where(d2s[:, 0] <= r2, d2s[:, 0], r2).astype(f32)
+    s = (fast_sqrt((D * f32(1.0001)).astype(f32), g) + sigma).astype(f32)
+    lim = ((s * s).astype(f32) * f32(1.0001)).astype(f32)
+    inl = d2s[:, :8] <= lim[:, None]
+    m = inl.sum(axis=1)
+    rho2 = np.where(m < 8, lim, d2s[:, 7]).astype(f32)
+    return order[:, :8], inl, rho2
+
+
+def test_a_covering_list_holds_the_exact_nearest():
+    """The validity test of a list at a new position p: while (sqrt(D') + |p - p_b|)^2 (with the kernel's
+    margins) is below rho2, D' being the best listed d2 within r2 (r2 if none), the exact float32 nearest
+    neighbour within r, ties to the lower index, is a listed target or there is none.  Random clouds,
+    quantised clouds with duplicates (ties at every distance), moves from 0 to 2 sigma."""
+    g = np.random.default_rng(5)
+    r, sigma = 0.02, f32(0.002)
+    r2 = (f32(r) * f32(r)).astype(f32)
+    covered_total = 0
+    for quant in (None, 0.001):
+        tgt = g.uniform(0.0, 0.05, (1500, 3))
+        if quant:
+            tgt = np.round(tgt / quant) * quant
+            tgt[750:900] = tgt[:150]
+        tgt = tgt.astype(f32)
+        pb = g.uniform(0.005, 0.045, (3000, 3)).astype(f32)
+        if quant:
+            pb = (np.round(pb / quant) * quant).astype(f32)
+        lists, inl, rho2 = _lists(g, tgt, pb, r, sigma)
+        for motion in (0.0, 0.3, 1.0, 2.0):
+            dirs = g.normal(size=pb.shape)
+            dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+            p = (pb + dirs * g.uniform(0.0, motion * float(sigma), (len(pb), 1))).astype(f32)
+            if quant and motion == 0.3:
+                p = (np.round(p / quant) * quant).astype(f32)
+            d2l = dist2_rn(p[:, None, :], tgt[lists])
+            d2l = np.where(inl & (d2l <= r2), d2l, np.inf)
+            Dp = np.minimum(d2l.min(axis=1), r2).astype(f32)
+            moved = dist2_rn(p, pb)
+            s = (fast_sqrt((Dp * f32(1.0001)).astype(f32), g) + fast_sqrt((moved * f32(1.0001)).astype(f32), g)).astype(f32)
+            covered = (((s * s).astype(f32) * f32(1.0001)).astype(f32) + f32(1e-30)) < rho2
+            d2 = dist2_rn(p[:, None, :], tgt[None, :, :])
+            d2 = np.where(d2 <= r2, d2, np.inf)
+            best = np.lexsort((np.arange(len(tgt))[None, :].repeat(len(p), 0), d2), axis=1)[:, 0]
+            has = np.isfinite(d2[np.arange(len(p)), best])
+            listed = ((lists == best[:, None]) & inl).any(axis=1)
+            assert np.all(~covered | ~has | listed), (quant, motion)
+            covered_total += int(covered.sum())
+    assert covered_total > 5000  # most lists cover small moves
