@@ -241,7 +241,13 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    pr = synth.fragment_pair(seed=4 + rank)
+    # every rank registers its own copy of the pair (replicas); rank 0 renders it into the cache first, so
+    # that the ranks of a node do not render it at once
+    if dist and rank != 0:
+        dist.barrier()
+    pr = synth.fragment_pair(seed=4)
+    if dist and rank == 0:
+        dist.barrier()
     ns, nt, r, iters = len(pr.src), len(pr.tgt), pr.max_corr_dist, pr.max_iter
     src = torch.from_numpy(pr.src).to(dev)
     tgt = torch.from_numpy(pr.tgt).to(dev)
